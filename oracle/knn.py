@@ -1,0 +1,103 @@
+"""Exact kNN for the oracle (TEST INFRASTRUCTURE ONLY; see oracle/__init__.py).
+
+`knn` calls the plain C brute force in knn_bf.c (compiled by `build()` with
+-ffp-contract=off, OpenMP over rows).  `knn_dense` is an independent numpy
+brute force over the full distance matrix, used to pin the C code on small n.
+
+Definition (Sec. 2.1, Eq. for b^2 and I(x, k)): the k nearest *other* samples,
+ordered by the canonical FP64 squared distance, ties broken by smaller index.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "knn_bf.c")
+_LIB = os.path.join(_HERE, "_build", "libknn_bf.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile knn_bf.c into oracle/_build/libknn_bf.so (plain gcc, no contraction)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.oracle_knn.restype = ctypes.c_int
+            lib.oracle_knn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+            lib.oracle_pair_d2.restype = None
+            lib.oracle_pair_d2.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int64, ctypes.c_void_p]
+            _lib = lib
+    return _lib
+
+
+def knn(x: np.ndarray, k: int, rows: tuple[int, int] | None = None):
+    """Exact kNN of the FP32 points x [n, m] for rows [r0, r1) (all rows by default).
+    Returns (nbr int32 [rows, k], nbr_d2 float64 [rows, k])."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    n, m = x.shape
+    r0, r1 = (0, n) if rows is None else rows
+    nbr = np.empty((r1 - r0, k), dtype=np.int32)
+    d2 = np.empty((r1 - r0, k), dtype=np.float64)
+    rc = _load().oracle_knn(x.ctypes.data, n, m, k, r0, r1, nbr.ctypes.data, d2.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle_knn: k={k} outside [1, n-1] for n={n}")
+    return nbr, d2
+
+
+def pair_d2(x: np.ndarray, a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Canonical FP64 squared distances of the pairs (a[t], b[t])."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    a = np.ascontiguousarray(a, dtype=np.int64)
+    b = np.ascontiguousarray(b, dtype=np.int64)
+    out = np.empty(a.shape[0], dtype=np.float64)
+    _load().oracle_pair_d2(x.ctypes.data, x.shape[1], a.ctypes.data, b.ctypes.data, a.shape[0], out.ctypes.data)
+    return out
+
+
+def dense_d2(x: np.ndarray) -> np.ndarray:
+    """Full n x n matrix of canonical FP64 squared distances, in numpy: per
+    coordinate an RN difference and square, summed in ascending coordinate order."""
+    x64 = np.asarray(x, dtype=np.float32).astype(np.float64)
+    acc = None
+    for r in range(x64.shape[1]):
+        dl = x64[:, None, r] - x64[None, :, r]
+        s = dl * dl
+        acc = s if acc is None else acc + s
+    return acc
+
+
+def knn_dense(x: np.ndarray, k: int):
+    """Independent brute force for small n: lexicographic sort of every row of
+    the dense distance matrix by (d2, j), self removed."""
+    d2 = dense_d2(x)
+    n = d2.shape[0]
+    nbr = np.empty((n, k), dtype=np.int32)
+    out = np.empty((n, k), dtype=np.float64)
+    idx = np.arange(n)
+    for i in range(n):
+        mask = idx != i
+        j = idx[mask]
+        dj = d2[i, mask]
+        order = np.lexsort((j, dj))[:k]
+        nbr[i] = j[order]
+        out[i] = dj[order]
+    return nbr, out
