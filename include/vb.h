@@ -1,0 +1,265 @@
+/*
+ * vb.h -- C ABI of libvb: the sparse self-tuning variable-bandwidth (VB) kernel
+ * build of Davis & Giannakis, "Graph-theoretic algorithms for Kolmogorov
+ * operators" (arXiv 2104.15124), on one NVIDIA GB300 (sm_103a).
+ *
+ * The library turns n samples x^(i) in R^m (Sec. 2, problem statement) into
+ * the sparse symmetric matrix L-hat that approximates the Kolmogorov operator
+ * L_{psi,c} (Eq. symmetric discrete Kolmogorov operator), following the four
+ * steps of Sec. 4: exact kNN and the bandwidth b (Eq. bandwidth parameter),
+ * the self-tuned density kernel and density estimate psi (Sec. 2.1, 2.3), the
+ * self-tuned operator kernel and its normalisations (Sec. 2.2), the CSR of
+ * L-hat, and the sparse matrix-vector product consumed by eigen-solvers.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: VB_OK (0) or a negative vb_status.  Argument and launch
+ *     errors are returned synchronously; errors found on the device (a zero
+ *     bandwidth, a non-finite coordinate, an over-full row) are recorded in the
+ *     context's device report and read with vb_report_read().
+ *   - Every pointer argument is a DEVICE pointer owned by the caller unless
+ *     stated otherwise; arrays are dense and contiguous.  The library never
+ *     allocates, frees or keeps caller memory.  Scratch memory comes from a
+ *     caller-provided workspace of at least the size returned by the matching
+ *     vb_*_workspace() call (256-byte aligned base).
+ *   - All work is enqueued asynchronously on the context's CUDA stream.  No
+ *     call synchronises the host except vb_report_read() and vb_solve().
+ *   - Indices: int32 for points and columns, int64 for row offsets.
+ *     Limits: 2 <= n < 2^31 - 1, 1 <= m <= 128, 1 <= k <= n - 1,
+ *     k + margin <= 256.
+ *   - Sizes whose value is data-dependent (the number of stored entries nnz)
+ *     stay on the device; callers size CSR outputs for the worst case
+ *     n * (2k + 1) and read nnz from the device.
+ */
+#ifndef VB_H
+#define VB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t vb_status;
+#define VB_OK                 0
+#define VB_ERR_ARG           -1   /* invalid argument (sizes, NULL, limits) */
+#define VB_ERR_CUDA          -2   /* a CUDA runtime call or launch failed */
+#define VB_ERR_WORKSPACE     -3   /* workspace smaller than required */
+#define VB_ERR_DEGENERATE    -4   /* b_i = 0 (more than k_bw copies of a point) or non-finite input */
+#define VB_ERR_EPS_BOUNDARY  -5   /* tuned epsilon sits at an end of its grid (reported as a warning) */
+#define VB_ERR_NOT_CONVERGED -6   /* eigen-solver did not reach its tolerance */
+#define VB_ERR_TIMEOUT       -7   /* a bounded device-side wait ran out */
+#define VB_ERR_BOUNDS        -8   /* an index fell outside its array (debug checks) */
+#define VB_ERR_UNSUPPORTED   -9   /* valid request outside what this build handles */
+
+/* Human-readable name of a status code (static string). */
+const char* vb_status_string(vb_status s);
+
+/* ------------------------------------------------------------------ context */
+
+typedef struct vb_ctx vb_ctx;
+
+/* Creates a context bound to CUDA device `device` and stream `stream`
+ * (a cudaStream_t; NULL = legacy default stream).  Allocates one 256-byte
+ * device report block and a pinned host mirror, freed by vb_destroy(). */
+vb_status vb_create(vb_ctx** ctx, int32_t device, void* stream);
+vb_status vb_destroy(vb_ctx* ctx);
+/* Rebinds the context to another stream of the same device. */
+vb_status vb_set_stream(vb_ctx* ctx, void* stream);
+
+/* Device-side report of the work enqueued since the last reset. */
+typedef struct {
+    int32_t error;              /* first device-detected vb_status, 0 if none */
+    int32_t warnings;           /* bit 0: density epsilon at a grid end; bit 1: operator epsilon at a grid end */
+    int64_t knn_fallback_rows;  /* kNN rows whose FP32 candidate list failed the FP64 certificate */
+    int64_t knn_candidates;     /* (query, candidate) distances evaluated by the tiled search */
+    int64_t union_big_rows;     /* rows of the symmetric union longer than the warp path's limit */
+    int64_t reserved[4];
+} vb_report;
+
+/* Waits for the context's stream and copies the device report to *out. */
+vb_status vb_report_read(vb_ctx* ctx, vb_report* out);
+/* Clears the device report (asynchronous, on the context's stream). */
+vb_status vb_report_reset(vb_ctx* ctx);
+
+/* Measurement hooks (not part of the paper's method).  When enabled, every
+ * stage below is bracketed by CUDA events on the context's stream, and the
+ * host counts the kernel launches it enqueues. */
+#define VB_STAGE_KNN_ORDER       0   /* bounding box, Morton keys, radix sort, gather, tile boxes */
+#define VB_STAGE_KNN_TILE        1   /* tiled FP32 search, FP64 rescoring and certificate */
+#define VB_STAGE_KNN_FALLBACK    2   /* exact FP64 selection of uncertified rows */
+#define VB_STAGE_GRAPH           3   /* symmetric union CSR */
+#define VB_STAGE_BANDWIDTH       4
+#define VB_STAGE_SWEEP_DENSITY   5
+#define VB_STAGE_DENSITY         6
+#define VB_STAGE_CENTRE          7
+#define VB_STAGE_SWEEP_OPERATOR  8
+#define VB_STAGE_OPERATOR        9   /* q and D passes */
+#define VB_STAGE_LHAT           10   /* L-hat CSR values */
+#define VB_NUM_STAGES           11
+vb_status vb_profile_enable(vb_ctx* ctx, int32_t on);
+/* Synchronises the stream; ms[s] = duration of stage s in its most recent run
+ * since the last read (negative when it did not run); *launches = kernels
+ * enqueued since profiling was enabled.  Either output may be NULL. */
+vb_status vb_profile_read(vb_ctx* ctx, float* ms, int64_t* launches);
+
+/* --------------------------------------------------------------- kNN (a1-a5)
+ * Exact k nearest neighbours (Sec. 2.1: I(x, r) is the r-th closest sample,
+ * I(x^(i), 0) = i, so the point itself is excluded).  Distances are the
+ * canonical FP64 squared distances
+ *     d2 = ((s_0 + s_1) + s_2) + ...,  s_r = (x_ir - x_jr)^2  (RN, no FMA),
+ * and neighbours are ordered by (d2, j): distance first, then smaller index.
+ * The search stages the points in a Morton order, prunes 64-point tiles by
+ * bounding boxes and keeps the k + margin nearest FP32 candidates per row;
+ * an FP64 rescoring with a proven FP32 error bound certifies every row, and
+ * rows that fail it are recomputed by an exact FP64 radix selection.  The
+ * output is therefore exact, identical to a brute-force FP64 search. */
+
+#define VB_PREC_FP32 0    /* FP32 ALU distances */
+#define VB_PRUNE_NONE  0  /* visit every candidate tile (brute force) */
+#define VB_PRUNE_EXACT 1  /* skip tiles whose box distance exceeds the running k+margin-th distance */
+
+typedef struct {
+    int32_t k;          /* neighbours per point */
+    int32_t margin;     /* extra FP32 candidates kept for the certificate (16 is typical) */
+    int32_t precision;  /* VB_PREC_* */
+    int32_t prune;      /* VB_PRUNE_* */
+} vb_knn_params;
+
+/* Workspace bytes vb_knn() needs for n points in R^m. */
+size_t vb_knn_workspace(int64_t n, int32_t m, const vb_knn_params* p);
+
+/* x: n x m FP32 row-major.  nbr: n x k int32, nbr_d2: n x k FP64 (row i holds
+ * the neighbours of point i in rank order). */
+vb_status vb_knn(vb_ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_params* p,
+                 int32_t* nbr, double* nbr_d2, void* ws, size_t ws_bytes);
+
+/* ------------------------------------------------- symmetric pattern (a6)
+ * The sparsity pattern of the kernel matrices: the diagonal (Algorithm 1
+ * starts its inner loop at j = i) united with every kNN pair in both
+ * directions (K^ij = K^ji, Algorithm 1).  Rows are sorted by column; ed2
+ * holds every stored entry's squared distance rounded to FP32 (0 on the
+ * diagonal), bitwise symmetric. */
+
+typedef struct {
+    int64_t n;
+    const int64_t* row_ptr;  /* n + 1 */
+    const int32_t* col;      /* nnz */
+    const float* ed2;        /* nnz */
+} vb_graph;
+
+size_t vb_graph_workspace(int64_t n, int32_t k);
+
+/* nbr / nbr_d2 as written by vb_knn().  row_ptr: n + 1 int64; col, ed2: cap
+ * entries, cap >= n * (2k + 1); nnz_dev: one int64 receiving nnz. */
+vb_status vb_graph_build(vb_ctx* ctx, int64_t n, int32_t k, const int32_t* nbr, const double* nbr_d2,
+                         int64_t* row_ptr, int32_t* col, float* ed2, int64_t cap, int64_t* nnz_dev,
+                         void* ws, size_t ws_bytes);
+
+/* --------------------------------------------------------- bandwidth (a8)
+ * Eq. (bandwidth parameter): b_i^2 = sum_{r=1}^{k_bw} d2(i, I(i, r)), summed in
+ * rank order in FP64; b = sqrt(b^2).  nbr_d2: n x k with k_bw <= k.  A zero
+ * b_i records VB_ERR_DEGENERATE in the report. */
+vb_status vb_bandwidth(vb_ctx* ctx, int64_t n, int32_t k, int32_t k_bw, const double* nbr_d2, double* b);
+
+/* -------------------------------------------------- epsilon sweep (a9, a11)
+ * Sec. 2.3, Eq. (bandwidth sensitivity): with eps^2 = 2^xi on the grid
+ * xi_g = xi_c + xi_lo + g * dxi (g = 0 .. G-1, G <= 64),
+ *     chi_g  = sum_{(i,j) in E} exp(-ed2_ij / (scale * 2^xi_g * rho_i * rho_j)),
+ *     chi'_g = (ln chi_{g+1} - ln chi_g) / (dxi ln 2),
+ * g* = the first maximiser of chi', eps2 = 2^xi_{g*}, dim_est = 2 chi'_{g*}.
+ * scale = 1 with rho = b gives the density sweep (K_eps); scale = 4 with
+ * rho = P = psi^beta the operator sweep (K_{eps,beta}, rho = 2 psi^beta in
+ * Algorithm 1).  xi_c_dev: optional device FP64 grid offset (NULL = 0).
+ * Outputs (device FP64): eps2_dev[1], chi_dev[G], dim_est_dev[1].
+ * warn_bit (1 or 2) is set in the report when g* is an end of the grid. */
+size_t vb_epsilon_tune_workspace(int64_t n);
+vb_status vb_epsilon_tune(vb_ctx* ctx, const vb_graph* g, const double* rho, double scale,
+                          const double* xi_c_dev, double xi_lo, double xi_hi, double dxi, int32_t warn_bit,
+                          double* eps2_dev, double* chi_dev, double* dim_est_dev, void* ws, size_t ws_bytes);
+
+/* ---------------------------------------------------------- density (a10)
+ * Eq. (density estimation): psi = W^-1 K_eps 1 with
+ * K_eps^ij = exp(-ed2_ij / (eps^2 b_i b_j)), W_ii = n (pi eps^2 b_i^2)^(d/2);
+ * P_i = psi_i^beta (Sec. 2.2).  eps2_dev: device FP64 scalar. */
+size_t vb_density_workspace(int64_t n);
+vb_status vb_density(vb_ctx* ctx, const vb_graph* g, const double* b, const double* eps2_dev, double d,
+                     double beta, double* psi, double* P, void* ws, size_t ws_bytes);
+
+/* Operator-sweep centre (the paper leaves the grid of the operator sweep
+ * unstated; this library centres it):
+ *     xi_c = round(4 log2(sum_E' ed2/(4 P_i P_j) / sum_E' ed2/(b_i b_j))) / 4,
+ * E' = off-diagonal entries.  Writes one FP64 to xi_c_dev. */
+size_t vb_operator_centre_workspace(int64_t n);
+vb_status vb_operator_centre(vb_ctx* ctx, const vb_graph* g, const double* b, const double* P,
+                             double* xi_c_dev, void* ws, size_t ws_bytes);
+
+/* ------------------------------------------- operator and L-hat (a12-a13)
+ * Sec. 2.2 in order: K_{eps,beta}^ij = exp(-ed2/(4 eps^2 P_i P_j)),
+ * q_i = psi_i^(-beta d) sum_j K^ij, K~^ij = K^ij / (q_i q_j)^alpha with
+ * alpha = (2 - c + (d + 2) beta) / 2 (from c = 2 - 2 alpha + d beta + 2 beta),
+ * D_i = sum_j K~^ij, S_i = P_i D_i^(1/2), and the CSR values of
+ *     L-hat = eps^-2 (S^-1 K~ S^-1 - P^-2)   (Eq. symmetric discrete Kolmogorov operator)
+ * written as L-hat_ij = K~^ij / (eps^2 S_i S_j) off the diagonal and
+ * L-hat_ii = -sum_{j != i} K~^ij / (eps^2 S_i^2) on it (the same value,
+ * since S P^-2 S = D, without cancellation).  val is bitwise symmetric.
+ * val: nnz FP32 in the graph's order; q, D, S: n FP64. */
+typedef struct {
+    double c;      /* Kolmogorov operator parameter */
+    double beta;   /* variable-bandwidth exponent (the paper's examples use -1/4) */
+    double d;      /* intrinsic dimension */
+} vb_op_params;
+
+size_t vb_kernel_csr_workspace(int64_t n);
+vb_status vb_kernel_csr(vb_ctx* ctx, const vb_graph* g, const double* psi, const double* P,
+                        const vb_op_params* op, const double* eps2_op_dev, float* val, double* q, double* D,
+                        double* S, void* ws, size_t ws_bytes);
+
+/* ------------------------------------------------------------- SpMV (a14)
+ * y = alpha * A x + beta * y for the CSR matrix (g, val), one warp per row.
+ * VB_SPMV_PLAIN uses every stored value.  VB_SPMV_LAPLACIAN applies L-hat in
+ * difference form, y_i = alpha * sum_{j != i} val_ij S_j (x_j/S_j - x_i/S_i)
+ * + beta y_i, which equals L-hat x because L-hat (S 1) = 0, and keeps the
+ * accuracy of smooth vectors: the differences x_j/S_j - x_i/S_i are taken in
+ * FP64 and the diagonal is not read.  S: n FP64, used in Laplacian mode only,
+ * which also needs a workspace of vb_spmv_workspace(n) bytes (plain mode
+ * accepts ws = NULL).  x, y: n FP32 (x and y must not alias). */
+#define VB_SPMV_PLAIN     0
+#define VB_SPMV_LAPLACIAN 1
+size_t vb_spmv_workspace(int64_t n);
+vb_status vb_spmv(vb_ctx* ctx, const vb_graph* g, const float* val, const double* S, int32_t mode,
+                  float alpha, const float* x, float beta, float* y, void* ws, size_t ws_bytes);
+
+/* ------------------------------------------------- the whole build (a0-a13)
+ * One call for Sec. 4 steps 1-3 up to L-hat: kNN, pattern, bandwidth,
+ * density sweep, density, operator-sweep centre, operator sweep, L-hat.
+ * Every array is a caller-owned device buffer. */
+typedef struct {
+    vb_knn_params knn;
+    int32_t k_bw;         /* neighbours in b (<= knn.k; 0 = knn.k) */
+    vb_op_params op;
+    double xi_lo, xi_hi, dxi;   /* sweep grid (the paper's parameterisation eps^2 = 2^xi) */
+    int32_t pin_eps;      /* 1 = skip both sweeps and use *eps2_den / *eps2_op as given */
+} vb_build_params;
+
+typedef struct {
+    int32_t* nbr;      double* nbr_d2;             /* n x k */
+    double* b;                                     /* n */
+    int64_t* row_ptr;  int32_t* col; float* ed2;   /* n + 1, cap, cap */
+    int64_t cap;       int64_t* nnz;               /* cap >= n (2k + 1); nnz: 1 */
+    double* eps2_den;  double* chi_den; double* dim_den;   /* 1, G, 1 */
+    double* psi;       double* P;                  /* n, n */
+    double* xi_c;                                  /* 1 */
+    double* eps2_op;   double* chi_op;  double* dim_op;    /* 1, G, 1 */
+    float* val;                                    /* cap */
+    double* q;         double* D;       double* S; /* n, n, n */
+} vb_build_out;
+
+size_t vb_build_workspace(int64_t n, int32_t m, const vb_build_params* p);
+vb_status vb_build(vb_ctx* ctx, const float* x, int64_t n, int32_t m, const vb_build_params* p,
+                   const vb_build_out* out, void* ws, size_t ws_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VB_H */

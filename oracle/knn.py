@@ -42,6 +42,9 @@ def _load():
             lib.oracle_knn.restype = ctypes.c_int
             lib.oracle_knn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+            lib.oracle_knn_rows.restype = ctypes.c_int
+            lib.oracle_knn_rows.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
             lib.oracle_pair_d2.restype = None
             lib.oracle_pair_d2.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_int64, ctypes.c_void_p]
@@ -60,6 +63,20 @@ def knn(x: np.ndarray, k: int, rows: tuple[int, int] | None = None):
     rc = _load().oracle_knn(x.ctypes.data, n, m, k, r0, r1, nbr.ctypes.data, d2.ctypes.data)
     if rc != 0:
         raise ValueError(f"oracle_knn: k={k} outside [1, n-1] for n={n}")
+    return nbr, d2
+
+
+def knn_rows(x: np.ndarray, k: int, rows: np.ndarray):
+    """Exact kNN of the listed rows only (output row t is point rows[t])."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    n, m = x.shape
+    nbr = np.empty((rows.shape[0], k), dtype=np.int32)
+    d2 = np.empty((rows.shape[0], k), dtype=np.float64)
+    rc = _load().oracle_knn_rows(x.ctypes.data, n, m, k, rows.ctypes.data, rows.shape[0], nbr.ctypes.data,
+                                 d2.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_knn_rows: bad k or row index")
     return nbr, d2
 
 

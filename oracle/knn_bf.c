@@ -43,14 +43,34 @@ void oracle_pair_d2(const float* x, int32_t m, const int64_t* a, const int64_t* 
  * row-major n x m).  nbr / nbr_d2 hold (row_end - row_begin) x k entries.
  * Returns 0, or -1 when k is outside [1, n - 1].
  */
+static void knn_row(const float* x, int64_t n, int32_t m, int32_t k, int64_t i, int32_t* bj, double* bd);
+
 int oracle_knn(const float* x, int64_t n, int32_t m, int32_t k, int64_t row_begin, int64_t row_end,
                int32_t* nbr, double* nbr_d2)
 {
     if (k < 1 || (int64_t)k > n - 1 || row_begin < 0 || row_end > n || row_begin > row_end) return -1;
     #pragma omp parallel for schedule(dynamic, 8)
-    for (int64_t i = row_begin; i < row_end; ++i) {
-        double* bd = nbr_d2 + (i - row_begin) * k;
-        int32_t* bj = nbr + (i - row_begin) * k;
+    for (int64_t i = row_begin; i < row_end; ++i)
+        knn_row(x, n, m, k, i, nbr + (i - row_begin) * k, nbr_d2 + (i - row_begin) * k);
+    return 0;
+}
+
+/* The same search for an explicit list of rows (rows[t] -> output row t). */
+int oracle_knn_rows(const float* x, int64_t n, int32_t m, int32_t k, const int64_t* rows, int64_t nrows,
+                    int32_t* nbr, double* nbr_d2)
+{
+    if (k < 1 || (int64_t)k > n - 1) return -1;
+    for (int64_t t = 0; t < nrows; ++t)
+        if (rows[t] < 0 || rows[t] >= n) return -1;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t t = 0; t < nrows; ++t)
+        knn_row(x, n, m, k, rows[t], nbr + t * k, nbr_d2 + t * k);
+    return 0;
+}
+
+static void knn_row(const float* x, int64_t n, int32_t m, int32_t k, int64_t i, int32_t* bj, double* bd)
+{
+    {
         int32_t cnt = 0;
         const float* xi = x + i * m;
         for (int64_t j = 0; j < n; ++j) {
@@ -68,5 +88,4 @@ int oracle_knn(const float* x, int64_t n, int32_t m, int32_t k, int64_t row_begi
             bj[pos] = (int32_t)j;
         }
     }
-    return 0;
 }

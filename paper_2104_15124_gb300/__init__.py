@@ -1,0 +1,377 @@
+"""Python binding of libvb (the C ABI in include/vb.h): argument marshalling only.
+
+Every step of the variable-bandwidth kernel build runs in the CUDA kernels of
+libvb.so; this module allocates the caller-side device buffers with PyTorch,
+passes their pointers and the current CUDA stream, and turns status codes into
+exceptions.  There is no CPU fallback: without the compiled library every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libvb.so")
+
+VB_PREC_FP32 = 0
+VB_PRUNE_NONE, VB_PRUNE_EXACT = 0, 1
+VB_SPMV_PLAIN, VB_SPMV_LAPLACIAN = 0, 1
+XI_LO, XI_HI, DXI = -10.0, 4.0, 0.25
+
+_STATUS = {0: "VB_OK", -1: "VB_ERR_ARG", -2: "VB_ERR_CUDA", -3: "VB_ERR_WORKSPACE", -4: "VB_ERR_DEGENERATE",
+           -5: "VB_ERR_EPS_BOUNDARY", -6: "VB_ERR_NOT_CONVERGED", -7: "VB_ERR_TIMEOUT", -8: "VB_ERR_BOUNDS",
+           -9: "VB_ERR_UNSUPPORTED"}
+
+
+class VbError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {_STATUS.get(code, code)}")
+
+
+# ----------------------------------------------------------------------------- ctypes mirrors of vb.h
+c_p = ctypes.c_void_p
+c_i32, c_i64, c_f32, c_f64, c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double, ctypes.c_size_t
+
+
+class KnnParams(ctypes.Structure):
+    _fields_ = [("k", c_i32), ("margin", c_i32), ("precision", c_i32), ("prune", c_i32)]
+
+
+class GraphC(ctypes.Structure):
+    _fields_ = [("n", c_i64), ("row_ptr", c_p), ("col", c_p), ("ed2", c_p)]
+
+
+class OpParams(ctypes.Structure):
+    _fields_ = [("c", c_f64), ("beta", c_f64), ("d", c_f64)]
+
+
+class BuildParams(ctypes.Structure):
+    _fields_ = [("knn", KnnParams), ("k_bw", c_i32), ("op", OpParams), ("xi_lo", c_f64), ("xi_hi", c_f64),
+                ("dxi", c_f64), ("pin_eps", c_i32)]
+
+
+class BuildOut(ctypes.Structure):
+    _fields_ = [(f, c_p) for f in ("nbr", "nbr_d2", "b", "row_ptr", "col", "ed2")] + [("cap", c_i64)] + \
+               [(f, c_p) for f in ("nnz", "eps2_den", "chi_den", "dim_den", "psi", "P", "xi_c", "eps2_op", "chi_op",
+                                   "dim_op", "val", "q", "D", "S")]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("error", c_i32), ("warnings", c_i32), ("knn_fallback_rows", c_i64), ("knn_candidates", c_i64),
+                ("union_big_rows", c_i64), ("reserved", c_i64 * 4)]
+
+
+_SIGS = {
+    "vb_status_string": (ctypes.c_char_p, [c_i32]),
+    "vb_create": (c_i32, [ctypes.POINTER(c_p), c_i32, c_p]),
+    "vb_destroy": (c_i32, [c_p]),
+    "vb_set_stream": (c_i32, [c_p, c_p]),
+    "vb_report_read": (c_i32, [c_p, ctypes.POINTER(Report)]),
+    "vb_report_reset": (c_i32, [c_p]),
+    "vb_profile_enable": (c_i32, [c_p, c_i32]),
+    "vb_profile_read": (c_i32, [c_p, ctypes.POINTER(c_f32), ctypes.POINTER(c_i64)]),
+    "vb_knn_workspace": (c_sz, [c_i64, c_i32, ctypes.POINTER(KnnParams)]),
+    "vb_knn": (c_i32, [c_p, c_p, c_i64, c_i32, ctypes.POINTER(KnnParams), c_p, c_p, c_p, c_sz]),
+    "vb_graph_workspace": (c_sz, [c_i64, c_i32]),
+    "vb_graph_build": (c_i32, [c_p, c_i64, c_i32, c_p, c_p, c_p, c_p, c_p, c_i64, c_p, c_p, c_sz]),
+    "vb_bandwidth": (c_i32, [c_p, c_i64, c_i32, c_i32, c_p, c_p]),
+    "vb_epsilon_tune_workspace": (c_sz, [c_i64]),
+    "vb_epsilon_tune": (c_i32, [c_p, ctypes.POINTER(GraphC), c_p, c_f64, c_p, c_f64, c_f64, c_f64, c_i32, c_p, c_p,
+                                c_p, c_p, c_sz]),
+    "vb_density_workspace": (c_sz, [c_i64]),
+    "vb_density": (c_i32, [c_p, ctypes.POINTER(GraphC), c_p, c_p, c_f64, c_f64, c_p, c_p, c_p, c_sz]),
+    "vb_operator_centre_workspace": (c_sz, [c_i64]),
+    "vb_operator_centre": (c_i32, [c_p, ctypes.POINTER(GraphC), c_p, c_p, c_p, c_p, c_sz]),
+    "vb_kernel_csr_workspace": (c_sz, [c_i64]),
+    "vb_kernel_csr": (c_i32, [c_p, ctypes.POINTER(GraphC), c_p, c_p, ctypes.POINTER(OpParams), c_p, c_p, c_p, c_p,
+                              c_p, c_p, c_sz]),
+    "vb_spmv_workspace": (c_sz, [c_i64]),
+    "vb_spmv": (c_i32, [c_p, ctypes.POINTER(GraphC), c_p, c_p, c_i32, c_f32, c_p, c_f32, c_p, c_p, c_sz]),
+    "vb_build_workspace": (c_sz, [c_i64, c_i32, ctypes.POINTER(BuildParams)]),
+    "vb_build": (c_i32, [c_p, c_p, c_i64, c_i32, ctypes.POINTER(BuildParams), ctypes.POINTER(BuildOut), c_p, c_sz]),
+}
+EXPORTED = tuple(_SIGS)
+
+_lock = threading.Lock()
+_lib = None
+_ctxs: dict[int, int] = {}
+
+
+def lib():
+    """The loaded libvb.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libvb.so is not built ({LIB_PATH}); run paper_2104_15124_gb300.native.compile_library()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(code: int, where: str) -> None:
+    if code != 0:
+        raise VbError(code, where)
+
+
+def _ctx(device: torch.device) -> int:
+    idx = device.index if device.index is not None else torch.cuda.current_device()
+    with _lock:
+        h = _ctxs.get(idx)
+    if h is None:
+        out = c_p()
+        _check(lib().vb_create(ctypes.byref(out), idx, c_p(torch.cuda.current_stream(idx).cuda_stream)), "vb_create")
+        with _lock:
+            _ctxs[idx] = out.value
+        h = out.value
+    _check(lib().vb_set_stream(c_p(h), c_p(torch.cuda.current_stream(idx).cuda_stream)), "vb_set_stream")
+    return h
+
+
+def _p(t: torch.Tensor | None) -> c_p:
+    if t is None:
+        return c_p(0)
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return c_p(t.data_ptr())
+
+
+def _ws(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def report(device=None) -> dict:
+    """Synchronises the current stream and returns the device report."""
+    dev = torch.device("cuda", device if isinstance(device, int) else torch.cuda.current_device()) \
+        if not isinstance(device, torch.device) else device
+    r = Report()
+    _check(lib().vb_report_read(c_p(_ctx(dev)), ctypes.byref(r)), "vb_report_read")
+    return dict(error=r.error, warnings=r.warnings, knn_fallback_rows=r.knn_fallback_rows,
+                knn_candidates=r.knn_candidates, union_big_rows=r.union_big_rows)
+
+
+def report_reset(device=None) -> None:
+    dev = torch.device("cuda", device if isinstance(device, int) else torch.cuda.current_device()) \
+        if not isinstance(device, torch.device) else device
+    _check(lib().vb_report_reset(c_p(_ctx(dev))), "vb_report_reset")
+
+
+def raise_on_device_error(device=None) -> dict:
+    r = report(device)
+    if r["error"] != 0:
+        raise VbError(r["error"], "device report")
+    return r
+
+
+STAGES = ("knn_order", "knn_tile", "knn_fallback", "graph", "bandwidth", "sweep_density", "density", "centre",
+          "sweep_operator", "operator", "lhat")
+
+
+def profile_enable(on: bool = True, device=None) -> None:
+    """Bracket every stage with CUDA events on the stream and count launches (measurement hook)."""
+    dev = torch.device("cuda", device if isinstance(device, int) else torch.cuda.current_device()) \
+        if not isinstance(device, torch.device) else device
+    _check(lib().vb_profile_enable(c_p(_ctx(dev)), 1 if on else 0), "vb_profile_enable")
+
+
+def profile_read(device=None) -> tuple[dict, int]:
+    """(stage -> ms of its latest run, kernel launches enqueued since enabling); synchronises."""
+    dev = torch.device("cuda", device if isinstance(device, int) else torch.cuda.current_device()) \
+        if not isinstance(device, torch.device) else device
+    ms = (c_f32 * len(STAGES))()
+    n = c_i64()
+    _check(lib().vb_profile_read(c_p(_ctx(dev)), ms, ctypes.byref(n)), "vb_profile_read")
+    return {s: ms[i] for i, s in enumerate(STAGES) if ms[i] >= 0}, int(n.value)
+
+
+# ----------------------------------------------------------------------------- graph handle
+@dataclasses.dataclass
+class Graph:
+    """The symmetric CSR pattern: row_ptr [n+1] int64, col [cap] int32, ed2 [cap] fp32, nnz [1] int64 (device)."""
+    n: int
+    row_ptr: torch.Tensor
+    col: torch.Tensor
+    ed2: torch.Tensor
+    nnz_dev: torch.Tensor
+
+    def c(self) -> GraphC:
+        return GraphC(self.n, _p(self.row_ptr), _p(self.col), _p(self.ed2))
+
+    @property
+    def nnz(self) -> int:
+        return int(self.nnz_dev.item())
+
+
+# ----------------------------------------------------------------------------- the calls
+def knn(x: torch.Tensor, k: int, margin: int = 16, prune: bool = True):
+    """Exact kNN (vb_knn): returns (nbr int32 [n, k], nbr_d2 fp64 [n, k])."""
+    n, m = x.shape
+    dev = x.device
+    p = KnnParams(k, margin, VB_PREC_FP32, VB_PRUNE_EXACT if prune else VB_PRUNE_NONE)
+    nbr = torch.empty((n, k), dtype=torch.int32, device=dev)
+    d2 = torch.empty((n, k), dtype=torch.float64, device=dev)
+    ws = _ws(lib().vb_knn_workspace(n, m, ctypes.byref(p)), dev)
+    _check(lib().vb_knn(c_p(_ctx(dev)), _p(x), n, m, ctypes.byref(p), _p(nbr), _p(d2), _p(ws), ws.numel()), "vb_knn")
+    return nbr, d2
+
+
+def graph(nbr: torch.Tensor, nbr_d2: torch.Tensor) -> Graph:
+    """Symmetric pattern diag U kNN U kNN^T (vb_graph_build)."""
+    n, k = nbr.shape
+    dev = nbr.device
+    cap = n * (2 * k + 1)
+    g = Graph(n, torch.empty(n + 1, dtype=torch.int64, device=dev), torch.empty(cap, dtype=torch.int32, device=dev),
+              torch.empty(cap, dtype=torch.float32, device=dev), torch.empty(1, dtype=torch.int64, device=dev))
+    ws = _ws(lib().vb_graph_workspace(n, k), dev)
+    _check(lib().vb_graph_build(c_p(_ctx(dev)), n, k, _p(nbr), _p(nbr_d2), _p(g.row_ptr), _p(g.col), _p(g.ed2), cap,
+                                _p(g.nnz_dev), _p(ws), ws.numel()), "vb_graph_build")
+    return g
+
+
+def bandwidth(nbr_d2: torch.Tensor, k_bw: int | None = None) -> torch.Tensor:
+    n, k = nbr_d2.shape
+    b = torch.empty(n, dtype=torch.float64, device=nbr_d2.device)
+    _check(lib().vb_bandwidth(c_p(_ctx(nbr_d2.device)), n, k, k if k_bw is None else k_bw, _p(nbr_d2), _p(b)),
+           "vb_bandwidth")
+    return b
+
+
+def epsilon_tune(g: Graph, rho: torch.Tensor, scale: float, xi_c: torch.Tensor | None = None,
+                 grid=(XI_LO, XI_HI, DXI), warn_bit: int = 1):
+    """One fused sweep over the grid (vb_epsilon_tune): returns (eps2 [1], chi [G], dim_est [1]) on the device."""
+    dev = rho.device
+    G = int(round((grid[1] - grid[0]) / grid[2])) + 1
+    eps2 = torch.empty(1, dtype=torch.float64, device=dev)
+    chi = torch.empty(G, dtype=torch.float64, device=dev)
+    dim = torch.empty(1, dtype=torch.float64, device=dev)
+    ws = _ws(lib().vb_epsilon_tune_workspace(g.n), dev)
+    gc = g.c()
+    _check(lib().vb_epsilon_tune(c_p(_ctx(dev)), ctypes.byref(gc), _p(rho), scale, _p(xi_c), grid[0], grid[1],
+                                 grid[2], warn_bit, _p(eps2), _p(chi), _p(dim), _p(ws), ws.numel()), "vb_epsilon_tune")
+    return eps2, chi, dim
+
+
+def density(g: Graph, b: torch.Tensor, eps2: torch.Tensor, d: float, beta: float):
+    dev = b.device
+    psi = torch.empty(g.n, dtype=torch.float64, device=dev)
+    P = torch.empty(g.n, dtype=torch.float64, device=dev)
+    ws = _ws(lib().vb_density_workspace(g.n), dev)
+    gc = g.c()
+    _check(lib().vb_density(c_p(_ctx(dev)), ctypes.byref(gc), _p(b), _p(eps2), d, beta, _p(psi), _p(P), _p(ws),
+                            ws.numel()), "vb_density")
+    return psi, P
+
+
+def operator_centre(g: Graph, b: torch.Tensor, P: torch.Tensor) -> torch.Tensor:
+    dev = b.device
+    xi_c = torch.empty(1, dtype=torch.float64, device=dev)
+    ws = _ws(lib().vb_operator_centre_workspace(g.n), dev)
+    gc = g.c()
+    _check(lib().vb_operator_centre(c_p(_ctx(dev)), ctypes.byref(gc), _p(b), _p(P), _p(xi_c), _p(ws), ws.numel()),
+           "vb_operator_centre")
+    return xi_c
+
+
+def kernel_csr(g: Graph, psi: torch.Tensor, P: torch.Tensor, eps2_op: torch.Tensor, c: float, beta: float, d: float):
+    """K_{eps,beta}, normalisations and the CSR values of L-hat (vb_kernel_csr): returns (val, q, D, S)."""
+    dev = psi.device
+    val = torch.empty(g.col.numel(), dtype=torch.float32, device=dev)
+    q, D, S = (torch.empty(g.n, dtype=torch.float64, device=dev) for _ in range(3))
+    ws = _ws(lib().vb_kernel_csr_workspace(g.n), dev)
+    gc = g.c()
+    op = OpParams(c, beta, d)
+    _check(lib().vb_kernel_csr(c_p(_ctx(dev)), ctypes.byref(gc), _p(psi), _p(P), ctypes.byref(op), _p(eps2_op),
+                               _p(val), _p(q), _p(D), _p(S), _p(ws), ws.numel()), "vb_kernel_csr")
+    return val, q, D, S
+
+
+def spmv(g: Graph, val: torch.Tensor, x: torch.Tensor, S: torch.Tensor | None = None, laplacian: bool = False,
+         alpha: float = 1.0, beta: float = 0.0, y: torch.Tensor | None = None) -> torch.Tensor:
+    """y = alpha A x + beta y (vb_spmv); laplacian=True applies L-hat in difference form with S."""
+    dev = x.device
+    if y is None:
+        y = torch.zeros(g.n, dtype=torch.float32, device=dev)
+    ws = _ws(lib().vb_spmv_workspace(g.n), dev) if laplacian else None
+    gc = g.c()
+    _check(lib().vb_spmv(c_p(_ctx(dev)), ctypes.byref(gc), _p(val), _p(S), VB_SPMV_LAPLACIAN if laplacian else
+                         VB_SPMV_PLAIN, alpha, _p(x), beta, _p(y), _p(ws), 0 if ws is None else ws.numel()), "vb_spmv")
+    return y
+
+
+@dataclasses.dataclass
+class Build:
+    nbr: torch.Tensor
+    nbr_d2: torch.Tensor
+    b: torch.Tensor
+    graph: Graph
+    eps2_den: torch.Tensor
+    chi_den: torch.Tensor
+    dim_den: torch.Tensor
+    psi: torch.Tensor
+    P: torch.Tensor
+    xi_c: torch.Tensor
+    eps2_op: torch.Tensor
+    chi_op: torch.Tensor
+    dim_op: torch.Tensor
+    val: torch.Tensor
+    q: torch.Tensor
+    D: torch.Tensor
+    S: torch.Tensor
+
+
+class Builder:
+    """Holds the output and workspace buffers of vb_build for one problem size, so
+    repeated builds (and timing loops) allocate nothing."""
+
+    def __init__(self, n: int, m: int, k: int, d: float, c: float, beta: float = -0.25, margin: int = 16,
+                 k_bw: int | None = None, prune: bool = True, device=None, grid=(XI_LO, XI_HI, DXI)):
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.n, self.m, self.k, self.device = n, m, k, dev
+        G = int(round((grid[1] - grid[0]) / grid[2])) + 1
+        self.params = BuildParams(KnnParams(k, margin, VB_PREC_FP32, VB_PRUNE_EXACT if prune else VB_PRUNE_NONE),
+                                  0 if k_bw is None else k_bw, OpParams(c, beta, d), grid[0], grid[1], grid[2], 0)
+        cap = n * (2 * k + 1)
+        f64 = lambda s: torch.empty(s, dtype=torch.float64, device=dev)
+        g = Graph(n, torch.empty(n + 1, dtype=torch.int64, device=dev), torch.empty(cap, dtype=torch.int32, device=dev),
+                  torch.empty(cap, dtype=torch.float32, device=dev), torch.empty(1, dtype=torch.int64, device=dev))
+        self.out = Build(nbr=torch.empty((n, k), dtype=torch.int32, device=dev), nbr_d2=f64((n, k)), b=f64(n), graph=g,
+                         eps2_den=f64(1), chi_den=f64(G), dim_den=f64(1), psi=f64(n), P=f64(n), xi_c=f64(1),
+                         eps2_op=f64(1), chi_op=f64(G), dim_op=f64(1),
+                         val=torch.empty(cap, dtype=torch.float32, device=dev), q=f64(n), D=f64(n), S=f64(n))
+        o = self.out
+        self.cout = BuildOut(_p(o.nbr), _p(o.nbr_d2), _p(o.b), _p(g.row_ptr), _p(g.col), _p(g.ed2), cap, _p(g.nnz_dev),
+                             _p(o.eps2_den), _p(o.chi_den), _p(o.dim_den), _p(o.psi), _p(o.P), _p(o.xi_c),
+                             _p(o.eps2_op), _p(o.chi_op), _p(o.dim_op), _p(o.val), _p(o.q), _p(o.D), _p(o.S))
+        self.ws = _ws(lib().vb_build_workspace(n, m, ctypes.byref(self.params)), dev)
+
+    def __call__(self, x: torch.Tensor, eps2_den: float | None = None, eps2_op: float | None = None) -> Build:
+        if x.shape != (self.n, self.m) or x.dtype != torch.float32:
+            raise ValueError("x must be float32 [n, m] matching the builder")
+        pin = eps2_den is not None or eps2_op is not None
+        if pin:
+            if eps2_den is None or eps2_op is None:
+                raise ValueError("pin both eps2_den and eps2_op")
+            self.out.eps2_den.fill_(eps2_den)
+            self.out.eps2_op.fill_(eps2_op)
+        self.params.pin_eps = 1 if pin else 0
+        _check(lib().vb_build(c_p(_ctx(self.device)), _p(x), self.n, self.m, ctypes.byref(self.params),
+                              ctypes.byref(self.cout), _p(self.ws), self.ws.numel()), "vb_build")
+        return self.out
+
+
+def build(x: torch.Tensor, k: int, d: float, c: float, beta: float = -0.25, margin: int = 16,
+          k_bw: int | None = None, prune: bool = True, eps2_den: float | None = None,
+          eps2_op: float | None = None) -> Build:
+    """The whole build, kNN to L-hat (vb_build), on x's device and current stream."""
+    n, m = x.shape
+    return Builder(n, m, k, d, c, beta, margin, k_bw, prune, x.device)(x, eps2_den, eps2_op)

@@ -1,0 +1,299 @@
+// The extern "C" boundary of libvb (declared in include/vb.h): argument checks,
+// device selection, workspace sizing and the ordering of the launches.
+#include "vb_internal.cuh"
+
+#include <algorithm>
+#include <new>
+
+using namespace vb;
+
+namespace {
+
+// Makes the context's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+Ctx* C(vb_ctx* c) { return reinterpret_cast<Ctx*>(c); }
+
+size_t build_ws(int64_t n, int32_t m, const vb_build_params* p)
+{
+    Carve c(nullptr);
+    size_t knn = knn_plan(c, n, m, &p->knn, nullptr);
+    size_t s = std::max({knn, graph_plan_bytes(n, p->knn.k), sweep_ws_bytes(n), density_ws_bytes(n),
+                         centre_ws_bytes(n), kernel_csr_ws_bytes(n)});
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* vb_status_string(vb_status s)
+{
+    switch (s) {
+        case VB_OK: return "ok";
+        case VB_ERR_ARG: return "invalid argument";
+        case VB_ERR_CUDA: return "CUDA error";
+        case VB_ERR_WORKSPACE: return "workspace too small";
+        case VB_ERR_DEGENERATE: return "degenerate input (zero bandwidth or non-finite coordinate)";
+        case VB_ERR_EPS_BOUNDARY: return "epsilon at the end of its grid";
+        case VB_ERR_NOT_CONVERGED: return "eigen-solver did not converge";
+        case VB_ERR_TIMEOUT: return "device-side wait timed out";
+        case VB_ERR_BOUNDS: return "index out of bounds";
+        case VB_ERR_UNSUPPORTED: return "unsupported request";
+        default: return "unknown status";
+    }
+}
+
+vb_status vb_create(vb_ctx** out, int32_t device, void* stream)
+{
+    if (!out) return VB_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return VB_ERR_ARG;
+    DeviceGuard g(device);
+    if (!g.ok) return VB_ERR_CUDA;
+    Ctx* c = new (std::nothrow) Ctx();
+    if (!c) return VB_ERR_CUDA;
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    if (cudaMalloc(&c->rep, sizeof(DevReport)) != cudaSuccess) { delete c; return VB_ERR_CUDA; }
+    if (cudaMallocHost(&c->host_rep, sizeof(vb_report)) != cudaSuccess) {
+        cudaFree(c->rep);
+        delete c;
+        return VB_ERR_CUDA;
+    }
+    if (cudaMemsetAsync(c->rep, 0, sizeof(DevReport), c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaFree(c->rep);
+        cudaFreeHost(c->host_rep);
+        delete c;
+        return VB_ERR_CUDA;
+    }
+    *out = reinterpret_cast<vb_ctx*>(c);
+    return VB_OK;
+}
+
+vb_status vb_destroy(vb_ctx* ctx)
+{
+    if (!ctx) return VB_ERR_ARG;
+    Ctx* c = C(ctx);
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto& e : c->ev)
+        if (e) cudaEventDestroy(e);
+    cudaFree(c->rep);
+    cudaFreeHost(c->host_rep);
+    delete c;
+    return VB_OK;
+}
+
+vb_status vb_set_stream(vb_ctx* ctx, void* stream)
+{
+    if (!ctx) return VB_ERR_ARG;
+    C(ctx)->stream = (cudaStream_t)stream;
+    return VB_OK;
+}
+
+vb_status vb_report_read(vb_ctx* ctx, vb_report* out)
+{
+    if (!ctx || !out) return VB_ERR_ARG;
+    Ctx* c = C(ctx);
+    DeviceGuard g(c->device);
+    if (cudaMemcpyAsync(c->host_rep, c->rep, sizeof(vb_report), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return VB_ERR_CUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return VB_ERR_CUDA;
+    *out = *c->host_rep;
+    return VB_OK;
+}
+
+vb_status vb_report_reset(vb_ctx* ctx)
+{
+    if (!ctx) return VB_ERR_ARG;
+    Ctx* c = C(ctx);
+    DeviceGuard g(c->device);
+    return cuda_status(cudaMemsetAsync(c->rep, 0, sizeof(DevReport), c->stream));
+}
+
+vb_status vb_profile_enable(vb_ctx* ctx, int32_t on)
+{
+    if (!ctx) return VB_ERR_ARG;
+    Ctx* c = C(ctx);
+    DeviceGuard g(c->device);
+    if (on && !c->ev[0]) {
+        for (auto& e : c->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return VB_ERR_CUDA;
+    }
+    c->prof = on != 0;
+    c->recorded = 0;
+    c->launches = 0;
+    return VB_OK;
+}
+
+vb_status vb_profile_read(vb_ctx* ctx, float* ms, int64_t* launches)
+{
+    if (!ctx) return VB_ERR_ARG;
+    Ctx* c = C(ctx);
+    DeviceGuard g(c->device);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return VB_ERR_CUDA;
+    if (ms) {
+        for (int s = 0; s < VB_NUM_STAGES; ++s) {
+            ms[s] = -1.f;
+            if (c->ev[0] && (c->recorded >> s & 1u)) {
+                float t = 0.f;
+                if (cudaEventElapsedTime(&t, c->ev[2 * s], c->ev[2 * s + 1]) == cudaSuccess) ms[s] = t;
+            }
+        }
+        c->recorded = 0;
+    }
+    if (launches) *launches = c->launches;
+    return VB_OK;
+}
+
+size_t vb_knn_workspace(int64_t n, int32_t m, const vb_knn_params* p)
+{
+    Carve c(nullptr);
+    return knn_plan(c, n, m, p, nullptr);
+}
+
+vb_status vb_knn(vb_ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_params* p, int32_t* nbr,
+                 double* nbr_d2, void* ws, size_t ws_bytes)
+{
+    if (!ctx) return VB_ERR_ARG;
+    DeviceGuard g(C(ctx)->device);
+    if (!g.ok) return VB_ERR_CUDA;
+    return knn_run(C(ctx), x, n, m, p, nbr, nbr_d2, ws, ws_bytes);
+}
+
+size_t vb_graph_workspace(int64_t n, int32_t k) { return graph_plan_bytes(n, k); }
+
+vb_status vb_graph_build(vb_ctx* ctx, int64_t n, int32_t k, const int32_t* nbr, const double* nbr_d2,
+                         int64_t* row_ptr, int32_t* col, float* ed2, int64_t cap, int64_t* nnz_dev, void* ws,
+                         size_t ws_bytes)
+{
+    if (!ctx) return VB_ERR_ARG;
+    DeviceGuard g(C(ctx)->device);
+    if (!g.ok) return VB_ERR_CUDA;
+    return graph_run(C(ctx), n, k, nbr, nbr_d2, row_ptr, col, ed2, cap, nnz_dev, ws, ws_bytes);
+}
+
+vb_status vb_bandwidth(vb_ctx* ctx, int64_t n, int32_t k, int32_t k_bw, const double* nbr_d2, double* b)
+{
+    if (!ctx) return VB_ERR_ARG;
+    DeviceGuard g(C(ctx)->device);
+    if (!g.ok) return VB_ERR_CUDA;
+    return bandwidth_run(C(ctx), n, k, k_bw, nbr_d2, b);
+}
+
+size_t vb_epsilon_tune_workspace(int64_t n) { return sweep_ws_bytes(n); }
+
+vb_status vb_epsilon_tune(vb_ctx* ctx, const vb_graph* gr, const double* rho, double scale, const double* xi_c_dev,
+                          double xi_lo, double xi_hi, double dxi, int32_t warn_bit, double* eps2_dev, double* chi_dev,
+                          double* dim_est_dev, void* ws, size_t ws_bytes)
+{
+    if (!ctx) return VB_ERR_ARG;
+    DeviceGuard g(C(ctx)->device);
+    if (!g.ok) return VB_ERR_CUDA;
+    return sweep_run(C(ctx), gr, rho, scale, xi_c_dev, xi_lo, xi_hi, dxi, warn_bit, eps2_dev, chi_dev, dim_est_dev, ws,
+                     ws_bytes);
+}
+
+size_t vb_density_workspace(int64_t n) { return density_ws_bytes(n); }
+
+vb_status vb_density(vb_ctx* ctx, const vb_graph* gr, const double* b, const double* eps2_dev, double d, double beta,
+                     double* psi, double* P, void* ws, size_t ws_bytes)
+{
+    if (!ctx) return VB_ERR_ARG;
+    DeviceGuard g(C(ctx)->device);
+    if (!g.ok) return VB_ERR_CUDA;
+    return density_run(C(ctx), gr, b, eps2_dev, d, beta, psi, P, ws, ws_bytes);
+}
+
+size_t vb_operator_centre_workspace(int64_t n) { return centre_ws_bytes(n); }
+
+vb_status vb_operator_centre(vb_ctx* ctx, const vb_graph* gr, const double* b, const double* P, double* xi_c_dev,
+                             void* ws, size_t ws_bytes)
+{
+    if (!ctx) return VB_ERR_ARG;
+    DeviceGuard g(C(ctx)->device);
+    if (!g.ok) return VB_ERR_CUDA;
+    return centre_run(C(ctx), gr, b, P, xi_c_dev, ws, ws_bytes);
+}
+
+size_t vb_kernel_csr_workspace(int64_t n) { return kernel_csr_ws_bytes(n); }
+
+vb_status vb_kernel_csr(vb_ctx* ctx, const vb_graph* gr, const double* psi, const double* P, const vb_op_params* op,
+                        const double* eps2_op_dev, float* val, double* q, double* D, double* S, void* ws,
+                        size_t ws_bytes)
+{
+    if (!ctx) return VB_ERR_ARG;
+    DeviceGuard g(C(ctx)->device);
+    if (!g.ok) return VB_ERR_CUDA;
+    return kernel_csr_run(C(ctx), gr, psi, P, op, eps2_op_dev, val, q, D, S, ws, ws_bytes);
+}
+
+size_t vb_spmv_workspace(int64_t n) { return spmv_ws_bytes(n); }
+
+vb_status vb_spmv(vb_ctx* ctx, const vb_graph* gr, const float* val, const double* S, int32_t mode, float alpha,
+                  const float* x, float beta, float* y, void* ws, size_t ws_bytes)
+{
+    if (!ctx) return VB_ERR_ARG;
+    DeviceGuard g(C(ctx)->device);
+    if (!g.ok) return VB_ERR_CUDA;
+    return spmv_run(C(ctx), gr, val, S, mode, alpha, x, beta, y, ws, ws_bytes);
+}
+
+size_t vb_build_workspace(int64_t n, int32_t m, const vb_build_params* p)
+{
+    if (!p) return 0;
+    return build_ws(n, m, p);
+}
+
+vb_status vb_build(vb_ctx* ctx, const float* x, int64_t n, int32_t m, const vb_build_params* p,
+                   const vb_build_out* o, void* ws, size_t ws_bytes)
+{
+    if (!ctx || !p || !o) return VB_ERR_ARG;
+    Ctx* c = C(ctx);
+    DeviceGuard g(c->device);
+    if (!g.ok) return VB_ERR_CUDA;
+    const int32_t k = p->knn.k;
+    const int32_t k_bw = p->k_bw > 0 ? p->k_bw : k;
+    if (k_bw > k) return VB_ERR_ARG;
+    if (!ws || ws_bytes < build_ws(n, m, p)) return VB_ERR_WORKSPACE;
+    vb_status st = knn_run(c, x, n, m, &p->knn, o->nbr, o->nbr_d2, ws, ws_bytes);
+    if (st) return st;
+    st = graph_run(c, n, k, o->nbr, o->nbr_d2, o->row_ptr, o->col, o->ed2, o->cap, o->nnz, ws, ws_bytes);
+    if (st) return st;
+    st = bandwidth_run(c, n, k, k_bw, o->nbr_d2, o->b);
+    if (st) return st;
+    vb_graph gr{n, o->row_ptr, o->col, o->ed2};
+    if (!p->pin_eps) {
+        st = sweep_run(c, &gr, o->b, 1.0, nullptr, p->xi_lo, p->xi_hi, p->dxi, 1, o->eps2_den, o->chi_den, o->dim_den,
+                       ws, ws_bytes);
+        if (st) return st;
+    }
+    st = density_run(c, &gr, o->b, o->eps2_den, p->op.d, p->op.beta, o->psi, o->P, ws, ws_bytes);
+    if (st) return st;
+    st = centre_run(c, &gr, o->b, o->P, o->xi_c, ws, ws_bytes);
+    if (st) return st;
+    if (!p->pin_eps) {
+        st = sweep_run(c, &gr, o->P, 4.0, o->xi_c, p->xi_lo, p->xi_hi, p->dxi, 2, o->eps2_op, o->chi_op, o->dim_op, ws,
+                       ws_bytes);
+        if (st) return st;
+    }
+    return kernel_csr_run(c, &gr, o->psi, o->P, &p->op, o->eps2_op, o->val, o->q, o->D, o->S, ws, ws_bytes);
+}
+
+}  // extern "C"

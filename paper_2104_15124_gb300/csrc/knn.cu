@@ -1,0 +1,693 @@
+// Exact k-nearest-neighbour search on the GPU (steps a1-a5 of the build).
+//
+// Definition (Sec. 2.1, the index map I(x, r) of the bandwidth function): the k
+// nearest other samples of every point, ordered by the canonical FP64 squared
+// distance and then by index.  The search itself runs in FP32 and is made
+// exact by an FP64 certificate:
+//   a1  Morton order: bounding box, 32-bit Morton keys of the first min(m,4)
+//       coordinates (first 3 when m > 4), stable LSD radix sort, gather of the
+//       coordinates into 64-point tiles (zero-padded to MP = 4, 8, ..., 128).
+//   a2  pruning: every tile carries its bounding box; a candidate tile is
+//       skipped when the box-to-box (and, per query, point-to-box) distance,
+//       rounded down by a proven FP32 error factor, exceeds the running
+//       (k+margin)-th smallest FP32 distance of the query tile.
+//   a3  distances: FP32 difference form sum_r (q_r - c_r)^2 on the ALUs.
+//   a4  selection: per query a max-heap of the k + margin smallest keys
+//       (FP32 distance bits << 32 | sorted position) in shared memory.
+//   a5  rescoring: FP64 canonical distances of the kept candidates, ranked by
+//       (d2, index); the row is certified when the k-th FP64 distance lies
+//       below the smallest FP64 distance any excluded candidate can have,
+//       H (1 - 2 gamma), H = the largest kept FP32 distance and
+//       gamma = (m + 2) 2^-24 the relative error bound of the FP32 sum.
+//       Uncertified rows (ties, duplicates) are recomputed by an exact FP64
+//       radix selection over all points.
+#include "vb_internal.cuh"
+
+#include <algorithm>
+
+namespace vb {
+
+constexpr int TILE = 64;            // points per query tile and per candidate tile
+constexpr int RADIX_T = 256;        // threads of the radix kernels
+constexpr int RADIX_ITEMS = 1024;   // keys per radix block (4 rounds of 256)
+constexpr int FB_THREADS = 256;
+
+struct KnnWs {
+    int* bbox;            // 8 ordered ints: min[4], max[4]
+    uint32_t* key[2];
+    uint32_t* val[2];     // val[0] after the sort = perm (sorted position -> original index)
+    uint32_t* hist;       // 256 * nblk
+    float* xs;            // npad * MP sorted coordinates
+    float* tlo;           // ntiles * MP
+    float* thi;
+    int* fb_list;         // n
+    int* fb_count;        // 1
+};
+
+static int pad_dim(int m)
+{
+    int mp = 4;
+    while (mp < m) mp *= 2;
+    return mp;
+}
+static int morton_dims(int m) { return m <= 4 ? m : 3; }
+static int morton_bits(int md) { return md == 1 ? 30 : md == 2 ? 15 : md == 3 ? 10 : 8; }
+
+size_t knn_plan(Carve& c, int64_t n, int32_t m, const vb_knn_params*, KnnWs* w)
+{
+    const int mp = pad_dim(m);
+    const int64_t ntiles = (n + TILE - 1) / TILE;
+    const int64_t npad = ntiles * TILE;
+    const int64_t nblk = (n + RADIX_ITEMS - 1) / RADIX_ITEMS;
+    KnnWs t;
+    t.bbox = c.take<int>(8);
+    t.key[0] = c.take<uint32_t>(n);
+    t.key[1] = c.take<uint32_t>(n);
+    t.val[0] = c.take<uint32_t>(n);
+    t.val[1] = c.take<uint32_t>(n);
+    t.hist = c.take<uint32_t>(256 * nblk);
+    t.xs = c.take<float>(npad * mp);
+    t.tlo = c.take<float>(ntiles * mp);
+    t.thi = c.take<float>(ntiles * mp);
+    t.fb_list = c.take<int>(n);
+    t.fb_count = c.take<int>(1);
+    if (w) *w = t;
+    return c.off;
+}
+
+// ------------------------------------------------------------------ a1: order
+__device__ __forceinline__ int f2ord(float f)
+{
+    int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ord2f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+__global__ void bbox_init_kernel(int* bbox, int* fb_count)
+{
+    int t = threadIdx.x;
+    if (t < 4) bbox[t] = 0x7fffffff;
+    else if (t < 8) bbox[t] = (int)0x80000000;
+    if (t == 0) *fb_count = 0;
+}
+
+// Bounding box of the Morton coordinates; also rejects non-finite input.
+__global__ void bbox_kernel(const float* __restrict__ x, int64_t n, int m, int md, int* bbox, DevReport* rep)
+{
+    int lo[4], hi[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) { lo[r] = 0x7fffffff; hi[r] = (int)0x80000000; }
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int r = 0; r < m; ++r) {
+            float v = x[i * m + r];
+            if (!isfinite(v)) bad = true;
+            if (r < md) {
+                int o = f2ord(v);
+                lo[r] = min(lo[r], o);
+                hi[r] = max(hi[r], o);
+            }
+        }
+    }
+    if (bad) report_error(rep, VB_ERR_DEGENERATE);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        int a = __reduce_min_sync(0xffffffffu, lo[r]);
+        int b = __reduce_max_sync(0xffffffffu, hi[r]);
+        if ((threadIdx.x & 31) == 0 && r < md) {
+            atomicMin(&bbox[r], a);
+            atomicMax(&bbox[4 + r], b);
+        }
+    }
+}
+
+__global__ void morton_kernel(const float* __restrict__ x, int64_t n, int m, int md, int bits,
+                              const int* __restrict__ bbox, uint32_t* key, uint32_t* val)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float qmax = (float)((1u << bits) - 1u);
+    uint32_t q[4] = {0, 0, 0, 0};
+    for (int r = 0; r < md; ++r) {
+        float lo = ord2f(bbox[r]), hi = ord2f(bbox[4 + r]);
+        float ext = hi - lo;
+        float s = ext > 0.f ? qmax / ext : 0.f;
+        float v = fminf(fmaxf((x[i * m + r] - lo) * s, 0.f), qmax);
+        q[r] = min((uint32_t)v, (1u << bits) - 1u);
+    }
+    uint32_t k = 0;
+    for (int b = bits - 1; b >= 0; --b)
+        for (int r = 0; r < md; ++r) k = (k << 1) | ((q[r] >> b) & 1u);
+    key[i] = k;
+    val[i] = (uint32_t)i;
+}
+
+__global__ void radix_hist_kernel(const uint32_t* __restrict__ key, int64_t n, int shift, uint32_t* hist, int nblk)
+{
+    __shared__ uint32_t cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * RADIX_ITEMS;
+    for (int r = 0; r < RADIX_ITEMS / RADIX_T; ++r) {
+        int64_t e = base + r * RADIX_T + threadIdx.x;
+        if (e < n) atomicAdd(&cnt[(key[e] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// In-place exclusive scan of len uint32 values by one block of 1024 threads.
+__global__ void scan_u32_single_kernel(uint32_t* a, int64_t len)
+{
+    __shared__ uint32_t part[1024];
+    const int t = threadIdx.x;
+    int64_t chunk = (len + 1023) / 1024;
+    int64_t b = t * chunk, e = min(len, b + chunk);
+    uint32_t s = 0;
+    for (int64_t i = b; i < e; ++i) s += a[i];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        uint32_t v = t >= o ? part[t - o] : 0u;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[t] - s;
+    for (int64_t i = b; i < e; ++i) {
+        uint32_t v = a[i];
+        a[i] = run;
+        run += v;
+    }
+}
+
+// Stable scatter: inside a block, rounds of 256 consecutive keys; inside a
+// round the order is (warp, lane), ranked with __match_any_sync.
+__global__ void radix_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                     uint32_t* kout, uint32_t* vout, int64_t n, int shift,
+                                     const uint32_t* __restrict__ hist, int nblk)
+{
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t wcnt[RADIX_T / 32][256];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    base[t] = hist[(int64_t)t * nblk + blockIdx.x];
+    int64_t b0 = (int64_t)blockIdx.x * RADIX_ITEMS;
+    for (int r = 0; r < RADIX_ITEMS / RADIX_T; ++r) {
+        for (int i = t; i < (RADIX_T / 32) * 256; i += RADIX_T) (&wcnt[0][0])[i] = 0;
+        __syncthreads();
+        int64_t e = b0 + r * RADIX_T + t;
+        bool ok = e < n;
+        uint32_t k = ok ? kin[e] : 0u, v = ok ? vin[e] : 0u;
+        uint32_t dg = (k >> shift) & 255u;
+        unsigned act = __ballot_sync(0xffffffffu, ok);
+        unsigned peers = 0;
+        if (ok) {
+            peers = __match_any_sync(act, dg);
+            int leader = __ffs(peers) - 1;
+            if (lane == leader) wcnt[w][dg] = __popc(peers);
+        }
+        __syncthreads();
+        if (ok) {
+            uint32_t off = base[dg] + __popc(peers & ((1u << lane) - 1u));
+            for (int ww = 0; ww < w; ++ww) off += wcnt[ww][dg];
+            kout[off] = k;
+            vout[off] = v;
+        }
+        __syncthreads();
+        uint32_t add = 0;
+        for (int ww = 0; ww < RADIX_T / 32; ++ww) add += wcnt[ww][t];
+        base[t] += add;
+        __syncthreads();
+    }
+}
+
+__global__ void gather_kernel(const float* __restrict__ x, const uint32_t* __restrict__ perm, int64_t n,
+                              int64_t npad, int m, int mp, float* xs)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= npad * mp) return;
+    int64_t p = i / mp;
+    int r = (int)(i - p * mp);
+    xs[i] = (p < n && r < m) ? x[(int64_t)perm[p] * m + r] : 0.f;
+}
+
+// One warp per tile: bounding box of its valid points (padding dims stay 0).
+__global__ void tile_box_kernel(const float* __restrict__ xs, int64_t n, int64_t ntiles, int m, int mp,
+                                float* tlo, float* thi)
+{
+    int64_t tile = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (tile >= ntiles) return;
+    int64_t p0 = tile * TILE + lane, p1 = p0 + 32;
+    for (int r = 0; r < mp; ++r) {
+        float lo = INFINITY, hi = -INFINITY;
+        if (p0 < n) { float v = xs[p0 * mp + r]; lo = fminf(lo, v); hi = fmaxf(hi, v); }
+        if (p1 < n) { float v = xs[p1 * mp + r]; lo = fminf(lo, v); hi = fmaxf(hi, v); }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) {
+            tlo[tile * mp + r] = r < m ? lo : 0.f;
+            thi[tile * mp + r] = r < m ? hi : 0.f;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ a2-a5: the tiled search
+__device__ __forceinline__ double canon_d2(const float* a, const float* b, int m)
+{
+    double acc = 0.0;
+    for (int r = 0; r < m; ++r) {
+        double dl = __dsub_rn((double)a[r], (double)b[r]);
+        double s = __dmul_rn(dl, dl);
+        acc = r == 0 ? s : __dadd_rn(acc, s);
+    }
+    return acc;
+}
+
+struct TileArgs {
+    const float* xs;
+    const float* tlo;
+    const float* thi;
+    const uint32_t* perm;
+    int64_t n;
+    int64_t ntiles;
+    int m, k, L, prune;
+    float lb_factor;     // 1 - 4 (m + 2) 2^-24, applied rounding down
+    double cert_factor;  // 1 - 2 (m + 2) 2^-24
+    int32_t* nbr;
+    double* nbr_d2;
+    int* fb_list;
+    int* fb_count;
+    DevReport* rep;
+};
+
+template <int MP>
+__device__ __forceinline__ float box_gap2(const float* q, const float* lo, const float* hi)
+{
+    float acc = 0.f;
+#pragma unroll
+    for (int r = 0; r < MP; ++r) {
+        float g = fmaxf(fmaxf(lo[r] - q[r], q[r] - hi[r]), 0.f);
+        acc = fmaf(g, g, acc);
+    }
+    return acc;
+}
+
+// Query tile per CTA (64 threads, one query each).  Shared memory:
+//   heap  [L][64] uint64   max-heaps, one column per query
+//   cand  [64][MP] float   staged candidate tile
+//   qs    [MP][64] float   query coordinates (only when MP > 16)
+//   sd/so [2][L]           per-warp rescoring scratch
+template <int MP>
+__global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int L = a.L;
+    uint64_t* heap = (uint64_t*)smem;
+    float* cand = (float*)(heap + (size_t)L * TILE);
+    float* qs = cand + TILE * MP;
+    uint64_t* sd = (uint64_t*)(qs + (MP > 16 ? TILE * MP : 0));
+    uint32_t* so = (uint32_t*)(sd + 2 * L);
+    __shared__ float sqlo[MP], sqhi[MP];
+    __shared__ int slist[TILE];
+    __shared__ float slb[TILE];
+    __shared__ uint32_t sthr[2];
+
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t qt = blockIdx.x;
+    const int64_t p = qt * TILE + t;
+    const bool valid = p < a.n;
+    constexpr bool QREG = MP <= 16;
+
+    float qr[QREG ? MP : 1];
+    if constexpr (QREG) {
+#pragma unroll
+        for (int r = 0; r < MP; ++r) qr[r] = a.xs[p * MP + r];
+    } else {
+        for (int r = 0; r < MP; ++r) qs[r * TILE + t] = a.xs[p * MP + r];
+    }
+    for (int s = 0; s < L; ++s) heap[s * TILE + t] = ~0ull;
+    for (int r = t; r < MP; r += TILE) {
+        sqlo[r] = a.tlo[qt * MP + r];
+        sqhi[r] = a.thi[qt * MP + r];
+    }
+    uint64_t maxkey = ~0ull;
+    uint32_t thr_blk = 0xffffffffu;   // float bits of the tile's running threshold (+inf as 0xffffffff)
+    unsigned long long evaluated = 0;
+    __syncthreads();
+
+    const int64_t nt = a.ntiles;
+    for (int64_t o0 = 0; o0 < 2 * nt; o0 += TILE) {
+        // tile order: own tile, then +1, -1, +2, -2, ...
+        int64_t o = o0 + t;
+        int64_t ct = -1;
+        if (o == 0) ct = qt;
+        else if (o < 2 * nt) {
+            int64_t s = (o + 1) >> 1;
+            ct = (o & 1) ? qt + s : qt - s;
+            if (ct < 0 || ct >= nt) ct = -1;
+        }
+        float lb = 0.f;
+        bool keep = ct >= 0;
+        if (keep && a.prune) {
+            float acc = 0.f;
+            for (int r = 0; r < MP; ++r) {
+                float g = fmaxf(fmaxf(a.tlo[ct * MP + r] - sqhi[r], sqlo[r] - a.thi[ct * MP + r]), 0.f);
+                acc = fmaf(g, g, acc);
+            }
+            lb = __fmul_rd(acc, a.lb_factor);
+            keep = __float_as_uint(lb) <= thr_blk;
+        }
+        // compact the surviving tiles in order
+        unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) sthr[warp] = __popc(bal);
+        __syncthreads();
+        int pos = __popc(bal & ((1u << lane) - 1u)) + (warp ? sthr[0] : 0);
+        if (keep) { slist[pos] = (int)ct; slb[pos] = lb; }
+        int total = sthr[0] + sthr[1];
+        __syncthreads();
+
+        for (int si = 0; si < total; ++si) {
+            if (a.prune && __float_as_uint(slb[si]) > thr_blk) continue;   // block-uniform
+            const int64_t c0 = (int64_t)slist[si] * TILE;
+            {   // stage the candidate tile
+                const float4* src = (const float4*)(a.xs + c0 * MP);
+                float4* dst = (float4*)cand;
+                for (int i = t; i < TILE * MP / 4; i += TILE) dst[i] = src[i];
+            }
+            __syncthreads();
+            bool skip = !valid;
+            if (!skip && a.prune) {
+                const float* clo = a.tlo + (int64_t)slist[si] * MP;
+                const float* chi = a.thi + (int64_t)slist[si] * MP;
+                float acc = 0.f;
+                if constexpr (QREG) {
+#pragma unroll
+                    for (int r = 0; r < MP; ++r) {
+                        float g = fmaxf(fmaxf(clo[r] - qr[r], qr[r] - chi[r]), 0.f);
+                        acc = fmaf(g, g, acc);
+                    }
+                } else {
+                    for (int r = 0; r < MP; ++r) {
+                        float qv = qs[r * TILE + t];
+                        float g = fmaxf(fmaxf(clo[r] - qv, qv - chi[r]), 0.f);
+                        acc = fmaf(g, g, acc);
+                    }
+                }
+                skip = __float_as_uint(__fmul_rd(acc, a.lb_factor)) > (uint32_t)(maxkey >> 32);
+            }
+            if (!skip) {
+                evaluated += TILE;
+                for (int c = 0; c < TILE; ++c) {
+                    float acc = 0.f;
+                    if constexpr (QREG) {
+                        const float4* cv = (const float4*)(cand + c * MP);
+#pragma unroll
+                        for (int r4 = 0; r4 < MP / 4; ++r4) {
+                            float4 v = cv[r4];
+                            float d0 = qr[4 * r4 + 0] - v.x, d1 = qr[4 * r4 + 1] - v.y;
+                            float d2 = qr[4 * r4 + 2] - v.z, d3 = qr[4 * r4 + 3] - v.w;
+                            acc = fmaf(d0, d0, acc);
+                            acc = fmaf(d1, d1, acc);
+                            acc = fmaf(d2, d2, acc);
+                            acc = fmaf(d3, d3, acc);
+                        }
+                    } else {
+                        for (int r = 0; r < MP; ++r) {
+                            float d = qs[r * TILE + t] - cand[c * MP + r];
+                            acc = fmaf(d, d, acc);
+                        }
+                    }
+                    const int64_t cp = c0 + c;
+                    uint64_t key = ((uint64_t)__float_as_uint(acc) << 32) | (uint32_t)cp;
+                    if (key < maxkey && cp != p && cp < a.n) {
+                        // replace the root of the max-heap and sift down
+                        int i = 0;
+                        for (;;) {
+                            int l = 2 * i + 1;
+                            if (l >= L) break;
+                            uint64_t ck = heap[l * TILE + t];
+                            int ch = l;
+                            if (l + 1 < L) {
+                                uint64_t rk = heap[(l + 1) * TILE + t];
+                                if (rk > ck) { ck = rk; ch = l + 1; }
+                            }
+                            if (ck <= key) break;
+                            heap[i * TILE + t] = ck;
+                            i = ch;
+                        }
+                        heap[i * TILE + t] = key;
+                        maxkey = heap[t];
+                    }
+                }
+            }
+            // block threshold = max over valid queries of their heap maxima
+            uint32_t mine = valid ? (uint32_t)(maxkey >> 32) : 0u;
+            uint32_t wmax = __reduce_max_sync(0xffffffffu, mine);
+            __syncthreads();
+            if (lane == 0) sthr[warp] = wmax;
+            __syncthreads();
+            thr_blk = max(sthr[0], sthr[1]);
+        }
+        __syncthreads();
+    }
+
+    // ---------------- a5: FP64 rescoring, exact ranking and certificate (warp w: queries 32w .. 32w+31)
+    unsigned long long ev = evaluated;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    if (lane == 0 && ev) atomicAdd(&a.rep->knn_candidates, ev);
+
+    uint64_t* wsd = sd + warp * L;
+    uint32_t* wso = so + warp * L;
+    for (int qq = 0; qq < 32; ++qq) {
+        const int tq = warp * 32 + qq;
+        const int64_t pq = qt * TILE + tq;
+        if (pq >= a.n) break;
+        const uint64_t root = heap[tq];
+        const uint32_t oq = a.perm[pq];
+        const float* qc = a.xs + pq * MP;
+        for (int s = lane; s < L; s += 32) {
+            uint64_t key = heap[s * TILE + tq];
+            uint64_t db = ~0ull;
+            uint32_t oj = 0xffffffffu;
+            if (key != ~0ull) {
+                uint32_t cp = (uint32_t)key;
+                oj = a.perm[cp];
+                db = (uint64_t)__double_as_longlong(canon_d2(qc, a.xs + (int64_t)cp * MP, a.m));
+            }
+            wsd[s] = db;
+            wso[s] = oj;
+        }
+        __syncwarp();
+        double dk = -1.0;
+        for (int s = lane; s < L; s += 32) {
+            const uint64_t ds = wsd[s];
+            const uint32_t os = wso[s];
+            int rank = 0;
+            for (int u = 0; u < L; ++u) {
+                uint64_t du = wsd[u];
+                rank += (du < ds) || (du == ds && wso[u] < os);
+            }
+            if (rank < a.k) {
+                a.nbr[(int64_t)oq * a.k + rank] = (int32_t)os;
+                a.nbr_d2[(int64_t)oq * a.k + rank] = __longlong_as_double((long long)ds);
+            }
+            if (rank == a.k - 1) dk = __longlong_as_double((long long)ds);
+        }
+        // certificate, evaluated by the lane holding rank k-1
+        if (dk >= 0.0) {
+            bool ok;
+            if (a.n - 1 <= (int64_t)L || root == ~0ull) ok = true;   // every candidate was kept
+            else {
+                float H = __uint_as_float((uint32_t)(root >> 32));
+                ok = isfinite(H) && dk < (double)H * a.cert_factor - (double)a.m * 1.1754943508222875e-38;
+            }
+            if (!ok) {
+                int slot = atomicAdd(a.fb_count, 1);
+                a.fb_list[slot] = (int)oq;
+                atomicAdd(&a.rep->knn_fallback_rows, 1ull);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ exact FP64 fallback rows
+// One block per listed row: radix selection of the k-th smallest canonical
+// FP64 distance (8 passes over the 8 bytes of its bit pattern), then the
+// strictly smaller ones plus the lowest-index ties, ranked by (d2, index).
+__global__ void __launch_bounds__(FB_THREADS) knn_fallback_kernel(const float* __restrict__ x, int64_t n, int m,
+                                                                   int k, const int* __restrict__ fb_list,
+                                                                   const int* __restrict__ fb_count,
+                                                                   int32_t* nbr, double* nbr_d2)
+{
+    __shared__ uint32_t hist[256];
+    __shared__ uint64_t skey[256];
+    __shared__ uint32_t sidx[256];
+    __shared__ uint64_t s_prefix, s_mask;
+    __shared__ uint32_t s_need, s_less, s_wtot[FB_THREADS / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int cnt = *fb_count;
+    for (int f = blockIdx.x; f < cnt; f += gridDim.x) {
+        const int64_t q = fb_list[f];
+        const float* xq = x + q * m;
+        if (t == 0) { s_prefix = 0; s_mask = 0; s_need = (uint32_t)k; s_less = 0; }
+        __syncthreads();
+        for (int byte = 7; byte >= 0; --byte) {
+            hist[t] = 0;
+            __syncthreads();
+            const uint64_t prefix = s_prefix, mask = s_mask;
+            for (int64_t j = t; j < n; j += FB_THREADS) {
+                if (j == q) continue;
+                uint64_t key = (uint64_t)__double_as_longlong(canon_d2(xq, x + j * m, m));
+                if ((key & mask) == prefix) atomicAdd(&hist[(key >> (8 * byte)) & 255u], 1u);
+            }
+            __syncthreads();
+            if (t == 0) {
+                uint32_t need = s_need, cum = 0;
+                int dgt = 0;
+                for (; dgt < 256; ++dgt) {
+                    if (cum + hist[dgt] >= need) break;
+                    cum += hist[dgt];
+                }
+                s_prefix = prefix | ((uint64_t)dgt << (8 * byte));
+                s_mask = mask | (0xffull << (8 * byte));
+                s_need = need - cum;
+            }
+            __syncthreads();
+        }
+        const uint64_t T = s_prefix;
+        const uint32_t need = s_need;          // how many ties at T are taken
+        const uint32_t nless = (uint32_t)k - need;
+        for (int64_t j = t; j < n; j += FB_THREADS) {
+            if (j == q) continue;
+            uint64_t key = (uint64_t)__double_as_longlong(canon_d2(xq, x + j * m, m));
+            if (key < T) {
+                uint32_t s = atomicAdd(&s_less, 1u);
+                skey[s] = key;
+                sidx[s] = (uint32_t)j;
+            }
+        }
+        __syncthreads();
+        uint32_t taken = 0;
+        for (int64_t b0 = 0; b0 < n && taken < need; b0 += FB_THREADS) {
+            int64_t j = b0 + t;
+            bool fl = j < n && j != q &&
+                      (uint64_t)__double_as_longlong(canon_d2(xq, x + j * m, m)) == T;
+            unsigned bal = __ballot_sync(0xffffffffu, fl);
+            if (lane == 0) s_wtot[w] = __popc(bal);
+            __syncthreads();
+            uint32_t off = __popc(bal & ((1u << lane) - 1u));
+            uint32_t tot = 0;
+            for (int ww = 0; ww < FB_THREADS / 32; ++ww) {
+                if (ww < w) off += s_wtot[ww];
+                tot += s_wtot[ww];
+            }
+            if (fl && taken + off < need) {
+                skey[nless + taken + off] = T;
+                sidx[nless + taken + off] = (uint32_t)j;
+            }
+            taken += tot;
+            __syncthreads();
+        }
+        __syncthreads();
+        for (int s = t; s < k; s += FB_THREADS) {
+            uint64_t ks = skey[s];
+            uint32_t is = sidx[s];
+            int rank = 0;
+            for (int u = 0; u < k; ++u) rank += (skey[u] < ks) || (skey[u] == ks && sidx[u] < is);
+            nbr[q * k + rank] = (int32_t)is;
+            nbr_d2[q * k + rank] = __longlong_as_double((long long)ks);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ host orchestration
+template <int MP>
+static size_t tile_smem(int L)
+{
+    return (size_t)L * TILE * 8 + TILE * MP * 4 + (MP > 16 ? TILE * MP * 4 : 0) + 2 * (size_t)L * 12;
+}
+
+template <int MP>
+static vb_status launch_tile(const TileArgs& a, cudaStream_t s)
+{
+    size_t sm = tile_smem<MP>(a.L);
+    static bool attr_set[16] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!attr_set[dev & 15]) {
+        if (cudaFuncSetAttribute(knn_tile_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tile_smem<MP>(256)) !=
+            cudaSuccess)
+            return VB_ERR_CUDA;
+        attr_set[dev & 15] = true;
+    }
+    knn_tile_kernel<MP><<<(unsigned)a.ntiles, TILE, sm, s>>>(a);
+    return last_launch();
+}
+
+vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_params* p, int32_t* nbr,
+                  double* nbr_d2, void* ws, size_t ws_bytes)
+{
+    if (!x || !nbr || !nbr_d2 || !p || n < 2 || n >= INT32_MAX || m < 1 || m > 128) return VB_ERR_ARG;
+    if (p->k < 1 || (int64_t)p->k > n - 1 || p->margin < 0 || p->k + p->margin > 256) return VB_ERR_ARG;
+    if (p->precision != VB_PREC_FP32) return VB_ERR_UNSUPPORTED;
+    KnnWs w;
+    Carve c(ws);
+    size_t need = knn_plan(c, n, m, p, &w);
+    if (!ws || ws_bytes < need) return VB_ERR_WORKSPACE;
+    cudaStream_t s = ctx->stream;
+    const int mp = pad_dim(m), md = morton_dims(m), bits = morton_bits(md);
+    const int64_t ntiles = (n + TILE - 1) / TILE, npad = ntiles * TILE;
+    const int nblk = (int)((n + RADIX_ITEMS - 1) / RADIX_ITEMS);
+
+    mark(ctx, VB_STAGE_KNN_ORDER, 0);
+    bbox_init_kernel<<<1, 32, 0, s>>>(w.bbox, w.fb_count);
+    bbox_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 4), 256, 0, s>>>(x, n, m, md, w.bbox, ctx->rep);
+    morton_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n, m, md, bits, w.bbox, w.key[0], w.val[0]);
+    int cur = 0;
+    for (int shift = 0; shift < 32; shift += 8) {
+        radix_hist_kernel<<<nblk, RADIX_T, 0, s>>>(w.key[cur], n, shift, w.hist, nblk);
+        scan_u32_single_kernel<<<1, 1024, 0, s>>>(w.hist, (int64_t)256 * nblk);
+        radix_scatter_kernel<<<nblk, RADIX_T, 0, s>>>(w.key[cur], w.val[cur], w.key[cur ^ 1], w.val[cur ^ 1], n,
+                                                      shift, w.hist, nblk);
+        cur ^= 1;
+    }
+    const uint32_t* perm = w.val[cur];
+    gather_kernel<<<(unsigned)((npad * mp + 255) / 256), 256, 0, s>>>(x, perm, n, npad, m, mp, w.xs);
+    tile_box_kernel<<<(unsigned)((ntiles * 32 + 255) / 256), 256, 0, s>>>(w.xs, n, ntiles, m, mp, w.tlo, w.thi);
+    vb_status st = last_launch();
+    if (st != VB_OK) return st;
+    mark(ctx, VB_STAGE_KNN_ORDER, 1);
+
+    TileArgs a;
+    a.xs = w.xs; a.tlo = w.tlo; a.thi = w.thi; a.perm = perm; a.n = n; a.ntiles = ntiles;
+    a.m = m; a.k = p->k; a.L = p->k + p->margin; a.prune = p->prune != VB_PRUNE_NONE;
+    a.lb_factor = 1.0f - 4.0f * (float)(m + 2) * 5.9604645e-8f;
+    a.cert_factor = 1.0 - 2.0 * (double)(m + 2) * 5.9604644775390625e-8;
+    a.nbr = nbr; a.nbr_d2 = nbr_d2; a.fb_list = w.fb_list; a.fb_count = w.fb_count; a.rep = ctx->rep;
+    mark(ctx, VB_STAGE_KNN_TILE, 0);
+    switch (mp) {
+        case 4: st = launch_tile<4>(a, s); break;
+        case 8: st = launch_tile<8>(a, s); break;
+        case 16: st = launch_tile<16>(a, s); break;
+        case 32: st = launch_tile<32>(a, s); break;
+        case 64: st = launch_tile<64>(a, s); break;
+        default: st = launch_tile<128>(a, s); break;
+    }
+    if (st != VB_OK) return st;
+    mark(ctx, VB_STAGE_KNN_TILE, 1);
+    mark(ctx, VB_STAGE_KNN_FALLBACK, 0);
+    knn_fallback_kernel<<<152, FB_THREADS, 0, s>>>(x, n, m, p->k, w.fb_list, w.fb_count, nbr, nbr_d2);
+    mark(ctx, VB_STAGE_KNN_FALLBACK, 1);
+    ctx->launches += 19;
+    return last_launch();
+}
+
+}  // namespace vb

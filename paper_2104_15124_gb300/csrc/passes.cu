@@ -1,0 +1,524 @@
+// Row passes over the symmetric pattern (steps a9-a14 of the build).
+//
+// Every pass is a fixed grid of warps walking CSR rows (warp w takes rows
+// w, w + W, ...), lanes striding the row's entries.  Per-entry arithmetic is
+// FP32 (ex2 on the SFU); row sums and sweep sums are carried to FP64 in a
+// fixed order, so every result is bitwise reproducible run to run.
+//   a9/a11 epsilon sweep (Sec. 2.3): chi_g = sum_E exp(-ed2 / (scale 2^xi_g rho_i rho_j))
+//          for all grid points in one pass; the diagonal contributes n.
+//   a10    density (Sec. 2.1): psi_i = sum_j K_eps^ij / (n (pi eps^2 b_i^2)^(d/2)), P = psi^beta.
+//   (R9)   operator-sweep centre from sum_E' ed2/(4 P_i P_j) and sum_E' ed2/(b_i b_j).
+//   a12    K_{eps,beta}, q = psi^(-beta d) K 1, K~ = K / (q_i q_j)^alpha, D = K~ 1, S = P D^(1/2) (Sec. 2.2).
+//   a13    L-hat_ij = K~^ij / (eps^2 S_i S_j), L-hat_ii = -sum_{j != i} K~^ij / (eps^2 S_i^2).
+//          Each off-diagonal value is a product of pairwise products
+//          (x_i * x_j), so (i, j) and (j, i) give the same bits.
+//   a14    CSR SpMV, plain and difference (Laplacian) form.
+#include "vb_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace vb {
+
+constexpr int WARPS = kRowThreads / 32;
+constexpr int FLUSH = 1024;   // entries a warp sums in FP32 before carrying to FP64
+
+struct RowIter {
+    int64_t i, step;
+    int lane, w;
+    __device__ RowIter()
+    {
+        lane = threadIdx.x & 31;
+        w = threadIdx.x >> 5;
+        i = (int64_t)blockIdx.x * WARPS + w;
+        step = (int64_t)gridDim.x * WARPS;
+    }
+};
+
+__global__ void recip_f32_kernel(const double* __restrict__ v, int64_t n, float scale, float* out)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)(1.0 / v[i]) * scale;
+}
+
+// ------------------------------------------------------------------ a9 / a11 epsilon sweep
+struct SweepConst {
+    float negr[kMaxGrid];   // -2^-(xi_lo + g dxi)
+};
+
+__global__ void __launch_bounds__(kRowThreads) sweep_kernel(const int64_t* __restrict__ row_ptr,
+                                                          const int32_t* __restrict__ col,
+                                                          const float* __restrict__ ed2, int64_t n,
+                                                          const float* __restrict__ irho,
+                                                          const double* __restrict__ xi_c_dev, double scale, int G,
+                                                          SweepConst sc, double* partial)
+{
+    __shared__ double wacc[WARPS][kMaxGrid];
+    for (int i = threadIdx.x; i < WARPS * kMaxGrid; i += blockDim.x) (&wacc[0][0])[i] = 0.0;
+    __syncthreads();
+    const double xc = xi_c_dev ? *xi_c_dev : 0.0;
+    const float c0 = (float)(1.4426950408889634 / (scale * exp2(xc)));
+    float acc[kMaxGrid];
+#pragma unroll
+    for (int g = 0; g < kMaxGrid; ++g) acc[g] = 0.f;
+    RowIter it;
+    int since = 0;
+    auto flush = [&]() {
+#pragma unroll
+        for (int g = 0; g < kMaxGrid; ++g) {
+            if (g < G) {
+                float v = warp_sum_f32(acc[g]);
+                if (it.lane == 0) wacc[it.w][g] += (double)v;
+            }
+            acc[g] = 0.f;
+        }
+    };
+    for (int64_t i = it.i; i < n; i += it.step) {
+        const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
+        const float ri = irho[i];
+        for (int64_t e = rb + it.lane; e < re; e += 32) {
+            const int32_t j = col[e];
+            if (j == i) continue;
+            const float u = ed2[e] * (ri * irho[j]) * c0;
+#pragma unroll
+            for (int g = 0; g < kMaxGrid; ++g)
+                if (g < G) acc[g] += ex2_approx(u * sc.negr[g]);
+        }
+        since += (int)(re - rb);
+        if (since >= FLUSH) {
+            flush();
+            since = 0;
+        }
+    }
+    flush();
+    __syncthreads();
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < WARPS; ++w) s += wacc[w][g];
+        partial[(int64_t)blockIdx.x * G + g] = s;
+    }
+}
+
+// One block of 64 warps-worth of work: warp w sums grid columns w, w + 32, ... over
+// the block partials in a fixed lane-strided order, then 64 threads take one log
+// each and one warp finds the first maximiser of chi'.
+__global__ void __launch_bounds__(1024) sweep_finish_kernel(const double* __restrict__ partial, int nblk, int G,
+                                                           int64_t n, double xi_lo, double dxi,
+                                                           const double* __restrict__ xi_c_dev, int warn_bit,
+                                                           double* eps2, double* chi, double* dim, DevReport* rep)
+{
+    __shared__ double sh[kMaxGrid], lg[kMaxGrid];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int g = w; g < G; g += 32) {
+        double s = 0.0;
+        for (int b = lane; b < nblk; b += 32) s += partial[(int64_t)b * G + g];
+        s = warp_sum_f64(s);
+        if (lane == 0) {
+            s += (double)n;   // diagonal entries: exp(0) = 1 each
+            sh[g] = s;
+            chi[g] = s;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < G) lg[threadIdx.x] = log(sh[threadIdx.x]);
+    __syncthreads();
+    if (w == 0) {
+        const double inv = 1.0 / (dxi * 0.69314718055994531);
+        double bv = -INFINITY;
+        int best = 0;
+        for (int h = lane; h + 1 < G; h += 32) {
+            double cp = (lg[h + 1] - lg[h]) * inv;
+            if (cp > bv) { bv = cp; best = h; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            int ob = __shfl_xor_sync(0xffffffffu, best, o);
+            if (ov > bv || (ov == bv && ob < best)) { bv = ov; best = ob; }
+        }
+        if (lane == 0) {
+            const double xc = xi_c_dev ? *xi_c_dev : 0.0;
+            *eps2 = exp2(xc + xi_lo + best * dxi);
+            *dim = 2.0 * bv;
+            if (best == 0 || best == G - 2) atomicOr(&rep->warnings, warn_bit);
+        }
+    }
+}
+
+size_t sweep_ws_bytes(int64_t n)
+{
+    Carve c(nullptr);
+    c.take<float>(n);
+    c.take<double>((size_t)kRowBlocks * kMaxGrid);
+    return c.off;
+}
+
+vb_status sweep_run(Ctx* ctx, const vb_graph* g, const double* rho, double scale, const double* xi_c_dev,
+                    double xi_lo, double xi_hi, double dxi, int warn_bit, double* eps2, double* chi, double* dim,
+                    void* ws, size_t ws_bytes)
+{
+    if (!g || !g->row_ptr || !g->col || !g->ed2 || g->n < 1 || !rho || !eps2 || !chi || !dim) return VB_ERR_ARG;
+    if (!(dxi > 0) || !(scale > 0)) return VB_ERR_ARG;
+    const int G = (int)std::lround((xi_hi - xi_lo) / dxi) + 1;
+    if (G < 3 || G > kMaxGrid) return VB_ERR_ARG;
+    Carve c(ws);
+    float* irho = c.take<float>(g->n);
+    double* partial = c.take<double>((size_t)kRowBlocks * kMaxGrid);
+    if (!ws || ws_bytes < c.off) return VB_ERR_WORKSPACE;
+    SweepConst sc;
+    for (int h = 0; h < kMaxGrid; ++h) sc.negr[h] = h < G ? -(float)std::exp2(-(xi_lo + h * dxi)) : 0.f;
+    cudaStream_t s = ctx->stream;
+    const int stage = warn_bit == 2 ? VB_STAGE_SWEEP_OPERATOR : VB_STAGE_SWEEP_DENSITY;
+    recip_f32_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(rho, g->n, 1.f, irho);
+    mark(ctx, stage, 0);
+    sweep_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, g->n, irho, xi_c_dev, scale, G, sc,
+                                                    partial);
+    mark(ctx, stage, 1);
+    sweep_finish_kernel<<<1, 1024, 0, s>>>(partial, kRowBlocks, G, g->n, xi_lo, dxi, xi_c_dev, warn_bit, eps2, chi,
+                                           dim, ctx->rep);
+    ctx->launches += 3;
+    return last_launch();
+}
+
+// ------------------------------------------------------------------ a10 density
+__global__ void __launch_bounds__(kRowThreads) density_kernel(const int64_t* __restrict__ row_ptr,
+                                                            const int32_t* __restrict__ col,
+                                                            const float* __restrict__ ed2, int64_t n,
+                                                            const double* __restrict__ b, const float* __restrict__ ib,
+                                                            const double* __restrict__ eps2_dev, double d, double beta,
+                                                            double* psi, double* P)
+{
+    const double e2 = *eps2_dev;
+    const float c = (float)(1.4426950408889634 / e2);
+    const float pi_e2 = (float)(3.14159265358979323846 * e2), hd = (float)(0.5 * d), fbeta = (float)beta;
+    const float inv_n = 1.0f / (float)n;
+    RowIter it;
+    for (int64_t i = it.i; i < n; i += it.step) {
+        const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
+        const float bi = ib[i];
+        float s = 0.f;
+        for (int64_t e = rb + it.lane; e < re; e += 32) s += ex2_approx(-(ed2[e] * (bi * ib[col[e]])) * c);
+        double tot = warp_sum_f64((double)s);
+        if (it.lane == 0) {
+            // w_i = n (pi eps^2 b_i^2)^(d/2), psi_i = sum / w_i, P_i = psi_i^beta (FP32 SFU powers)
+            const float bb = (float)b[i];
+            const float w = pow_sfu(pi_e2 * bb * bb, hd);
+            const float ps = (float)tot * (inv_n / w);
+            psi[i] = (double)ps;
+            P[i] = (double)pow_sfu(ps, fbeta);
+        }
+    }
+}
+
+size_t density_ws_bytes(int64_t n)
+{
+    Carve c(nullptr);
+    c.take<float>(n);
+    return c.off;
+}
+
+vb_status density_run(Ctx* ctx, const vb_graph* g, const double* b, const double* eps2_dev, double d, double beta,
+                      double* psi, double* P, void* ws, size_t ws_bytes)
+{
+    if (!g || !g->row_ptr || !b || !eps2_dev || !psi || !P || !(d > 0)) return VB_ERR_ARG;
+    Carve c(ws);
+    float* ib = c.take<float>(g->n);
+    if (!ws || ws_bytes < c.off) return VB_ERR_WORKSPACE;
+    mark(ctx, VB_STAGE_DENSITY, 0);
+    recip_f32_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, ctx->stream>>>(b, g->n, 1.f, ib);
+    density_kernel<<<kRowBlocks, kRowThreads, 0, ctx->stream>>>(g->row_ptr, g->col, g->ed2, g->n, b, ib, eps2_dev, d,
+                                                                beta, psi, P);
+    mark(ctx, VB_STAGE_DENSITY, 1);
+    ctx->launches += 2;
+    return last_launch();
+}
+
+// ------------------------------------------------------------------ operator-sweep centre
+__global__ void __launch_bounds__(kRowThreads) centre_kernel(const int64_t* __restrict__ row_ptr,
+                                                           const int32_t* __restrict__ col,
+                                                           const float* __restrict__ ed2, int64_t n,
+                                                           const float* __restrict__ ib,
+                                                           const float* __restrict__ iP, double* partial)
+{
+    __shared__ double sh[WARPS][2];
+    RowIter it;
+    double a_op = 0.0, a_den = 0.0;
+    for (int64_t i = it.i; i < n; i += it.step) {
+        const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
+        const float pi_ = iP[i], bi = ib[i];
+        float so = 0.f, sd = 0.f;
+        for (int64_t e = rb + it.lane; e < re; e += 32) {
+            const int32_t j = col[e];
+            if (j == i) continue;
+            const float x = ed2[e];
+            so += x * (pi_ * iP[j]);
+            sd += x * (bi * ib[j]);
+        }
+        a_op += (double)so;
+        a_den += (double)sd;
+    }
+    a_op = warp_sum_f64(a_op);
+    a_den = warp_sum_f64(a_den);
+    if (it.lane == 0) { sh[it.w][0] = a_op; sh[it.w][1] = a_den; }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double s = 0.0;
+        for (int w = 0; w < WARPS; ++w) s += sh[w][threadIdx.x];
+        partial[2 * (int64_t)blockIdx.x + threadIdx.x] = s;
+    }
+}
+
+__global__ void centre_finish_kernel(const double* __restrict__ partial, int nblk, double* xi_c)
+{
+    const int lane = threadIdx.x;
+    double so = 0.0, sd = 0.0;
+    for (int b = lane; b < nblk; b += 32) { so += partial[2 * b]; sd += partial[2 * b + 1]; }
+    so = warp_sum_f64(so);
+    sd = warp_sum_f64(sd);
+    // R9: the operator argument is ed2 / (4 P_i P_j); so holds sum ed2 / (P_i P_j)
+    if (lane == 0) *xi_c = floor(4.0 * log2(0.25 * so / sd) + 0.5) / 4.0;
+}
+
+size_t centre_ws_bytes(int64_t n)
+{
+    Carve c(nullptr);
+    c.take<float>(n);
+    c.take<float>(n);
+    c.take<double>((size_t)kRowBlocks * 2);
+    return c.off;
+}
+
+vb_status centre_run(Ctx* ctx, const vb_graph* g, const double* b, const double* P, double* xi_c_dev, void* ws,
+                     size_t ws_bytes)
+{
+    if (!g || !g->row_ptr || !b || !P || !xi_c_dev) return VB_ERR_ARG;
+    Carve c(ws);
+    float* ib = c.take<float>(g->n);
+    float* iP = c.take<float>(g->n);
+    double* partial = c.take<double>((size_t)kRowBlocks * 2);
+    if (!ws || ws_bytes < c.off) return VB_ERR_WORKSPACE;
+    cudaStream_t s = ctx->stream;
+    mark(ctx, VB_STAGE_CENTRE, 0);
+    recip_f32_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(b, g->n, 1.f, ib);
+    recip_f32_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(P, g->n, 1.f, iP);
+    centre_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, g->n, ib, iP, partial);
+    centre_finish_kernel<<<1, 32, 0, s>>>(partial, kRowBlocks, xi_c_dev);
+    mark(ctx, VB_STAGE_CENTRE, 1);
+    ctx->launches += 4;
+    return last_launch();
+}
+
+// ------------------------------------------------------------------ a12 / a13 operator and L-hat
+struct OpVec {
+    float* iP;    // 1 / P
+    float* qa;    // q^-alpha
+    float* iS;    // 1 / S
+};
+
+// K_{eps,beta}^ij in the shared form used by all three passes (symmetric in i, j)
+__device__ __forceinline__ float k_op(float x, float iPi, float iPj, float c1)
+{
+    return ex2_approx(-(x * (iPi * iPj)) * c1);
+}
+
+__global__ void __launch_bounds__(kRowThreads) q_kernel(const int64_t* __restrict__ row_ptr,
+                                                      const int32_t* __restrict__ col, const float* __restrict__ ed2,
+                                                      int64_t n, const double* __restrict__ psi,
+                                                      const float* __restrict__ iP, const double* __restrict__ eps2_dev,
+                                                      double beta, double d, double alpha, double* q, float* qa)
+{
+    const float c1 = (float)(1.4426950408889634 / (4.0 * *eps2_dev));
+    const float mbd = (float)(-beta * d), malpha = (float)(-alpha);
+    RowIter it;
+    for (int64_t i = it.i; i < n; i += it.step) {
+        const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
+        const float pi_ = iP[i];
+        float s = 0.f;
+        for (int64_t e = rb + it.lane; e < re; e += 32) s += k_op(ed2[e], pi_, iP[col[e]], c1);
+        const double tot = warp_sum_f64((double)s);
+        if (it.lane == 0) {
+            const float qi = pow_sfu((float)psi[i], mbd) * (float)tot;
+            q[i] = (double)qi;
+            qa[i] = pow_sfu(qi, malpha);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kRowThreads) d_kernel(const int64_t* __restrict__ row_ptr,
+                                                      const int32_t* __restrict__ col, const float* __restrict__ ed2,
+                                                      int64_t n, const float* __restrict__ iP,
+                                                      const float* __restrict__ qa, const double* __restrict__ P,
+                                                      const double* __restrict__ eps2_dev, double* D, double* S,
+                                                      float* iS)
+{
+    const float c1 = (float)(1.4426950408889634 / (4.0 * *eps2_dev));
+    RowIter it;
+    for (int64_t i = it.i; i < n; i += it.step) {
+        const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
+        const float pi_ = iP[i], qi = qa[i];
+        float s = 0.f;
+        for (int64_t e = rb + it.lane; e < re; e += 32) {
+            const int32_t j = col[e];
+            s += k_op(ed2[e], pi_, iP[j], c1) * (qi * qa[j]);
+        }
+        const double tot = warp_sum_f64((double)s);
+        if (it.lane == 0) {
+            const double si = P[i] * sqrt(tot);
+            D[i] = tot;
+            S[i] = si;
+            iS[i] = (float)(1.0 / si);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kRowThreads) lhat_kernel(const int64_t* __restrict__ row_ptr,
+                                                         const int32_t* __restrict__ col,
+                                                         const float* __restrict__ ed2, int64_t n,
+                                                         const float* __restrict__ iP, const float* __restrict__ qa,
+                                                         const float* __restrict__ iS, const double* __restrict__ S,
+                                                         const double* __restrict__ eps2_dev, float* val)
+{
+    const double e2 = *eps2_dev;
+    const float c1 = (float)(1.4426950408889634 / (4.0 * e2));
+    const float ie = (float)(1.0 / e2);
+    RowIter it;
+    for (int64_t i = it.i; i < n; i += it.step) {
+        const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
+        const float pi_ = iP[i], qi = qa[i], si = iS[i];
+        float off = 0.f;
+        int64_t diag = -1;
+        for (int64_t e = rb + it.lane; e < re; e += 32) {
+            const int32_t j = col[e];
+            if (j == i) { diag = e; continue; }
+            const float kt = k_op(ed2[e], pi_, iP[j], c1) * (qi * qa[j]);
+            off += kt;
+            val[e] = kt * (si * iS[j]) * ie;
+        }
+        const double tot = warp_sum_f64((double)off);
+        if (diag >= 0) {
+            const double sii = S[i];
+            val[diag] = (float)(-tot / (e2 * sii * sii));
+        }
+    }
+}
+
+size_t kernel_csr_ws_bytes(int64_t n)
+{
+    Carve c(nullptr);
+    c.take<float>(n);
+    c.take<float>(n);
+    c.take<float>(n);
+    return c.off;
+}
+
+vb_status kernel_csr_run(Ctx* ctx, const vb_graph* g, const double* psi, const double* P, const vb_op_params* op,
+                         const double* eps2_op_dev, float* val, double* q, double* D, double* S, void* ws,
+                         size_t ws_bytes)
+{
+    if (!g || !g->row_ptr || !psi || !P || !op || !eps2_op_dev || !val || !q || !D || !S) return VB_ERR_ARG;
+    if (!(op->d > 0)) return VB_ERR_ARG;
+    Carve c(ws);
+    OpVec v;
+    v.iP = c.take<float>(g->n);
+    v.qa = c.take<float>(g->n);
+    v.iS = c.take<float>(g->n);
+    if (!ws || ws_bytes < c.off) return VB_ERR_WORKSPACE;
+    // Sec. 2.2: c = 2 - 2 alpha + d beta + 2 beta
+    const double alpha = (2.0 - op->c + op->d * op->beta + 2.0 * op->beta) / 2.0;
+    cudaStream_t s = ctx->stream;
+    const int64_t n = g->n;
+    mark(ctx, VB_STAGE_OPERATOR, 0);
+    recip_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, n, 1.f, v.iP);
+    q_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, n, psi, v.iP, eps2_op_dev, op->beta, op->d,
+                                                alpha, q, v.qa);
+    d_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, n, v.iP, v.qa, P, eps2_op_dev, D, S, v.iS);
+    mark(ctx, VB_STAGE_OPERATOR, 1);
+    mark(ctx, VB_STAGE_LHAT, 0);
+    lhat_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, n, v.iP, v.qa, v.iS, S, eps2_op_dev,
+                                                   val);
+    mark(ctx, VB_STAGE_LHAT, 1);
+    ctx->launches += 4;
+    return last_launch();
+}
+
+// ------------------------------------------------------------------ a14 SpMV
+__global__ void __launch_bounds__(kRowThreads) spmv_plain_kernel(const int64_t* __restrict__ row_ptr,
+                                                               const int32_t* __restrict__ col,
+                                                               const float* __restrict__ val, int64_t n, float alpha,
+                                                               const float* __restrict__ x, float beta, float* y)
+{
+    RowIter it;
+    for (int64_t i = it.i; i < n; i += it.step) {
+        const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
+        float s = 0.f;
+        for (int64_t e = rb + it.lane; e < re; e += 32) s = fmaf(val[e], x[col[e]], s);
+        const double tot = warp_sum_f64((double)s);
+        if (it.lane == 0) y[i] = (float)((double)alpha * tot + (beta != 0.f ? (double)beta * y[i] : 0.0));
+    }
+}
+
+__global__ void lap_prep_kernel(const float* __restrict__ x, const double* __restrict__ S, int64_t n, double* z,
+                                float* sf)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        const double si = S[i];
+        z[i] = (double)x[i] / si;
+        sf[i] = (float)si;
+    }
+}
+
+// y_i = alpha sum_{j != i} val_ij S_j (z_j - z_i) + beta y_i, z = x / S: the
+// differences are taken in FP64 so that smooth vectors keep their accuracy.
+__global__ void __launch_bounds__(kRowThreads) spmv_lap_kernel(const int64_t* __restrict__ row_ptr,
+                                                             const int32_t* __restrict__ col,
+                                                             const float* __restrict__ val, int64_t n, float alpha,
+                                                             const double* __restrict__ z, const float* __restrict__ sf,
+                                                             float beta, float* y)
+{
+    RowIter it;
+    for (int64_t i = it.i; i < n; i += it.step) {
+        const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
+        const double zi = z[i];
+        float s = 0.f;
+        for (int64_t e = rb + it.lane; e < re; e += 32) {
+            const int32_t j = col[e];
+            if (j == i) continue;
+            s = fmaf(val[e] * sf[j], (float)(z[j] - zi), s);
+        }
+        const double tot = warp_sum_f64((double)s);
+        if (it.lane == 0) y[i] = (float)((double)alpha * tot + (beta != 0.f ? (double)beta * y[i] : 0.0));
+    }
+}
+
+size_t spmv_ws_bytes(int64_t n)
+{
+    Carve c(nullptr);
+    c.take<double>(n);
+    c.take<float>(n);
+    return c.off;
+}
+
+vb_status spmv_run(Ctx* ctx, const vb_graph* g, const float* val, const double* S, int mode, float alpha,
+                   const float* x, float beta, float* y, void* ws, size_t ws_bytes)
+{
+    if (!g || !g->row_ptr || !g->col || !val || !x || !y || x == y) return VB_ERR_ARG;
+    if (mode == VB_SPMV_PLAIN) {
+        spmv_plain_kernel<<<kRowBlocks, kRowThreads, 0, ctx->stream>>>(g->row_ptr, g->col, val, g->n, alpha, x, beta, y);
+        ctx->launches += 1;
+    } else if (mode == VB_SPMV_LAPLACIAN) {
+        if (!S) return VB_ERR_ARG;
+        Carve c(ws);
+        double* z = c.take<double>(g->n);
+        float* sf = c.take<float>(g->n);
+        if (!ws || ws_bytes < c.off) return VB_ERR_WORKSPACE;
+        lap_prep_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, ctx->stream>>>(x, S, g->n, z, sf);
+        spmv_lap_kernel<<<kRowBlocks, kRowThreads, 0, ctx->stream>>>(g->row_ptr, g->col, val, g->n, alpha, z, sf, beta, y);
+        ctx->launches += 2;
+    } else {
+        return VB_ERR_ARG;
+    }
+    return last_launch();
+}
+
+}  // namespace vb

@@ -82,6 +82,9 @@ def test_row_ranges_and_errors():
         K.knn(x, 90)
     with pytest.raises(ValueError):
         K.knn(x, 0)
+    rows = np.array([5, 77, 5, 0])
+    r_nbr, r_d2 = K.knn_rows(x, 6, rows)
+    assert np.array_equal(r_nbr, full[0][rows]) and np.array_equal(r_d2, full[1][rows])
     # k = n - 1 returns every other point
     nbr, _ = K.knn(x[:12], 11)
     assert all(sorted(nbr[i]) == [j for j in range(12) if j != i] for i in range(12))
