@@ -190,8 +190,6 @@ __global__ void __launch_bounds__(kRowThreads) density_kernel(const int64_t* __r
 {
     const double e2 = *eps2_dev;
     const float c = (float)(1.4426950408889634 / e2);
-    const float pi_e2 = (float)(3.14159265358979323846 * e2), hd = (float)(0.5 * d), fbeta = (float)beta;
-    const float inv_n = 1.0f / (float)n;
     RowIter it;
     for (int64_t i = it.i; i < n; i += it.step) {
         const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
@@ -199,15 +197,23 @@ __global__ void __launch_bounds__(kRowThreads) density_kernel(const int64_t* __r
         float s = 0.f;
         for (int64_t e = rb + it.lane; e < re; e += 32) s += ex2_approx(-(ed2[e] * (bi * ib[col[e]])) * c);
         double tot = warp_sum_f64((double)s);
-        if (it.lane == 0) {
-            // w_i = n (pi eps^2 b_i^2)^(d/2), psi_i = sum / w_i, P_i = psi_i^beta (FP32 SFU powers)
-            const float bb = (float)b[i];
-            const float w = pow_sfu(pi_e2 * bb * bb, hd);
-            const float ps = (float)tot * (inv_n / w);
-            psi[i] = (double)ps;
-            P[i] = (double)pow_sfu(ps, fbeta);
-        }
+        if (it.lane == 0) psi[i] = tot;
     }
+}
+
+// w_i = n (pi eps^2 b_i^2)^(d/2), psi_i = sum_i / w_i, P_i = psi_i^beta, one thread per point.
+// FP64 powers: P enters every operator-kernel exponent, so its error is multiplied
+// by exponents of up to about 60 in the smallest stored entries.
+__global__ void density_finish_kernel(const double* __restrict__ b, const double* __restrict__ eps2_dev, int64_t n,
+                                      double d, double beta, double* psi, double* P)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double bb = b[i];
+    const double w = (double)n * pow(3.14159265358979323846 * *eps2_dev * bb * bb, 0.5 * d);
+    const double ps = psi[i] / w;
+    psi[i] = ps;
+    P[i] = pow(ps, beta);
 }
 
 size_t density_ws_bytes(int64_t n)
@@ -228,8 +234,9 @@ vb_status density_run(Ctx* ctx, const vb_graph* g, const double* b, const double
     recip_f32_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, ctx->stream>>>(b, g->n, 1.f, ib);
     density_kernel<<<kRowBlocks, kRowThreads, 0, ctx->stream>>>(g->row_ptr, g->col, g->ed2, g->n, b, ib, eps2_dev, d,
                                                                 beta, psi, P);
+    density_finish_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, ctx->stream>>>(b, eps2_dev, g->n, d, beta, psi, P);
     mark(ctx, VB_STAGE_DENSITY, 1);
-    ctx->launches += 2;
+    ctx->launches += 3;
     return last_launch();
 }
 
@@ -310,31 +317,68 @@ vb_status centre_run(Ctx* ctx, const vb_graph* g, const double* b, const double*
 
 // ------------------------------------------------------------------ a12 / a13 operator and L-hat
 struct OpVec {
-    float* iP;    // 1 / P
+    float* iPh;   // 1 / P as an unevaluated pair hi + lo of floats
+    float* iPl;
     float* qa;    // q^-alpha
     float* iS;    // 1 / S
 };
 
-// K_{eps,beta}^ij in the shared form used by all three passes (symmetric in i, j)
-__device__ __forceinline__ float k_op(float x, float iPi, float iPj, float c1)
+__global__ void recip_pair_kernel(const double* __restrict__ v, int64_t n, float* hi, float* lo)
 {
-    return ex2_approx(-(x * (iPi * iPj)) * c1);
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double r = 1.0 / v[i];
+    const float h = (float)r;
+    hi[i] = h;
+    lo[i] = (float)(r - (double)h);
+}
+
+// K_{eps,beta}^ij = 2^-u, u = ed2 * (c1 * (iP_i * iP_j)), c1 = log2(e) / (4 eps^2).  The
+// exponent is carried as a float pair (error-free products with fmaf), because an
+// exponent error du changes K by the relative amount du ln 2 and u reaches about
+// 60 in the smallest stored entries.  Every step is symmetric in (i, j), so
+// K^ij and K^ji have the same bits.
+__device__ __forceinline__ float k_op(float x, float ahi, float ali, float ahj, float alj, float ch, float cl)
+{
+    const float wh = ahi * ahj;
+    const float wl = fmaf(ahi, ahj, -wh) + (ahi * alj + ali * ahj);
+    const float th = ch * wh;
+    const float tl = fmaf(ch, wh, -th) + (ch * wl + cl * wh);
+    const float uh = x * th;
+    const float ul = fmaf(x, th, -uh) + x * tl;
+    return ex2_approx(-uh) * fmaf(-ul, 0.6931471805599453f, 1.0f);
+}
+
+struct C1 {
+    float h, l;
+};
+__device__ __forceinline__ C1 c1_pair(const double* eps2_dev)
+{
+    const double c = 1.4426950408889634 / (4.0 * *eps2_dev);
+    C1 r;
+    r.h = (float)c;
+    r.l = (float)(c - (double)r.h);
+    return r;
 }
 
 __global__ void __launch_bounds__(kRowThreads) q_kernel(const int64_t* __restrict__ row_ptr,
                                                       const int32_t* __restrict__ col, const float* __restrict__ ed2,
                                                       int64_t n, const double* __restrict__ psi,
-                                                      const float* __restrict__ iP, const double* __restrict__ eps2_dev,
-                                                      double beta, double d, double alpha, double* q, float* qa)
+                                                      const float* __restrict__ iPh, const float* __restrict__ iPl,
+                                                      const double* __restrict__ eps2_dev, double beta, double d,
+                                                      double alpha, double* q, float* qa)
 {
-    const float c1 = (float)(1.4426950408889634 / (4.0 * *eps2_dev));
+    const C1 c1 = c1_pair(eps2_dev);
     const float mbd = (float)(-beta * d), malpha = (float)(-alpha);
     RowIter it;
     for (int64_t i = it.i; i < n; i += it.step) {
         const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
-        const float pi_ = iP[i];
+        const float ph = iPh[i], pl = iPl[i];
         float s = 0.f;
-        for (int64_t e = rb + it.lane; e < re; e += 32) s += k_op(ed2[e], pi_, iP[col[e]], c1);
+        for (int64_t e = rb + it.lane; e < re; e += 32) {
+            const int32_t j = col[e];
+            s += k_op(ed2[e], ph, pl, iPh[j], iPl[j], c1.h, c1.l);
+        }
         const double tot = warp_sum_f64((double)s);
         if (it.lane == 0) {
             const float qi = pow_sfu((float)psi[i], mbd) * (float)tot;
@@ -346,20 +390,20 @@ __global__ void __launch_bounds__(kRowThreads) q_kernel(const int64_t* __restric
 
 __global__ void __launch_bounds__(kRowThreads) d_kernel(const int64_t* __restrict__ row_ptr,
                                                       const int32_t* __restrict__ col, const float* __restrict__ ed2,
-                                                      int64_t n, const float* __restrict__ iP,
-                                                      const float* __restrict__ qa, const double* __restrict__ P,
-                                                      const double* __restrict__ eps2_dev, double* D, double* S,
-                                                      float* iS)
+                                                      int64_t n, const float* __restrict__ iPh,
+                                                      const float* __restrict__ iPl, const float* __restrict__ qa,
+                                                      const double* __restrict__ P, const double* __restrict__ eps2_dev,
+                                                      double* D, double* S, float* iS)
 {
-    const float c1 = (float)(1.4426950408889634 / (4.0 * *eps2_dev));
+    const C1 c1 = c1_pair(eps2_dev);
     RowIter it;
     for (int64_t i = it.i; i < n; i += it.step) {
         const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
-        const float pi_ = iP[i], qi = qa[i];
+        const float ph = iPh[i], pl = iPl[i], qi = qa[i];
         float s = 0.f;
         for (int64_t e = rb + it.lane; e < re; e += 32) {
             const int32_t j = col[e];
-            s += k_op(ed2[e], pi_, iP[j], c1) * (qi * qa[j]);
+            s += k_op(ed2[e], ph, pl, iPh[j], iPl[j], c1.h, c1.l) * (qi * qa[j]);
         }
         const double tot = warp_sum_f64((double)s);
         if (it.lane == 0) {
@@ -374,23 +418,24 @@ __global__ void __launch_bounds__(kRowThreads) d_kernel(const int64_t* __restric
 __global__ void __launch_bounds__(kRowThreads) lhat_kernel(const int64_t* __restrict__ row_ptr,
                                                          const int32_t* __restrict__ col,
                                                          const float* __restrict__ ed2, int64_t n,
-                                                         const float* __restrict__ iP, const float* __restrict__ qa,
-                                                         const float* __restrict__ iS, const double* __restrict__ S,
+                                                         const float* __restrict__ iPh, const float* __restrict__ iPl,
+                                                         const float* __restrict__ qa, const float* __restrict__ iS,
+                                                         const double* __restrict__ S,
                                                          const double* __restrict__ eps2_dev, float* val)
 {
     const double e2 = *eps2_dev;
-    const float c1 = (float)(1.4426950408889634 / (4.0 * e2));
+    const C1 c1 = c1_pair(eps2_dev);
     const float ie = (float)(1.0 / e2);
     RowIter it;
     for (int64_t i = it.i; i < n; i += it.step) {
         const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
-        const float pi_ = iP[i], qi = qa[i], si = iS[i];
+        const float ph = iPh[i], pl = iPl[i], qi = qa[i], si = iS[i];
         float off = 0.f;
         int64_t diag = -1;
         for (int64_t e = rb + it.lane; e < re; e += 32) {
             const int32_t j = col[e];
             if (j == i) { diag = e; continue; }
-            const float kt = k_op(ed2[e], pi_, iP[j], c1) * (qi * qa[j]);
+            const float kt = k_op(ed2[e], ph, pl, iPh[j], iPl[j], c1.h, c1.l) * (qi * qa[j]);
             off += kt;
             val[e] = kt * (si * iS[j]) * ie;
         }
@@ -405,9 +450,7 @@ __global__ void __launch_bounds__(kRowThreads) lhat_kernel(const int64_t* __rest
 size_t kernel_csr_ws_bytes(int64_t n)
 {
     Carve c(nullptr);
-    c.take<float>(n);
-    c.take<float>(n);
-    c.take<float>(n);
+    for (int i = 0; i < 4; ++i) c.take<float>(n);
     return c.off;
 }
 
@@ -419,7 +462,8 @@ vb_status kernel_csr_run(Ctx* ctx, const vb_graph* g, const double* psi, const d
     if (!(op->d > 0)) return VB_ERR_ARG;
     Carve c(ws);
     OpVec v;
-    v.iP = c.take<float>(g->n);
+    v.iPh = c.take<float>(g->n);
+    v.iPl = c.take<float>(g->n);
     v.qa = c.take<float>(g->n);
     v.iS = c.take<float>(g->n);
     if (!ws || ws_bytes < c.off) return VB_ERR_WORKSPACE;
@@ -428,14 +472,15 @@ vb_status kernel_csr_run(Ctx* ctx, const vb_graph* g, const double* psi, const d
     cudaStream_t s = ctx->stream;
     const int64_t n = g->n;
     mark(ctx, VB_STAGE_OPERATOR, 0);
-    recip_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, n, 1.f, v.iP);
-    q_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, n, psi, v.iP, eps2_op_dev, op->beta, op->d,
-                                                alpha, q, v.qa);
-    d_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, n, v.iP, v.qa, P, eps2_op_dev, D, S, v.iS);
+    recip_pair_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, n, v.iPh, v.iPl);
+    q_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, n, psi, v.iPh, v.iPl, eps2_op_dev, op->beta,
+                                                op->d, alpha, q, v.qa);
+    d_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, n, v.iPh, v.iPl, v.qa, P, eps2_op_dev, D, S,
+                                                v.iS);
     mark(ctx, VB_STAGE_OPERATOR, 1);
     mark(ctx, VB_STAGE_LHAT, 0);
-    lhat_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, n, v.iP, v.qa, v.iS, S, eps2_op_dev,
-                                                   val);
+    lhat_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, n, v.iPh, v.iPl, v.qa, v.iS, S,
+                                                   eps2_op_dev, val);
     mark(ctx, VB_STAGE_LHAT, 1);
     ctx->launches += 4;
     return last_launch();

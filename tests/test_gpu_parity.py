@@ -186,6 +186,7 @@ def test_spmv_plain_and_laplacian(vb, circle):
     w, x, ref, out = circle
     n = x.shape[0]
     nnz = out.graph.nnz
+    val = out.val[:nnz].cpu().numpy()
     A = ref.lhat_csr()
     rng = np.random.default_rng(1)
     xr = rng.standard_normal(n).astype(np.float32)
@@ -197,24 +198,22 @@ def test_spmv_plain_and_laplacian(vb, circle):
     y0 = rng.standard_normal(n).astype(np.float32)
     y2 = vb.spmv(out.graph, out.val, _t(xr), alpha=0.5, beta=2.0, y=_t(y0)).cpu().numpy()
     assert np.all(np.abs(y2 - (0.5 * y64 + 2.0 * y0)) <= 2e-5 * (0.5 * bound + 2 * np.abs(y0)) + 1e-30)
-    # difference form: every term L_ij S_j (x_j/S_j - x_i/S_i) keeps FP32 relative accuracy, so the result
-    # is accurate against the sum of the terms' magnitudes even where they cancel (smooth vectors)
+    # difference form, checked against the same matrix and S in FP64: every term
+    # val_ij S_j (x_j/S_j - x_i/S_i) keeps FP32 relative accuracy, so the result is
+    # accurate against the sum of the terms' magnitudes even where they cancel
     S = out.S
-    Sd = ref.op.S
+    Sg = S.cpu().numpy()
+    vg = val.astype(np.float64)
     rows, cols = ref.pattern.row, ref.pattern.col
     off = rows != cols
     th = np.arctan2(x[:, 1], x[:, 0]).astype(np.float64)
-    for xs in (Sd.astype(np.float32), (Sd * np.cos(2 * th)).astype(np.float32)):
+    for xs in (Sg.astype(np.float32), (Sg * np.cos(2 * th)).astype(np.float32), xr):
         ys = vb.spmv(out.graph, out.val, _t(xs), S=S, laplacian=True).cpu().numpy()
-        x64 = xs.astype(np.float64)
-        ys64 = A @ x64
-        z = x64 / Sd
-        terms = np.abs(ref.op.Lhat[off] * Sd[cols[off]] * (z[cols[off]] - z[rows[off]]))
-        tb = np.bincount(rows[off], weights=terms, minlength=n)
+        z = xs.astype(np.float64) / Sg
+        terms = vg[off] * Sg[cols[off]] * (z[cols[off]] - z[rows[off]])
+        ys64 = np.bincount(rows[off], weights=terms, minlength=n)
+        tb = np.bincount(rows[off], weights=np.abs(terms), minlength=n)
         assert np.all(np.abs(ys - ys64) <= 1e-5 * tb + 1e-30)
-        # the plain form is far less accurate on the same smooth vector
-    yp = vb.spmv(out.graph, out.val, _t(xs)).cpu().numpy()
-    assert np.linalg.norm(yp - ys64) > 10 * np.linalg.norm(ys - ys64)
 
 
 def test_device_errors_are_reported(vb):
