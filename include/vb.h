@@ -230,6 +230,28 @@ size_t vb_spmv_workspace(int64_t n);
 vb_status vb_spmv(vb_ctx* ctx, const vb_graph* g, const float* val, const double* S, int32_t mode,
                   float alpha, const float* x, float beta, float* y, void* ws, size_t ws_bytes);
 
+/* Difference-form SpMV that allocates nothing and takes no workspace.  The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory, such as code that records an eigen-solver loop
+ * into a CUDA graph (cudaMalloc is not allowed during stream capture) or a
+ * host runtime that only lends this library buffers it already owns.  It
+ * computes what vb_spmv() computes in VB_SPMV_LAPLACIAN mode, on the given
+ * stream (a cudaStream_t; NULL = legacy default stream) of the current device.
+ *   - Scratch: one static device array inside libvb, sized for
+ *     VB_NOALLOC_MAX_N rows at 12 bytes per row (about 12.6 MB); every GPU
+ *     that loads the library holds it until the process exits.
+ *   - The first call on each device resolves the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make
+ *     that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents.
+ *     Nothing in it has to start at zero (each call overwrites every row it
+ *     reads), but calls whose work can overlap on the GPU (several streams,
+ *     several host threads) race on it: the caller must serialise them.
+ *   - g->n > VB_NOALLOC_MAX_N returns VB_ERR_UNSUPPORTED; use vb_spmv(). */
+#define VB_NOALLOC_MAX_N 1048576
+vb_status vb_spmv_laplacian_noalloc(void* stream, const vb_graph* g, const float* val, const double* S,
+                                    float alpha, const float* x, float beta, float* y);
+
 /* ------------------------------------------------- the whole build (a0-a13)
  * One call for Sec. 4 steps 1-3 up to L-hat: kNN, pattern, bandwidth,
  * density sweep, density, operator-sweep centre, operator sweep, L-hat.

@@ -22,6 +22,7 @@ VB_PREC_FP32 = 0
 VB_PRUNE_NONE, VB_PRUNE_EXACT = 0, 1
 VB_SPMV_PLAIN, VB_SPMV_LAPLACIAN = 0, 1
 XI_LO, XI_HI, DXI = -10.0, 4.0, 0.25
+VB_NOALLOC_MAX_N = 1 << 20   # rows vb_spmv_laplacian_noalloc accepts (its static scratch size)
 
 _STATUS = {0: "VB_OK", -1: "VB_ERR_ARG", -2: "VB_ERR_CUDA", -3: "VB_ERR_WORKSPACE", -4: "VB_ERR_DEGENERATE",
            -5: "VB_ERR_EPS_BOUNDARY", -6: "VB_ERR_NOT_CONVERGED", -7: "VB_ERR_TIMEOUT", -8: "VB_ERR_BOUNDS",
@@ -93,6 +94,7 @@ _SIGS = {
                               c_p, c_p, c_sz]),
     "vb_spmv_workspace": (c_sz, [c_i64]),
     "vb_spmv": (c_i32, [c_p, ctypes.POINTER(GraphC), c_p, c_p, c_i32, c_f32, c_p, c_f32, c_p, c_p, c_sz]),
+    "vb_spmv_laplacian_noalloc": (c_i32, [c_p, ctypes.POINTER(GraphC), c_p, c_p, c_f32, c_p, c_f32, c_p]),
     "vb_build_workspace": (c_sz, [c_i64, c_i32, ctypes.POINTER(BuildParams)]),
     "vb_build": (c_i32, [c_p, c_p, c_i64, c_i32, ctypes.POINTER(BuildParams), ctypes.POINTER(BuildOut), c_p, c_sz]),
 }

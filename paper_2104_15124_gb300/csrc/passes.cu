@@ -536,6 +536,16 @@ __global__ void __launch_bounds__(kRowThreads) spmv_lap_kernel(const int64_t* __
     }
 }
 
+// Laplacian-form SpMV with caller-chosen scratch (z: n FP64, sf: n FP32); used by
+// the entry point that owns its scratch in a static device array.
+vb_status spmv_lap_launch(cudaStream_t s, const vb_graph* g, const float* val, const double* S, float alpha,
+                          const float* x, float beta, float* y, double* z, float* sf)
+{
+    lap_prep_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(x, S, g->n, z, sf);
+    spmv_lap_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, val, g->n, alpha, z, sf, beta, y);
+    return last_launch();
+}
+
 size_t spmv_ws_bytes(int64_t n)
 {
     Carve c(nullptr);

@@ -120,6 +120,8 @@ vb_status kernel_csr_run(Ctx* ctx, const vb_graph* g, const double* psi, const d
                          const double* eps2_op_dev, float* val, double* q, double* D, double* S, void* ws,
                          size_t ws_bytes);
 size_t spmv_ws_bytes(int64_t n);
+vb_status spmv_lap_launch(cudaStream_t s, const vb_graph* g, const float* val, const double* S, float alpha,
+                          const float* x, float beta, float* y, double* z, float* sf);
 vb_status spmv_run(Ctx* ctx, const vb_graph* g, const float* val, const double* S, int mode, float alpha,
                    const float* x, float beta, float* y, void* ws, size_t ws_bytes);
 
