@@ -70,7 +70,7 @@ size_t knn_plan(Carve& c, int64_t n, int32_t m, const vb_knn_params*, KnnWs* w)
     t.tlo = c.take<float>(ntiles * mp);
     t.thi = c.take<float>(ntiles * mp);
     t.fb_list = c.take<int>(n);
-    t.fb_count = c.take<int>(1);
+    t.fb_count = c.take<int>(2);   // [0] fallback rows, [1] next query tile
     if (w) *w = t;
     return c.off;
 }
@@ -88,7 +88,7 @@ __global__ void bbox_init_kernel(int* bbox, int* fb_count)
     int t = threadIdx.x;
     if (t < 4) bbox[t] = 0x7fffffff;
     else if (t < 8) bbox[t] = (int)0x80000000;
-    if (t == 0) *fb_count = 0;
+    if (t == 0) { fb_count[0] = 0; fb_count[1] = 0; }
 }
 
 // Bounding box of the Morton coordinates; also rejects non-finite input.
@@ -274,18 +274,49 @@ struct TileArgs {
     const uint32_t* perm;
     int64_t n;
     int64_t ntiles;
-    int m, k, L, prune;
+    int m, k, L, prune, nseed;
     float lb_factor;     // 1 - 4 (m + 2) 2^-24, applied rounding down
+    float band;          // 1 + 4 (m + 2) 2^-24: FP32 distances closer than this may swap in FP64
     double cert_factor;  // 1 - 2 (m + 2) 2^-24
     int32_t* nbr;
     double* nbr_d2;
     int* fb_list;
     int* fb_count;
+    int* work;           // next query tile (persistent grid)
     DevReport* rep;
 };
 
+constexpr int IB = 16;        // candidates per insertion batch
+constexpr int SCAP = 512;     // candidate tiles per sorted chunk
+constexpr int RUN = 8;        // longest run of FP32-indistinguishable neighbours ordered in registers
+
+// Sift key down from node i of the max-heap heap[0..size) (column t of a [.][TILE] array).
+__device__ __forceinline__ void sift_down(uint64_t* heap, int t, int i, int size, uint64_t key)
+{
+    for (;;) {
+        int l = 2 * i + 1;
+        if (l >= size) break;
+        uint64_t ck = heap[l * TILE + t];
+        int ch = l;
+        if (l + 1 < size) {
+            uint64_t rk = heap[(l + 1) * TILE + t];
+            if (rk > ck) { ck = rk; ch = l + 1; }
+        }
+        if (ck <= key) break;
+        heap[i * TILE + t] = ck;
+        i = ch;
+    }
+    heap[i * TILE + t] = key;
+}
+
+// Floyd's bottom-up construction of a max-heap over heap[0..size).
+__device__ __forceinline__ void heapify(uint64_t* heap, int t, int size)
+{
+    for (int i = size / 2 - 1; i >= 0; --i) sift_down(heap, t, i, size, heap[i * TILE + t]);
+}
+
 template <int MP>
-__device__ __forceinline__ float box_gap2(const float* q, const float* lo, const float* hi)
+__device__ __forceinline__ float point_box_lb(const float* q, const float* lo, const float* hi)
 {
     float acc = 0.f;
 #pragma unroll
@@ -296,215 +327,269 @@ __device__ __forceinline__ float box_gap2(const float* q, const float* lo, const
     return acc;
 }
 
-// Query tile per CTA (64 threads, one query each).  Shared memory:
-//   heap  [L][64] uint64   max-heaps, one column per query
-//   cand  [64][MP] float   staged candidate tile
-//   qs    [MP][64] float   query coordinates (only when MP > 16)
-//   sd/so [2][L]           per-warp rescoring scratch
+// Query tiles are taken from a global counter by a persistent grid of 64-thread
+// CTAs, one query per thread.  Shared memory:
+//   heap  [L][64]  u64  max-heap per query of keys (FP32 distance bits << 32 | sorted position)
+//   buf   [IB][64] u64  per-thread batch of keys that passed the heap threshold
+//   cand  [64][MP] f32  staged candidate tile
+//   qs    [MP][64] f32  query coordinates (MP > 16 only)
+//   slist [SCAP]   u64  surviving candidate tiles keyed (box lower bound bits << 32 | tile)
 template <int MP>
 __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int L = a.L;
     uint64_t* heap = (uint64_t*)smem;
-    float* cand = (float*)(heap + (size_t)L * TILE);
+    uint64_t* buf = heap + (size_t)L * TILE;
+    uint64_t* slist = buf + IB * TILE;
+    float* cand = (float*)(slist + SCAP);
     float* qs = cand + TILE * MP;
-    uint64_t* sd = (uint64_t*)(qs + (MP > 16 ? TILE * MP : 0));
-    uint32_t* so = (uint32_t*)(sd + 2 * L);
     __shared__ float sqlo[MP], sqhi[MP];
-    __shared__ int slist[TILE];
-    __shared__ float slb[TILE];
-    __shared__ uint32_t sthr[2];
+    __shared__ uint32_t sred[2];
+    __shared__ int s_tile, s_cnt;
 
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int64_t qt = blockIdx.x;
-    const int64_t p = qt * TILE + t;
-    const bool valid = p < a.n;
     constexpr bool QREG = MP <= 16;
-
-    float qr[QREG ? MP : 1];
-    if constexpr (QREG) {
-#pragma unroll
-        for (int r = 0; r < MP; ++r) qr[r] = a.xs[p * MP + r];
-    } else {
-        for (int r = 0; r < MP; ++r) qs[r * TILE + t] = a.xs[p * MP + r];
-    }
-    for (int s = 0; s < L; ++s) heap[s * TILE + t] = ~0ull;
-    for (int r = t; r < MP; r += TILE) {
-        sqlo[r] = a.tlo[qt * MP + r];
-        sqhi[r] = a.thi[qt * MP + r];
-    }
-    uint64_t maxkey = ~0ull;
-    uint32_t thr_blk = 0xffffffffu;   // float bits of the tile's running threshold (+inf as 0xffffffff)
-    unsigned long long evaluated = 0;
-    __syncthreads();
-
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t nt = a.ntiles;
-    for (int64_t o0 = 0; o0 < 2 * nt; o0 += TILE) {
-        // tile order: own tile, then +1, -1, +2, -2, ...
-        int64_t o = o0 + t;
-        int64_t ct = -1;
-        if (o == 0) ct = qt;
-        else if (o < 2 * nt) {
-            int64_t s = (o + 1) >> 1;
-            ct = (o & 1) ? qt + s : qt - s;
-            if (ct < 0 || ct >= nt) ct = -1;
-        }
-        float lb = 0.f;
-        bool keep = ct >= 0;
-        if (keep && a.prune) {
-            float acc = 0.f;
-            for (int r = 0; r < MP; ++r) {
-                float g = fmaxf(fmaxf(a.tlo[ct * MP + r] - sqhi[r], sqlo[r] - a.thi[ct * MP + r]), 0.f);
-                acc = fmaf(g, g, acc);
-            }
-            lb = __fmul_rd(acc, a.lb_factor);
-            keep = __float_as_uint(lb) <= thr_blk;
-        }
-        // compact the surviving tiles in order
-        unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0) sthr[warp] = __popc(bal);
+    unsigned long long evaluated = 0;
+
+    for (;;) {
+        if (t == 0) s_tile = atomicAdd(a.work, 1);
         __syncthreads();
-        int pos = __popc(bal & ((1u << lane) - 1u)) + (warp ? sthr[0] : 0);
-        if (keep) { slist[pos] = (int)ct; slb[pos] = lb; }
-        int total = sthr[0] + sthr[1];
+        const int64_t qt = s_tile;
+        if (qt >= nt) break;
+        const int64_t p = qt * TILE + t;
+        const bool valid = p < a.n;
+        float qr[QREG ? MP : 1];
+        if constexpr (QREG) {
+#pragma unroll
+            for (int r = 0; r < MP; ++r) qr[r] = a.xs[p * MP + r];
+        } else {
+            for (int r = 0; r < MP; ++r) qs[r * TILE + t] = a.xs[p * MP + r];
+        }
+        for (int sl = 0; sl < L; ++sl) heap[sl * TILE + t] = ~0ull;
+        for (int r = t; r < MP; r += TILE) {
+            sqlo[r] = a.tlo[qt * MP + r];
+            sqhi[r] = a.thi[qt * MP + r];
+        }
+        uint64_t maxkey = ~0ull;
+        int fill = 0;               // keys stored so far; the heap is ordered once it holds L
+        uint32_t thr_blk = 0xffffffffu;
         __syncthreads();
 
-        for (int si = 0; si < total; ++si) {
-            if (a.prune && __float_as_uint(slb[si]) > thr_blk) continue;   // block-uniform
-            const int64_t c0 = (int64_t)slist[si] * TILE;
-            {   // stage the candidate tile
-                const float4* src = (const float4*)(a.xs + c0 * MP);
-                float4* dst = (float4*)cand;
-                for (int i = t; i < TILE * MP / 4; i += TILE) dst[i] = src[i];
-            }
-            __syncthreads();
-            bool skip = !valid;
-            if (!skip && a.prune) {
-                const float* clo = a.tlo + (int64_t)slist[si] * MP;
-                const float* chi = a.thi + (int64_t)slist[si] * MP;
-                float acc = 0.f;
+        // Visit candidate tile ct for every query of this tile that may still gain from it.
+        auto visit = [&](int64_t ct) {
+            const float* clo = a.tlo + ct * MP;
+            const float* chi = a.thi + ct * MP;
+            bool need = valid;
+            if (need && a.prune) {
+                float lb;
                 if constexpr (QREG) {
-#pragma unroll
-                    for (int r = 0; r < MP; ++r) {
-                        float g = fmaxf(fmaxf(clo[r] - qr[r], qr[r] - chi[r]), 0.f);
-                        acc = fmaf(g, g, acc);
-                    }
+                    lb = point_box_lb<MP>(qr, clo, chi);
                 } else {
+                    float acc = 0.f;
                     for (int r = 0; r < MP; ++r) {
                         float qv = qs[r * TILE + t];
                         float g = fmaxf(fmaxf(clo[r] - qv, qv - chi[r]), 0.f);
                         acc = fmaf(g, g, acc);
                     }
+                    lb = acc;
                 }
-                skip = __float_as_uint(__fmul_rd(acc, a.lb_factor)) > (uint32_t)(maxkey >> 32);
+                need = __float_as_uint(__fmul_rd(lb, a.lb_factor)) <= (uint32_t)(maxkey >> 32);
             }
-            if (!skip) {
+            if (!__syncthreads_or(need)) return;
+            {
+                const float4* src = (const float4*)(a.xs + ct * TILE * MP);
+                float4* dst = (float4*)cand;
+                for (int i = t; i < TILE * MP / 4; i += TILE) dst[i] = src[i];
+            }
+            __syncthreads();
+            if (need) {
                 evaluated += TILE;
-                for (int c = 0; c < TILE; ++c) {
-                    float acc = 0.f;
-                    if constexpr (QREG) {
-                        const float4* cv = (const float4*)(cand + c * MP);
+                const int64_t c0 = ct * TILE;
+                for (int cb = 0; cb < TILE; cb += IB) {
+                    // distances of one batch; keys under the current threshold go to buf
+                    int cnt = 0;
+                    const uint64_t thr = maxkey;
+#pragma unroll 4
+                    for (int c = cb; c < cb + IB; ++c) {
+                        float acc = 0.f;
+                        if constexpr (QREG) {
+                            const float4* cv = (const float4*)(cand + c * MP);
 #pragma unroll
-                        for (int r4 = 0; r4 < MP / 4; ++r4) {
-                            float4 v = cv[r4];
-                            float d0 = qr[4 * r4 + 0] - v.x, d1 = qr[4 * r4 + 1] - v.y;
-                            float d2 = qr[4 * r4 + 2] - v.z, d3 = qr[4 * r4 + 3] - v.w;
-                            acc = fmaf(d0, d0, acc);
-                            acc = fmaf(d1, d1, acc);
-                            acc = fmaf(d2, d2, acc);
-                            acc = fmaf(d3, d3, acc);
-                        }
-                    } else {
-                        for (int r = 0; r < MP; ++r) {
-                            float d = qs[r * TILE + t] - cand[c * MP + r];
-                            acc = fmaf(d, d, acc);
-                        }
-                    }
-                    const int64_t cp = c0 + c;
-                    uint64_t key = ((uint64_t)__float_as_uint(acc) << 32) | (uint32_t)cp;
-                    if (key < maxkey && cp != p && cp < a.n) {
-                        // replace the root of the max-heap and sift down
-                        int i = 0;
-                        for (;;) {
-                            int l = 2 * i + 1;
-                            if (l >= L) break;
-                            uint64_t ck = heap[l * TILE + t];
-                            int ch = l;
-                            if (l + 1 < L) {
-                                uint64_t rk = heap[(l + 1) * TILE + t];
-                                if (rk > ck) { ck = rk; ch = l + 1; }
+                            for (int r4 = 0; r4 < MP / 4; ++r4) {
+                                float4 v = cv[r4];
+                                float d0 = qr[4 * r4 + 0] - v.x, d1 = qr[4 * r4 + 1] - v.y;
+                                float d2 = qr[4 * r4 + 2] - v.z, d3 = qr[4 * r4 + 3] - v.w;
+                                acc = fmaf(d0, d0, acc);
+                                acc = fmaf(d1, d1, acc);
+                                acc = fmaf(d2, d2, acc);
+                                acc = fmaf(d3, d3, acc);
                             }
-                            if (ck <= key) break;
-                            heap[i * TILE + t] = ck;
-                            i = ch;
+                        } else {
+                            for (int r = 0; r < MP; ++r) {
+                                float d = qs[r * TILE + t] - cand[c * MP + r];
+                                acc = fmaf(d, d, acc);
+                            }
                         }
-                        heap[i * TILE + t] = key;
+                        const int64_t cp = c0 + c;
+                        const uint64_t key = ((uint64_t)__float_as_uint(acc) << 32) | (uint32_t)cp;
+                        const bool take = key < thr && cp != p && cp < a.n;
+                        if (take) buf[cnt * TILE + t] = key;
+                        cnt += take;
+                    }
+                    for (int b = 0; b < cnt; ++b) {
+                        const uint64_t key = buf[b * TILE + t];
+                        if (fill < L) {   // first L keys: append, then order them in one pass
+                            heap[fill * TILE + t] = key;
+                            if (++fill == L) {
+                                heapify(heap, t, L);
+                                maxkey = heap[t];
+                            }
+                            continue;
+                        }
+                        if (key >= maxkey) continue;
+                        sift_down(heap, t, 0, L, key);   // replace the root
                         maxkey = heap[t];
                     }
                 }
             }
-            // block threshold = max over valid queries of their heap maxima
+            // tile threshold = largest heap maximum among the tile's valid queries
             uint32_t mine = valid ? (uint32_t)(maxkey >> 32) : 0u;
             uint32_t wmax = __reduce_max_sync(0xffffffffu, mine);
+            if (lane == 0) sred[warp] = wmax;
             __syncthreads();
-            if (lane == 0) sthr[warp] = wmax;
+            thr_blk = max(sred[0], sred[1]);
             __syncthreads();
-            thr_blk = max(sthr[0], sthr[1]);
-        }
-        __syncthreads();
-    }
+        };
 
-    // ---------------- a5: FP64 rescoring, exact ranking and certificate (warp w: queries 32w .. 32w+31)
-    unsigned long long ev = evaluated;
+        // seed: the tile itself and its neighbours in Morton order
+        for (int sidx = 0; sidx < a.nseed; ++sidx) {
+            int64_t s2 = (sidx + 1) >> 1;
+            int64_t ct = (sidx & 1) ? qt + s2 : qt - s2;
+            if (ct >= 0 && ct < nt) visit(ct);
+        }
+        // every other tile whose box lower bound does not exceed the threshold, nearest first
+        for (int64_t c0 = 0; c0 < nt;) {
+            if (t == 0) s_cnt = 0;
+            __syncthreads();
+            for (; c0 < nt; c0 += TILE) {
+                const int64_t ct = c0 + t;
+                bool keep = ct < nt;
+                if (keep) {
+                    const int64_t dct = ct - qt;
+                    keep = (dct > (a.nseed >> 1) || dct < -((a.nseed - 1) >> 1));   // not a seed tile
+                }
+                float lb = 0.f;
+                if (keep) {
+                    float acc = 0.f;
+                    for (int r = 0; r < MP; ++r) {
+                        float g = fmaxf(fmaxf(a.tlo[ct * MP + r] - sqhi[r], sqlo[r] - a.thi[ct * MP + r]), 0.f);
+                        acc = fmaf(g, g, acc);
+                    }
+                    lb = __fmul_rd(acc, a.lb_factor);
+                    keep = !a.prune || __float_as_uint(lb) <= thr_blk;
+                }
+                unsigned bal = __ballot_sync(0xffffffffu, keep);
+                if (lane == 0 && bal) sred[warp] = atomicAdd(&s_cnt, __popc(bal));
+                __syncwarp();
+                if (keep) slist[sred[warp] + __popc(bal & ((1u << lane) - 1u))] = ((uint64_t)__float_as_uint(lb) << 32) | (uint32_t)ct;
+                __syncthreads();
+                if (s_cnt > SCAP - TILE) { c0 += TILE; break; }
+            }
+            const int cnt = s_cnt;
+            int P = 1;
+            while (P < cnt) P <<= 1;
+            for (int i = cnt + t; i < P; i += TILE) slist[i] = ~0ull;
+            __syncthreads();
+            for (int size = 2; size <= P; size <<= 1) {
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    for (int i = t; i < P / 2; i += TILE) {
+                        int lo = 2 * i - (i & (stride - 1));
+                        int hi = lo + stride;
+                        bool up = (lo & size) == 0;
+                        uint64_t x = slist[lo], y = slist[hi];
+                        if ((x > y) == up) { slist[lo] = y; slist[hi] = x; }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (int si = 0; si < cnt; ++si) {
+                const uint64_t e = slist[si];
+                if (a.prune && (uint32_t)(e >> 32) > thr_blk) break;   // sorted: the rest lie farther
+                visit((int64_t)(uint32_t)e);
+            }
+            __syncthreads();
+        }
+
+        // ---------------- a5: order the kept candidates, rescore in FP64, certify
+        const int64_t pq = p;
+        if (valid) {
+            // in-place heap sort: ascending (FP32 distance, sorted position)
+            if (fill < L) heapify(heap, t, L);   // fewer than L candidates: unused slots hold ~0
+            for (int e = L - 1; e > 0; --e) {
+                const uint64_t top = heap[t];
+                const uint64_t key = heap[e * TILE + t];
+                heap[e * TILE + t] = top;
+                sift_down(heap, t, 0, e, key);
+            }
+            const uint64_t Hkey = heap[(L - 1) * TILE + t];
+            const uint32_t oq = a.perm[pq];
+            const float* qc = a.xs + pq * MP;
+            double rd[RUN];
+            uint32_t ro[RUN];
+            int rlen = 0, out = 0;
+            float run_last = 0.f;
+            bool ok = true;
+            double dk = 0.0;
+            auto emit = [&]() {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
-    if (lane == 0 && ev) atomicAdd(&a.rep->knn_candidates, ev);
-
-    uint64_t* wsd = sd + warp * L;
-    uint32_t* wso = so + warp * L;
-    for (int qq = 0; qq < 32; ++qq) {
-        const int tq = warp * 32 + qq;
-        const int64_t pq = qt * TILE + tq;
-        if (pq >= a.n) break;
-        const uint64_t root = heap[tq];
-        const uint32_t oq = a.perm[pq];
-        const float* qc = a.xs + pq * MP;
-        for (int s = lane; s < L; s += 32) {
-            uint64_t key = heap[s * TILE + tq];
-            uint64_t db = ~0ull;
-            uint32_t oj = 0xffffffffu;
-            if (key != ~0ull) {
-                uint32_t cp = (uint32_t)key;
-                oj = a.perm[cp];
-                db = (uint64_t)__double_as_longlong(canon_d2(qc, a.xs + (int64_t)cp * MP, a.m));
+                for (int u = 0; u < RUN; ++u) {
+                    if (u < rlen && out < a.k) {
+                        a.nbr[(int64_t)oq * a.k + out] = (int32_t)ro[u];
+                        a.nbr_d2[(int64_t)oq * a.k + out] = rd[u];
+                        if (out == a.k - 1) dk = rd[u];
+                        ++out;
+                    }
+                }
+                rlen = 0;
+            };
+            for (int r = 0; r < L; ++r) {
+                const uint64_t key = heap[r * TILE + t];
+                if (key == ~0ull) break;
+                const float df = __uint_as_float((uint32_t)(key >> 32));
+                // a new run starts once the FP32 distance clears the error band (tiny distances,
+                // where FP32 may have underflowed, all stay in one run)
+                if (rlen > 0 && df > run_last * a.band && df > 1e-30f) {
+                    emit();
+                    if (out >= a.k) break;
+                }
+                if (rlen == RUN) { ok = false; break; }
+                const uint32_t cp = (uint32_t)key;
+                const uint32_t oj = a.perm[cp];
+                const double dj = canon_d2(qc, a.xs + (int64_t)cp * MP, a.m);
+                // insert (dj, oj) into the run, kept sorted by (d2, index)
+#pragma unroll
+                for (int u = 0; u < RUN; ++u)
+                    if (u == rlen) { rd[u] = dj; ro[u] = oj; }
+#pragma unroll
+                for (int u = RUN - 1; u > 0; --u) {
+                    if (u <= rlen && (rd[u] < rd[u - 1] || (rd[u] == rd[u - 1] && ro[u] < ro[u - 1]))) {
+                        double td = rd[u]; rd[u] = rd[u - 1]; rd[u - 1] = td;
+                        uint32_t to = ro[u]; ro[u] = ro[u - 1]; ro[u - 1] = to;
+                    }
+                }
+                ++rlen;
+                run_last = df;
             }
-            wsd[s] = db;
-            wso[s] = oj;
-        }
-        __syncwarp();
-        double dk = -1.0;
-        for (int s = lane; s < L; s += 32) {
-            const uint64_t ds = wsd[s];
-            const uint32_t os = wso[s];
-            int rank = 0;
-            for (int u = 0; u < L; ++u) {
-                uint64_t du = wsd[u];
-                rank += (du < ds) || (du == ds && wso[u] < os);
-            }
-            if (rank < a.k) {
-                a.nbr[(int64_t)oq * a.k + rank] = (int32_t)os;
-                a.nbr_d2[(int64_t)oq * a.k + rank] = __longlong_as_double((long long)ds);
-            }
-            if (rank == a.k - 1) dk = __longlong_as_double((long long)ds);
-        }
-        // certificate, evaluated by the lane holding rank k-1
-        if (dk >= 0.0) {
-            bool ok;
-            if (a.n - 1 <= (int64_t)L || root == ~0ull) ok = true;   // every candidate was kept
-            else {
-                float H = __uint_as_float((uint32_t)(root >> 32));
-                ok = isfinite(H) && dk < (double)H * a.cert_factor - (double)a.m * 1.1754943508222875e-38;
+            if (ok && out < a.k) emit();
+            if (ok) {
+                if (out < a.k) ok = false;   // cannot happen when n - 1 >= k; kept as a guard
+                else if (a.n - 1 > (int64_t)L && Hkey != ~0ull) {
+                    // candidates outside the heap have FP32 distance >= H: certify the k-th
+                    const float H = __uint_as_float((uint32_t)(Hkey >> 32));
+                    ok = isfinite(H) && dk < (double)H * a.cert_factor - (double)a.m * 1.1754943508222875e-38;
+                }
             }
             if (!ok) {
                 int slot = atomicAdd(a.fb_count, 1);
@@ -512,8 +597,12 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
                 atomicAdd(&a.rep->knn_fallback_rows, 1ull);
             }
         }
-        __syncwarp();
+        __syncthreads();
     }
+    unsigned long long ev = evaluated;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    if (lane == 0 && ev) atomicAdd(&a.rep->knn_candidates, ev);
 }
 
 // ------------------------------------------------------------------ exact FP64 fallback rows
@@ -611,7 +700,7 @@ __global__ void __launch_bounds__(FB_THREADS) knn_fallback_kernel(const float* _
 template <int MP>
 static size_t tile_smem(int L)
 {
-    return (size_t)L * TILE * 8 + TILE * MP * 4 + (MP > 16 ? TILE * MP * 4 : 0) + 2 * (size_t)L * 12;
+    return (size_t)L * TILE * 8 + IB * TILE * 8 + SCAP * 8 + TILE * MP * 4 + (MP > 16 ? TILE * MP * 4 : 0);
 }
 
 template <int MP>
@@ -669,7 +758,10 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
     TileArgs a;
     a.xs = w.xs; a.tlo = w.tlo; a.thi = w.thi; a.perm = perm; a.n = n; a.ntiles = ntiles;
     a.m = m; a.k = p->k; a.L = p->k + p->margin; a.prune = p->prune != VB_PRUNE_NONE;
+    a.nseed = 1 + 2 * (int)((a.L + TILE) / TILE);   // enough neighbouring tiles to fill every heap
     a.lb_factor = 1.0f - 4.0f * (float)(m + 2) * 5.9604645e-8f;
+    a.band = 1.0f + 4.0f * (float)(m + 2) * 5.9604645e-8f;
+    a.work = w.fb_count + 1;
     a.cert_factor = 1.0 - 2.0 * (double)(m + 2) * 5.9604644775390625e-8;
     a.nbr = nbr; a.nbr_d2 = nbr_d2; a.fb_list = w.fb_list; a.fb_count = w.fb_count; a.rep = ctx->rep;
     mark(ctx, VB_STAGE_KNN_TILE, 0);
