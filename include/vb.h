@@ -252,6 +252,36 @@ vb_status vb_spmv(vb_ctx* ctx, const vb_graph* g, const float* val, const double
 vb_status vb_spmv_laplacian_noalloc(void* stream, const vb_graph* g, const float* val, const double* S,
                                     float alpha, const float* x, float beta, float* y);
 
+/* ------------------------------------ eigenpairs and spectral solve (boundary)
+ * Sec. 2.2 and Sec. 4 step 3: the ell + 1 largest eigenvalues
+ * 0 ~ lambda_0 > lambda_1 >= ... of L (those of L-hat, Eq. symmetric discrete
+ * Kolmogorov operator) and the eigenvectors phi_j = S^-1 phi-hat_j, normalised
+ * so that <phi_i, phi_j>_S = delta_ij with <f, g>_S = f^T S^2 g / n (Eq. inner
+ * product), i.e. phi-hat_i^T phi-hat_j = n delta_ij.  Sec. 3.1 (Eqs. LS
+ * minimiser and f_LS), when g_rhs and f are given: f = sum_{j=1..ell}
+ * (<phi_j, g>_S / lambda_j) phi_j, lambda_0 excluded.
+ * Method: block Chebyshev-filtered subspace iteration on L in the coordinates
+ * z = S^-1 x, where (L z)_i = sum_{j != i} w_ij (z_j - z_i) with
+ * w_ij = L-hat_ij S_j / S_i, so FP32 differences keep smooth vectors exact;
+ * Rayleigh-Ritz in FP64 on the host.  Synchronises the host.
+ * val, S: from vb_kernel_csr (cap = capacity of val); evals: ell + 1 FP64
+ * (device); phi: (ell + 1) x n FP32 (device, eigenvector j contiguous) or
+ * NULL; g_rhs, f: n FP32 (device) or NULL; iters: host int32 or NULL.
+ * Returns VB_ERR_NOT_CONVERGED (outputs still written) when max_iter ran out. */
+typedef struct {
+    int32_t ell;        /* nonzero eigenpairs wanted (ell + 1 are computed), ell >= 1 */
+    int32_t block;      /* subspace size, multiple of 32, <= 128 (0 = max(2 (ell + 1), ell + 17) rounded up) */
+    int32_t degree;     /* Chebyshev filter degree per iteration (0 = 30) */
+    int32_t max_iter;   /* outer iterations (0 = 60) */
+    double tol;         /* stop once the wanted Ritz values move by < tol * max |lambda_j| twice (0 = 1e-7) */
+    uint64_t seed;      /* initial block */
+} vb_solve_params;
+
+size_t vb_solve_workspace(int64_t n, int64_t cap, const vb_solve_params* p);
+vb_status vb_solve(vb_ctx* ctx, const vb_graph* g, int64_t cap, const float* val, const double* S,
+                   const vb_solve_params* p, double* evals, float* phi, const float* g_rhs, float* f,
+                   int32_t* iters, void* ws, size_t ws_bytes);
+
 /* ------------------------------------------------- the whole build (a0-a13)
  * One call for Sec. 4 steps 1-3 up to L-hat: kNN, pattern, bandwidth,
  * density sweep, density, operator-sweep centre, operator sweep, L-hat.

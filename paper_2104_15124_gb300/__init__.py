@@ -63,6 +63,11 @@ class BuildOut(ctypes.Structure):
                                    "dim_op", "val", "q", "D", "S")]
 
 
+class SolveParams(ctypes.Structure):
+    _fields_ = [("ell", c_i32), ("block", c_i32), ("degree", c_i32), ("max_iter", c_i32), ("tol", c_f64),
+                ("seed", ctypes.c_uint64)]
+
+
 class Report(ctypes.Structure):
     _fields_ = [("error", c_i32), ("warnings", c_i32), ("knn_fallback_rows", c_i64), ("knn_candidates", c_i64),
                 ("union_big_rows", c_i64), ("reserved", c_i64 * 4)]
@@ -95,6 +100,9 @@ _SIGS = {
     "vb_spmv_workspace": (c_sz, [c_i64]),
     "vb_spmv": (c_i32, [c_p, ctypes.POINTER(GraphC), c_p, c_p, c_i32, c_f32, c_p, c_f32, c_p, c_p, c_sz]),
     "vb_spmv_laplacian_noalloc": (c_i32, [c_p, ctypes.POINTER(GraphC), c_p, c_p, c_f32, c_p, c_f32, c_p]),
+    "vb_solve_workspace": (c_sz, [c_i64, c_i64, ctypes.POINTER(SolveParams)]),
+    "vb_solve": (c_i32, [c_p, ctypes.POINTER(GraphC), c_i64, c_p, c_p, ctypes.POINTER(SolveParams), c_p, c_p, c_p,
+                         c_p, ctypes.POINTER(c_i32), c_p, c_sz]),
     "vb_build_workspace": (c_sz, [c_i64, c_i32, ctypes.POINTER(BuildParams)]),
     "vb_build": (c_i32, [c_p, c_p, c_i64, c_i32, ctypes.POINTER(BuildParams), ctypes.POINTER(BuildOut), c_p, c_sz]),
 }
@@ -308,6 +316,33 @@ def spmv(g: Graph, val: torch.Tensor, x: torch.Tensor, S: torch.Tensor | None = 
     _check(lib().vb_spmv(c_p(_ctx(dev)), ctypes.byref(gc), _p(val), _p(S), VB_SPMV_LAPLACIAN if laplacian else
                          VB_SPMV_PLAIN, alpha, _p(x), beta, _p(y), _p(ws), 0 if ws is None else ws.numel()), "vb_spmv")
     return y
+
+
+@dataclasses.dataclass
+class Eigen:
+    evals: torch.Tensor        # [ell + 1] FP64, descending (lambda_0 ~ 0 first)
+    phi: torch.Tensor          # [ell + 1, n] FP32, <phi_i, phi_j>_S = delta_ij
+    f: torch.Tensor | None     # [n] FP32 spectral solution of L f = g, when g was given
+    iters: int
+    converged: bool
+
+
+def solve(g: Graph, val: torch.Tensor, S: torch.Tensor, ell: int, rhs: torch.Tensor | None = None,
+          block: int = 0, degree: int = 0, max_iter: int = 0, tol: float = 0.0, seed: int = 1) -> Eigen:
+    """Leading eigenpairs of L and, with rhs, the spectral solve of L f = g (vb_solve)."""
+    dev = val.device
+    p = SolveParams(ell, block, degree, max_iter, tol, seed)
+    evals = torch.empty(ell + 1, dtype=torch.float64, device=dev)
+    phi = torch.empty((ell + 1, g.n), dtype=torch.float32, device=dev)
+    f = torch.empty(g.n, dtype=torch.float32, device=dev) if rhs is not None else None
+    it = c_i32()
+    ws = _ws(lib().vb_solve_workspace(g.n, val.numel(), ctypes.byref(p)), dev)
+    gc = g.c()
+    rc = lib().vb_solve(c_p(_ctx(dev)), ctypes.byref(gc), val.numel(), _p(val), _p(S), ctypes.byref(p), _p(evals),
+                        _p(phi), _p(rhs), _p(f), ctypes.byref(it), _p(ws), ws.numel())
+    if rc not in (0, -6):
+        _check(rc, "vb_solve")
+    return Eigen(evals, phi, f, int(it.value), rc == 0)
 
 
 @dataclasses.dataclass

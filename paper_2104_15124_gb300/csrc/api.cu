@@ -255,6 +255,18 @@ vb_status vb_spmv(vb_ctx* ctx, const vb_graph* gr, const float* val, const doubl
     return spmv_run(C(ctx), gr, val, S, mode, alpha, x, beta, y, ws, ws_bytes);
 }
 
+size_t vb_solve_workspace(int64_t n, int64_t cap, const vb_solve_params* p) { return solve_ws_bytes(n, cap, p); }
+
+vb_status vb_solve(vb_ctx* ctx, const vb_graph* gr, int64_t cap, const float* val, const double* S,
+                   const vb_solve_params* p, double* evals, float* phi, const float* g_rhs, float* f, int32_t* iters,
+                   void* ws, size_t ws_bytes)
+{
+    if (!ctx) return VB_ERR_ARG;
+    DeviceGuard g(C(ctx)->device);
+    if (!g.ok) return VB_ERR_CUDA;
+    return solve_run(C(ctx), gr, cap, val, S, p, evals, phi, g_rhs, f, iters, ws, ws_bytes);
+}
+
 size_t vb_build_workspace(int64_t n, int32_t m, const vb_build_params* p)
 {
     if (!p) return 0;

@@ -125,6 +125,12 @@ vb_status spmv_lap_launch(cudaStream_t s, const vb_graph* g, const float* val, c
 vb_status spmv_run(Ctx* ctx, const vb_graph* g, const float* val, const double* S, int mode, float alpha,
                    const float* x, float beta, float* y, void* ws, size_t ws_bytes);
 
+// eigen-solve (solve.cu)
+size_t solve_ws_bytes(int64_t n, int64_t cap, const vb_solve_params* p);
+vb_status solve_run(Ctx* ctx, const vb_graph* g, int64_t cap, const float* val, const double* S,
+                    const vb_solve_params* p, double* evals, float* phi, const float* rhs, float* f, int32_t* iters,
+                    void* ws, size_t ws_bytes);
+
 // exclusive scan of n int32 counts into n + 1 int64 offsets (graph.cu)
 size_t scan_ws_bytes(int64_t n);
 vb_status scan_counts(cudaStream_t s, const int32_t* counts, int64_t n, int64_t* out, void* ws);
