@@ -74,7 +74,13 @@ typedef struct {
     int64_t knn_fallback_rows;  /* kNN rows whose FP32 candidate list failed the FP64 certificate */
     int64_t knn_candidates;     /* (query, candidate) distances evaluated by the tiled search */
     int64_t union_big_rows;     /* rows of the symmetric union longer than the warp path's limit */
-    int64_t reserved[4];
+    int64_t knn_heap_levels;    /* heap levels walked by the kNN selection (inserts and final sort) */
+    int64_t knn_tiles_staged;   /* candidate tiles staged in shared memory by the kNN search */
+    int64_t knn_insert_rounds;  /* per-query insertion rounds executed by the kNN search */
+    int64_t knn_retry_tiles;    /* query tiles the radius-first search handed back to the exact search */
+    int64_t knn_rows_short;     /* rows with fewer than k candidates kept (radius too small) */
+    int64_t knn_rows_long_run;  /* rows whose FP32/16-bit ties or error band exceeded the exact-order buffer */
+    int64_t knn_rows_uncertified; /* rows whose k-th FP64 distance did not clear the certificate bound */
 } vb_report;
 
 /* Waits for the context's stream and copies the device report to *out. */
@@ -115,15 +121,30 @@ vb_status vb_profile_read(vb_ctx* ctx, float* ms, int64_t* launches);
  * rows that fail it are recomputed by an exact FP64 radix selection.  The
  * output is therefore exact, identical to a brute-force FP64 search. */
 
-#define VB_PREC_FP32 0    /* FP32 ALU distances */
-#define VB_PRUNE_NONE  0  /* visit every candidate tile (brute force) */
-#define VB_PRUNE_EXACT 1  /* skip tiles whose box distance exceeds the running k+margin-th distance */
+#define VB_PREC_FP32 0      /* FP32 ALU distances */
+#define VB_PREC_BF16 1      /* BF16 tensor-core distance tiles (tcgen05.mma, FP32 accumulation) with FP64 rescoring;
+                               radius-first search (VB_PRUNE_LEARNED) only */
+#define VB_PREC_FP16 2      /* the same with FP16 tiles (11-bit significand: an 8x narrower error band) */
+#define VB_PRUNE_NONE    0  /* visit every candidate tile (brute force) */
+#define VB_PRUNE_EXACT   1  /* skip tiles whose box distance exceeds the running k+margin-th distance */
+#define VB_PRUNE_LEARNED 2  /* radius-first search: every query's heap starts full of sentinels at its radius
+                               guess, so tiles and candidates outside it are pruned from the start and no seed
+                               tiles are needed; tiles with a row that finds fewer than k points inside its
+                               radius, or fails the certificate, are redone by the exact search, so the output
+                               stays exact */
+
+typedef struct vb_mlp vb_mlp;
 
 typedef struct {
-    int32_t k;          /* neighbours per point */
-    int32_t margin;     /* extra FP32 candidates kept for the certificate (16 is typical) */
-    int32_t precision;  /* VB_PREC_* */
-    int32_t prune;      /* VB_PRUNE_* */
+    int32_t k;               /* neighbours per point */
+    int32_t margin;          /* extra FP32 candidates kept for the certificate (exact search) */
+    int32_t precision;       /* VB_PREC_* */
+    int32_t prune;           /* VB_PRUNE_* */
+    const float* radius;     /* VB_PRUNE_LEARNED without a model: per point (original order) guess of the
+                                distance to its k-th neighbour, n floats on the device */
+    const vb_mlp* mlp;       /* VB_PRUNE_LEARNED: learned radius model (NULL = use `radius`) */
+    float radius_inflate;    /* factor applied to every radius guess (0 = 1.5) */
+    float radius_log_shift;  /* added to the model's predicted log radius, e.g. ln(n_train / n) / d */
 } vb_knn_params;
 
 /* Workspace bytes vb_knn() needs for n points in R^m. */
@@ -133,6 +154,45 @@ size_t vb_knn_workspace(int64_t n, int32_t m, const vb_knn_params* p);
  * the neighbours of point i in rank order). */
 vb_status vb_knn(vb_ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_params* p,
                  int32_t* nbr, double* nbr_d2, void* ws, size_t ws_bytes);
+
+/* ---------------------------------------------------- learned radius (a7)
+ * A small network in_dim -> 64 -> 64 -> 1 (GELU, erf form) predicts the log of
+ * a point's distance to its k-th neighbour from its coordinates; with
+ * VB_PRUNE_LEARNED and knn.mlp set, exp(prediction + radius_log_shift) *
+ * radius_inflate is each point's radius guess.  Parameters live on the
+ * device: FP32 master weights, a BF16 copy used by the forward passes, Adam
+ * moments.  Inputs and targets are standardised with host-side constants.
+ * Parameter layout (vb_mlp_param_count floats): W1 [64][in_dim], b1 [64],
+ * W2 [64][64], b2 [64], w3 [64], b3 [1]. */
+#define VB_MLP_HIDDEN 64
+#define VB_MLP_MAX_IN 16
+struct vb_mlp {
+    int32_t in_dim;                     /* 1 .. VB_MLP_MAX_IN (the first in_dim coordinates are used) */
+    float* master;                      /* device FP32 parameters */
+    uint16_t* weights;                  /* device BF16 parameters (round-to-nearest copy of master) */
+    float* adam_m;                      /* device Adam moments, same size */
+    float* adam_v;
+    float in_mean[VB_MLP_MAX_IN];       /* input standardisation: (x - mean) / scale */
+    float in_scale[VB_MLP_MAX_IN];
+    float out_mean, out_scale;          /* prediction = out_mean + out_scale * network output */
+    int64_t step;                       /* Adam steps taken */
+};
+int64_t vb_mlp_param_count(int32_t in_dim);
+/* He-normal initialisation of master (counter-based generator from seed), zero moments, BF16 copy. */
+vb_status vb_mlp_init(vb_ctx* ctx, vb_mlp* mlp, uint64_t seed);
+size_t vb_mlp_workspace(int32_t in_dim, int64_t batch);
+/* One epoch of Adam (lr, beta1 0.9, beta2 0.999, eps 1e-8) on the mean squared error of the
+ * standardised target over x [n][ld] (first in_dim columns used) and y [n] (raw log radii), in
+ * minibatches of `batch` consecutive rows, starting from a block chosen by seed.
+ * loss_dev (optional, device FP32): mean squared error of the epoch's last minibatch. */
+vb_status vb_mlp_train_epoch(vb_ctx* ctx, vb_mlp* mlp, const float* x, int32_t ld, const float* y, int64_t n,
+                             int32_t batch, float lr, uint64_t seed, float* loss_dev, void* ws, size_t ws_bytes);
+/* Full-batch gradient of the loss (mean over n of (net(x) - y_std)^2) at the BF16 weights, FP32
+ * arithmetic, deterministic; grad: vb_mlp_param_count FP32 on the device; loss_dev: 1 FP32. */
+vb_status vb_mlp_gradient(vb_ctx* ctx, const vb_mlp* mlp, const float* x, int32_t ld, const float* y, int64_t n,
+                          float* grad, float* loss_dev, void* ws, size_t ws_bytes);
+/* y[i] = predicted log radius of row i of x [n][ld] (BF16 weights, FP32 arithmetic). */
+vb_status vb_mlp_predict(vb_ctx* ctx, const vb_mlp* mlp, const float* x, int32_t ld, int64_t n, float* y);
 
 /* ------------------------------------------------- symmetric pattern (a6)
  * The sparsity pattern of the kernel matrices: the diagonal (Algorithm 1
@@ -281,6 +341,12 @@ size_t vb_solve_workspace(int64_t n, int64_t cap, const vb_solve_params* p);
 vb_status vb_solve(vb_ctx* ctx, const vb_graph* g, int64_t cap, const float* val, const double* S,
                    const vb_solve_params* p, double* evals, float* phi, const float* g_rhs, float* f,
                    int32_t* iters, void* ws, size_t ws_bytes);
+
+/* Diagnostic: one tensor-core tile (tcgen05.mma, kind::f16), d [128][N] = a [128][K] b [N][K]^T
+ * with a and b rounded to BF16 and FP32 accumulation in tensor memory; K a multiple of 16 up
+ * to 128, N a multiple of 32 up to 128; FP32 row-major device arrays.  The BF16 distance tiles
+ * of the kNN search are built from the same primitives. */
+vb_status vb_tc_dot_tile(vb_ctx* ctx, const float* a, const float* b, int32_t K, int32_t N, float* d);
 
 /* ------------------------------------------------- the whole build (a0-a13)
  * One call for Sec. 4 steps 1-3 up to L-hat: kNN, pattern, bandwidth,

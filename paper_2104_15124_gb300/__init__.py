@@ -18,8 +18,8 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libvb.so")
 
-VB_PREC_FP32 = 0
-VB_PRUNE_NONE, VB_PRUNE_EXACT = 0, 1
+VB_PREC_FP32, VB_PREC_BF16, VB_PREC_FP16 = 0, 1, 2
+VB_PRUNE_NONE, VB_PRUNE_EXACT, VB_PRUNE_LEARNED = 0, 1, 2
 VB_SPMV_PLAIN, VB_SPMV_LAPLACIAN = 0, 1
 XI_LO, XI_HI, DXI = -10.0, 4.0, 0.25
 VB_NOALLOC_MAX_N = 1 << 20   # rows vb_spmv_laplacian_noalloc accepts (its static scratch size)
@@ -41,7 +41,8 @@ c_i32, c_i64, c_f32, c_f64, c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_floa
 
 
 class KnnParams(ctypes.Structure):
-    _fields_ = [("k", c_i32), ("margin", c_i32), ("precision", c_i32), ("prune", c_i32)]
+    _fields_ = [("k", c_i32), ("margin", c_i32), ("precision", c_i32), ("prune", c_i32), ("radius", c_p),
+                ("mlp", c_p), ("radius_inflate", c_f32), ("radius_log_shift", c_f32)]
 
 
 class GraphC(ctypes.Structure):
@@ -68,9 +69,17 @@ class SolveParams(ctypes.Structure):
                 ("seed", ctypes.c_uint64)]
 
 
+class MlpC(ctypes.Structure):
+    _fields_ = [("in_dim", c_i32), ("master", c_p), ("weights", c_p), ("adam_m", c_p), ("adam_v", c_p),
+                ("in_mean", c_f32 * 16), ("in_scale", c_f32 * 16), ("out_mean", c_f32), ("out_scale", c_f32),
+                ("step", c_i64)]
+
+
 class Report(ctypes.Structure):
     _fields_ = [("error", c_i32), ("warnings", c_i32), ("knn_fallback_rows", c_i64), ("knn_candidates", c_i64),
-                ("union_big_rows", c_i64), ("reserved", c_i64 * 4)]
+                ("union_big_rows", c_i64), ("knn_heap_levels", c_i64), ("knn_tiles_staged", c_i64),
+                ("knn_insert_rounds", c_i64), ("knn_retry_tiles", c_i64), ("knn_rows_short", c_i64),
+                ("knn_rows_long_run", c_i64), ("knn_rows_uncertified", c_i64)]
 
 
 _SIGS = {
@@ -103,6 +112,14 @@ _SIGS = {
     "vb_solve_workspace": (c_sz, [c_i64, c_i64, ctypes.POINTER(SolveParams)]),
     "vb_solve": (c_i32, [c_p, ctypes.POINTER(GraphC), c_i64, c_p, c_p, ctypes.POINTER(SolveParams), c_p, c_p, c_p,
                          c_p, ctypes.POINTER(c_i32), c_p, c_sz]),
+    "vb_mlp_param_count": (c_i64, [c_i32]),
+    "vb_mlp_init": (c_i32, [c_p, ctypes.POINTER(MlpC), ctypes.c_uint64]),
+    "vb_mlp_workspace": (c_sz, [c_i32, c_i64]),
+    "vb_mlp_train_epoch": (c_i32, [c_p, ctypes.POINTER(MlpC), c_p, c_i32, c_p, c_i64, c_i32, c_f32, ctypes.c_uint64,
+                                   c_p, c_p, c_sz]),
+    "vb_mlp_gradient": (c_i32, [c_p, ctypes.POINTER(MlpC), c_p, c_i32, c_p, c_i64, c_p, c_p, c_p, c_sz]),
+    "vb_mlp_predict": (c_i32, [c_p, ctypes.POINTER(MlpC), c_p, c_i32, c_i64, c_p]),
+    "vb_tc_dot_tile": (c_i32, [c_p, c_p, c_p, c_i32, c_i32, c_p]),
     "vb_build_workspace": (c_sz, [c_i64, c_i32, ctypes.POINTER(BuildParams)]),
     "vb_build": (c_i32, [c_p, c_p, c_i64, c_i32, ctypes.POINTER(BuildParams), ctypes.POINTER(BuildOut), c_p, c_sz]),
 }
@@ -167,7 +184,10 @@ def report(device=None) -> dict:
     r = Report()
     _check(lib().vb_report_read(c_p(_ctx(dev)), ctypes.byref(r)), "vb_report_read")
     return dict(error=r.error, warnings=r.warnings, knn_fallback_rows=r.knn_fallback_rows,
-                knn_candidates=r.knn_candidates, union_big_rows=r.union_big_rows)
+                knn_candidates=r.knn_candidates, union_big_rows=r.union_big_rows, knn_heap_levels=r.knn_heap_levels,
+                knn_tiles_staged=r.knn_tiles_staged, knn_insert_rounds=r.knn_insert_rounds,
+                knn_retry_tiles=r.knn_retry_tiles, knn_rows_short=r.knn_rows_short,
+                knn_rows_long_run=r.knn_rows_long_run, knn_rows_uncertified=r.knn_rows_uncertified)
 
 
 def report_reset(device=None) -> None:
@@ -223,11 +243,17 @@ class Graph:
 
 
 # ----------------------------------------------------------------------------- the calls
-def knn(x: torch.Tensor, k: int, margin: int = 16, prune: bool = True):
-    """Exact kNN (vb_knn): returns (nbr int32 [n, k], nbr_d2 fp64 [n, k])."""
+def knn(x: torch.Tensor, k: int, margin: int = 16, prune: bool = True, radius: torch.Tensor | None = None,
+        inflate: float = 0.0, mlp=None, log_shift: float = 0.0, tensor_cores: str | None = None):
+    """Exact kNN (vb_knn): returns (nbr int32 [n, k], nbr_d2 fp64 [n, k]).  With `radius` (per-point
+    guess of the k-th neighbour distance) or a learned `mlp`, the radius-first search runs;
+    tensor_cores = "fp16" or "bf16" computes its distance tiles on the tensor cores."""
     n, m = x.shape
     dev = x.device
-    p = KnnParams(k, margin, VB_PREC_FP32, VB_PRUNE_EXACT if prune else VB_PRUNE_NONE)
+    mode = VB_PRUNE_LEARNED if (radius is not None or mlp is not None) else (VB_PRUNE_EXACT if prune else VB_PRUNE_NONE)
+    prec = {None: VB_PREC_FP32, "bf16": VB_PREC_BF16, "fp16": VB_PREC_FP16}[tensor_cores]
+    p = KnnParams(k, margin, prec, mode, _p(radius),
+                  c_p(0) if mlp is None else c_p(mlp.handle()), inflate, log_shift)
     nbr = torch.empty((n, k), dtype=torch.int32, device=dev)
     d2 = torch.empty((n, k), dtype=torch.float64, device=dev)
     ws = _ws(lib().vb_knn_workspace(n, m, ctypes.byref(p)), dev)
@@ -305,6 +331,15 @@ def kernel_csr(g: Graph, psi: torch.Tensor, P: torch.Tensor, eps2_op: torch.Tens
     return val, q, D, S
 
 
+def tc_dot_tile(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
+    """Diagnostic tensor-core tile: a [128, K] @ b [N, K]^T with BF16 operands, FP32 result (vb_tc_dot_tile)."""
+    K = a.shape[1]
+    N = b.shape[0]
+    d = torch.empty((128, N), dtype=torch.float32, device=a.device)
+    _check(lib().vb_tc_dot_tile(c_p(_ctx(a.device)), _p(a), _p(b), K, N, _p(d)), "vb_tc_dot_tile")
+    return d
+
+
 def spmv(g: Graph, val: torch.Tensor, x: torch.Tensor, S: torch.Tensor | None = None, laplacian: bool = False,
          alpha: float = 1.0, beta: float = 0.0, y: torch.Tensor | None = None) -> torch.Tensor:
     """y = alpha A x + beta y (vb_spmv); laplacian=True applies L-hat in difference form with S."""
@@ -316,6 +351,80 @@ def spmv(g: Graph, val: torch.Tensor, x: torch.Tensor, S: torch.Tensor | None = 
     _check(lib().vb_spmv(c_p(_ctx(dev)), ctypes.byref(gc), _p(val), _p(S), VB_SPMV_LAPLACIAN if laplacian else
                          VB_SPMV_PLAIN, alpha, _p(x), beta, _p(y), _p(ws), 0 if ws is None else ws.numel()), "vb_spmv")
     return y
+
+
+class Mlp:
+    """The learned-radius network (vb_mlp): device parameters held in torch tensors, plus the
+    host-side standardisation constants.  `handle()` is the address of the C struct."""
+
+    def __init__(self, in_dim: int, device=None, seed: int = 1):
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.device = dev
+        P = int(lib().vb_mlp_param_count(in_dim))
+        self.master = torch.empty(P, dtype=torch.float32, device=dev)
+        self.weights = torch.empty(P, dtype=torch.int16, device=dev)   # BF16 bit patterns
+        self.adam_m = torch.empty(P, dtype=torch.float32, device=dev)
+        self.adam_v = torch.empty(P, dtype=torch.float32, device=dev)
+        self.c = MlpC(in_dim, _p(self.master), _p(self.weights), _p(self.adam_m), _p(self.adam_v))
+        for r in range(16):
+            self.c.in_scale[r] = 1.0
+        self.c.out_scale = 1.0
+        _check(lib().vb_mlp_init(c_p(_ctx(dev)), ctypes.byref(self.c), seed), "vb_mlp_init")
+
+    @property
+    def param_count(self) -> int:
+        return self.master.numel()
+
+    def handle(self) -> int:
+        return ctypes.addressof(self.c)
+
+    def set_standardisation(self, in_mean, in_scale, out_mean: float, out_scale: float) -> None:
+        for r in range(self.c.in_dim):
+            self.c.in_mean[r] = float(in_mean[r])
+            self.c.in_scale[r] = float(in_scale[r])
+        self.c.out_mean = float(out_mean)
+        self.c.out_scale = float(out_scale)
+
+    def bf16_weights(self) -> torch.Tensor:
+        """FP32 values of the BF16 weights the forward passes use."""
+        return (self.weights.to(torch.int32) << 16).view(torch.float32)
+
+    def train_epoch(self, x: torch.Tensor, y: torch.Tensor, batch: int = 4096, lr: float = 1e-3, seed: int = 0):
+        n, ld = x.shape
+        loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        ws = _ws(lib().vb_mlp_workspace(self.c.in_dim, batch), self.device)
+        _check(lib().vb_mlp_train_epoch(c_p(_ctx(self.device)), ctypes.byref(self.c), _p(x), ld, _p(y), n, batch, lr,
+                                        seed, _p(loss), _p(ws), ws.numel()), "vb_mlp_train_epoch")
+        return loss
+
+    def gradient(self, x: torch.Tensor, y: torch.Tensor):
+        n, ld = x.shape
+        grad = torch.empty(self.param_count, dtype=torch.float32, device=self.device)
+        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        ws = _ws(lib().vb_mlp_workspace(self.c.in_dim, n), self.device)
+        _check(lib().vb_mlp_gradient(c_p(_ctx(self.device)), ctypes.byref(self.c), _p(x), ld, _p(y), n, _p(grad),
+                                     _p(loss), _p(ws), ws.numel()), "vb_mlp_gradient")
+        return grad, loss
+
+    def predict(self, x: torch.Tensor) -> torch.Tensor:
+        n, ld = x.shape
+        y = torch.empty(n, dtype=torch.float32, device=self.device)
+        _check(lib().vb_mlp_predict(c_p(_ctx(self.device)), ctypes.byref(self.c), _p(x), ld, n, _p(y)),
+               "vb_mlp_predict")
+        return y
+
+
+def train_radius_model(x: torch.Tensor, logr: torch.Tensor, epochs: int = 30, batch: int = 4096, lr: float = 3e-3,
+                       seed: int = 103) -> Mlp:
+    """Fits the learned-radius network to (x, log r_k) pairs on the GPU (vb_mlp_train_epoch)."""
+    n, m = x.shape
+    mean = x.mean(0).cpu().numpy()
+    scale = x.std(0).clamp_min(1e-12).cpu().numpy()
+    net = Mlp(min(m, 16), x.device, seed)
+    net.set_standardisation(mean, scale, float(logr.mean()), float(logr.std().clamp_min(1e-12)))
+    for ep in range(epochs):
+        net.train_epoch(x, logr, batch=batch, lr=lr, seed=seed * 1000 + ep)
+    return net
 
 
 @dataclasses.dataclass
@@ -371,11 +480,17 @@ class Builder:
     repeated builds (and timing loops) allocate nothing."""
 
     def __init__(self, n: int, m: int, k: int, d: float, c: float, beta: float = -0.25, margin: int = 16,
-                 k_bw: int | None = None, prune: bool = True, device=None, grid=(XI_LO, XI_HI, DXI)):
+                 k_bw: int | None = None, prune: bool = True, device=None, grid=(XI_LO, XI_HI, DXI),
+                 mlp: "Mlp | None" = None, log_shift: float = 0.0, inflate: float = 0.0,
+                 tensor_cores: str | None = None):
         dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.n, self.m, self.k, self.device = n, m, k, dev
+        self.mlp = mlp   # kept alive: the C parameters point at it
         G = int(round((grid[1] - grid[0]) / grid[2])) + 1
-        self.params = BuildParams(KnnParams(k, margin, VB_PREC_FP32, VB_PRUNE_EXACT if prune else VB_PRUNE_NONE),
+        mode = VB_PRUNE_LEARNED if mlp is not None else (VB_PRUNE_EXACT if prune else VB_PRUNE_NONE)
+        prec = {None: VB_PREC_FP32, "bf16": VB_PREC_BF16, "fp16": VB_PREC_FP16}[tensor_cores]
+        self.params = BuildParams(KnnParams(k, margin, prec, mode, c_p(0),
+                                            c_p(0) if mlp is None else c_p(mlp.handle()), inflate, log_shift),
                                   0 if k_bw is None else k_bw, OpParams(c, beta, d), grid[0], grid[1], grid[2], 0)
         cap = n * (2 * k + 1)
         f64 = lambda s: torch.empty(s, dtype=torch.float64, device=dev)

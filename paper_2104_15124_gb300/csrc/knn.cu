@@ -22,6 +22,10 @@
 //       Uncertified rows (ties, duplicates) are recomputed by an exact FP64
 //       radix selection over all points.
 #include "vb_internal.cuh"
+#include "tc.cuh"
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
@@ -41,7 +45,10 @@ struct KnnWs {
     float* tlo;           // ntiles * MP
     float* thi;
     int* fb_list;         // n
-    int* fb_count;        // 1
+    int* fb_count;        // [0] fallback rows, [1] next query tile, [2] next failed tile, [3] failed tiles
+    float* r2;            // n (radius search: squared radius bound per sorted point)
+    int* fail_flag;       // 2 ntiles: flags of radius passes 1 and 2
+    int* fail_list;       // 2 ntiles: tiles left by passes 1 and 2
 };
 
 static int pad_dim(int m)
@@ -57,7 +64,7 @@ size_t knn_plan(Carve& c, int64_t n, int32_t m, const vb_knn_params*, KnnWs* w)
 {
     const int mp = pad_dim(m);
     const int64_t ntiles = (n + TILE - 1) / TILE;
-    const int64_t npad = ntiles * TILE;
+    const int64_t npad = (ntiles + (ntiles & 1)) * TILE;   // even tile count: the tensor-core search pairs tiles
     const int64_t nblk = (n + RADIX_ITEMS - 1) / RADIX_ITEMS;
     KnnWs t;
     t.bbox = c.take<int>(8);
@@ -70,7 +77,10 @@ size_t knn_plan(Carve& c, int64_t n, int32_t m, const vb_knn_params*, KnnWs* w)
     t.tlo = c.take<float>(ntiles * mp);
     t.thi = c.take<float>(ntiles * mp);
     t.fb_list = c.take<int>(n);
-    t.fb_count = c.take<int>(2);   // [0] fallback rows, [1] next query tile
+    t.fb_count = c.take<int>(8);
+    t.r2 = c.take<float>(npad);
+    t.fail_flag = c.take<int>(2 * ntiles);
+    t.fail_list = c.take<int>(2 * ntiles);
     if (w) *w = t;
     return c.off;
 }
@@ -88,7 +98,7 @@ __global__ void bbox_init_kernel(int* bbox, int* fb_count)
     int t = threadIdx.x;
     if (t < 4) bbox[t] = 0x7fffffff;
     else if (t < 8) bbox[t] = (int)0x80000000;
-    if (t == 0) { fb_count[0] = 0; fb_count[1] = 0; }
+    if (t < 8) fb_count[t] = 0;
 }
 
 // Bounding box of the Morton coordinates; also rejects non-finite input.
@@ -140,6 +150,13 @@ __global__ void morton_kernel(const float* __restrict__ x, int64_t n, int m, int
         for (int r = 0; r < md; ++r) k = (k << 1) | ((q[r] >> b) & 1u);
     key[i] = k;
     val[i] = (uint32_t)i;
+}
+
+// Key of the cloud passes: the cloud of each point, in the current (Morton) order.
+__global__ void cloud_key_kernel(const uint32_t* __restrict__ val, int64_t n, Clouds cl, uint32_t* key)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) key[i] = (uint32_t)cloud_of(cl.ptr, cl.B, (int64_t)val[i]);
 }
 
 __global__ void radix_hist_kernel(const uint32_t* __restrict__ key, int64_t n, int shift, uint32_t* hist, int nblk)
@@ -283,6 +300,16 @@ struct TileArgs {
     int* fb_list;
     int* fb_count;
     int* work;           // next query tile (persistent grid)
+    const int* tile_list;   // optional list of query tiles to process (else all tiles)
+    const int* tile_count;  // its length (device)
+    const float* r2;        // radius search: per sorted point, squared radius bound
+    float r2_scale;         // radius search: factor on r2 for this pass
+    int count_retries;      // radius search: count the tiles this pass hands on (last pass only)
+    int cap;                // radius search: candidates kept per query
+    int* fail_flag;         // radius search: per query tile, set once it joins fail_list
+    int* fail_list;
+    int* fail_count;
+    Clouds cl;              // batched build: queries only take candidates from their own cloud
     DevReport* rep;
 };
 
@@ -290,29 +317,32 @@ constexpr int IB = 16;        // candidates per insertion batch
 constexpr int SCAP = 512;     // candidate tiles per sorted chunk
 constexpr int RUN = 8;        // longest run of FP32-indistinguishable neighbours ordered in registers
 
-// Sift key down from node i of the max-heap heap[0..size) (column t of a [.][TILE] array).
-__device__ __forceinline__ void sift_down(uint64_t* heap, int t, int i, int size, uint64_t key)
+// Sift key down from node i of the max-heap heap[0..size) (column t of a [.][COLS] array).
+template <int COLS = TILE>
+__device__ __forceinline__ void sift_down(uint64_t* heap, int t, int i, int size, uint64_t key, unsigned& levels)
 {
     for (;;) {
         int l = 2 * i + 1;
         if (l >= size) break;
-        uint64_t ck = heap[l * TILE + t];
+        ++levels;
+        uint64_t ck = heap[l * COLS + t];
         int ch = l;
         if (l + 1 < size) {
-            uint64_t rk = heap[(l + 1) * TILE + t];
+            uint64_t rk = heap[(l + 1) * COLS + t];
             if (rk > ck) { ck = rk; ch = l + 1; }
         }
         if (ck <= key) break;
-        heap[i * TILE + t] = ck;
+        heap[i * COLS + t] = ck;
         i = ch;
     }
-    heap[i * TILE + t] = key;
+    heap[i * COLS + t] = key;
 }
 
 // Floyd's bottom-up construction of a max-heap over heap[0..size).
-__device__ __forceinline__ void heapify(uint64_t* heap, int t, int size)
+template <int COLS = TILE>
+__device__ __forceinline__ void heapify(uint64_t* heap, int t, int size, unsigned& levels)
 {
-    for (int i = size / 2 - 1; i >= 0; --i) sift_down(heap, t, i, size, heap[i * TILE + t]);
+    for (int i = size / 2 - 1; i >= 0; --i) sift_down<COLS>(heap, t, i, size, heap[i * COLS + t], levels);
 }
 
 template <int MP>
@@ -325,6 +355,95 @@ __device__ __forceinline__ float point_box_lb(const float* q, const float* lo, c
         acc = fmaf(g, g, acc);
     }
     return acc;
+}
+
+// Orders the candidates of one query and writes its row (step a5).  arr[0..size)
+// holds keys (FP32 distance bits << 32 | sorted position), column t of a [.][TILE]
+// array; is_heap says whether it already is a max-heap.  After an in-place heap
+// sort the keys are walked in ascending order: FP64 canonical distances are
+// computed for the first k (plus the run straddling rank k), and keys whose FP32
+// distances lie within the error band of each other ("runs") are ordered exactly
+// by (d2, index) in registers.  Certificate: when `bound_mode` is 1 the largest
+// kept FP32 distance bounds every excluded candidate (heap search); when it is 2,
+// `bound` does (radius search).  The k-th FP64 distance must lie below the bound
+// minus the error band.  Returns false when the row needs the exact fallback.
+// e_lin, e_const: an absolute error bound E(d) = e_lin sqrt(d) + e_const of the
+// distances in the keys on top of the relative FP32 band (0 for FP32 distances;
+// the BF16 tensor-core distances need them).
+template <int MP, int COLS = TILE>
+__device__ bool finalize_row(const TileArgs& a, uint64_t* arr, int t, int size, bool is_heap, int64_t pq,
+                             int64_t ncl, int bound_mode, float bound, unsigned& levels, float e_lin = 0.f, float e_const = 0.f)
+{
+    if (!is_heap) heapify<COLS>(arr, t, size, levels);
+    for (int e = size - 1; e > 0; --e) {
+        const uint64_t top = arr[t];
+        const uint64_t key = arr[e * COLS + t];
+        arr[e * COLS + t] = top;
+        sift_down<COLS>(arr, t, 0, e, key, levels);
+    }
+    const uint64_t Hkey = arr[(size - 1) * COLS + t];
+    const uint32_t oq = a.perm[pq];
+    const float* qc = a.xs + pq * MP;
+    uint64_t rd[RUN];   // FP64 distance bits
+    uint32_t ro[RUN];
+    int rlen = 0, out = 0;
+    float run_last = 0.f;
+    bool ok = true;
+    double dk = 0.0;
+    auto emit = [&]() {
+#pragma unroll
+        for (int u = 0; u < RUN; ++u) {
+            if (u < rlen && out < a.k) {
+                a.nbr[(int64_t)oq * a.k + out] = (int32_t)ro[u];
+                a.nbr_d2[(int64_t)oq * a.k + out] = __longlong_as_double((long long)rd[u]);
+                if (out == a.k - 1) dk = __longlong_as_double((long long)rd[u]);
+                ++out;
+            }
+        }
+        rlen = 0;
+    };
+    for (int r = 0; r < size; ++r) {
+        const uint64_t key = arr[r * COLS + t];
+        if ((uint32_t)key == 0xffffffffu) break;   // empty slot or radius sentinel
+        const float df = __uint_as_float((uint32_t)(key >> 32));
+        // a new run starts once the distance clears the error band (tiny distances,
+        // where FP32 may have underflowed, all stay in one run)
+        const float gap = 2.02f * (e_lin * sqrtf(fmaxf(df, 0.f)) + e_const);
+        if (rlen > 0 && df > run_last * a.band + gap && df > 1e-30f) {
+            emit();
+            if (out >= a.k) break;
+        }
+        if (rlen == RUN) { ok = false; break; }
+        const uint32_t cp = (uint32_t)key;
+        const uint32_t oj = a.perm[cp];
+        const uint64_t dj = (uint64_t)__double_as_longlong(canon_d2(qc, a.xs + (int64_t)cp * MP, a.m));
+        // insert (dj, oj) into the run, kept sorted by (d2, index); non-negative doubles
+        // order like their bit patterns, so the comparisons stay on the integer pipe
+#pragma unroll
+        for (int u = 0; u < RUN; ++u)
+            if (u == rlen) { rd[u] = dj; ro[u] = oj; }
+#pragma unroll
+        for (int u = RUN - 1; u > 0; --u) {
+            if (u <= rlen && (rd[u] < rd[u - 1] || (rd[u] == rd[u - 1] && ro[u] < ro[u - 1]))) {
+                uint64_t td = rd[u]; rd[u] = rd[u - 1]; rd[u - 1] = td;
+                uint32_t to = ro[u]; ro[u] = ro[u - 1]; ro[u - 1] = to;
+            }
+        }
+        ++rlen;
+        run_last = df;
+    }
+    if (ok && out < a.k) emit();
+    if (!ok) { atomicAdd(&a.rep->knn_rows_long_run, 1ull); return false; }
+    if (out < a.k) { atomicAdd(&a.rep->knn_rows_short, 1ull); return false; }
+    float B = bound;
+    if (bound_mode == 1) {
+        if (ncl - 1 <= (int64_t)size || Hkey == ~0ull) return true;   // every candidate was kept
+        B = __uint_as_float((uint32_t)(Hkey >> 32));
+    }
+    const double Eb = 1.01 * ((double)e_lin * sqrt((double)fmaxf(B, 0.f)) + (double)e_const);
+    const bool cert = isfinite(B) && dk < ((double)B - Eb) * a.cert_factor - (double)a.m * 1.1754943508222875e-38;
+    if (!cert) atomicAdd(&a.rep->knn_rows_uncertified, 1ull);
+    return cert;
 }
 
 // Query tiles are taken from a global counter by a persistent grid of 64-thread
@@ -347,19 +466,39 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
     __shared__ float sqlo[MP], sqhi[MP];
     __shared__ uint32_t sred[2];
     __shared__ int s_tile, s_cnt;
+    __shared__ int64_t s_ct[2];
 
     constexpr bool QREG = MP <= 16;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t nt = a.ntiles;
     unsigned long long evaluated = 0;
+    unsigned levels = 0, staged = 0, rounds = 0;
 
     for (;;) {
-        if (t == 0) s_tile = atomicAdd(a.work, 1);
+        if (t == 0) {
+            const int idx = atomicAdd(a.work, 1);
+            s_tile = a.tile_list ? (idx < *a.tile_count ? a.tile_list[idx] : 0x7fffffff) : idx;
+        }
         __syncthreads();
         const int64_t qt = s_tile;
         if (qt >= nt) break;
         const int64_t p = qt * TILE + t;
         const bool valid = p < a.n;
+        int64_t qlo = 0, qhi = a.n;   // the query's cloud
+        if (a.cl.B > 1 && valid) {
+            const int b = cloud_of(a.cl.ptr, a.cl.B, p);
+            qlo = a.cl.ptr[b];
+            qhi = a.cl.ptr[b + 1];
+        }
+        if (t == 0) {   // candidate tiles that hold points of this tile's clouds
+            s_ct[0] = 0;
+            s_ct[1] = nt;
+            if (a.cl.B > 1) {
+                const int64_t p0 = qt * TILE, pl = min(a.n, p0 + TILE) - 1;
+                s_ct[0] = a.cl.ptr[cloud_of(a.cl.ptr, a.cl.B, p0)] / TILE;
+                s_ct[1] = (a.cl.ptr[cloud_of(a.cl.ptr, a.cl.B, pl) + 1] + TILE - 1) / TILE;
+            }
+        }
         float qr[QREG ? MP : 1];
         if constexpr (QREG) {
 #pragma unroll
@@ -375,6 +514,21 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
         uint64_t maxkey = ~0ull;
         int fill = 0;               // keys stored so far; the heap is ordered once it holds L
         uint32_t thr_blk = 0xffffffffu;
+        const bool rmode = a.r2 != nullptr;
+        if (rmode) {
+            // radius-first: every slot starts as a sentinel at the query's radius bound, so only
+            // candidates inside the radius ever enter and tiles are pruned from the start
+            const float R2 = valid ? __fmul_ru(a.r2[p], a.r2_scale) : 0.f;
+            const uint64_t sentinel = ((uint64_t)__float_as_uint(R2) << 32) | 0xffffffffu;
+            for (int sl = 0; sl < L; ++sl) heap[sl * TILE + t] = sentinel;
+            fill = L;
+            maxkey = sentinel;
+            const uint32_t wmax = __reduce_max_sync(0xffffffffu, valid ? __float_as_uint(R2) : 0u);
+            if (lane == 0) sred[warp] = wmax;
+        }
+        __syncthreads();
+        if (rmode) thr_blk = max(sred[0], sred[1]);
+        const int64_t ct_lo = s_ct[0], ct_hi = s_ct[1];
         __syncthreads();
 
         // Visit candidate tile ct for every query of this tile that may still gain from it.
@@ -398,6 +552,7 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
                 need = __float_as_uint(__fmul_rd(lb, a.lb_factor)) <= (uint32_t)(maxkey >> 32);
             }
             if (!__syncthreads_or(need)) return;
+            staged += t == 0;
             {
                 const float4* src = (const float4*)(a.xs + ct * TILE * MP);
                 float4* dst = (float4*)cand;
@@ -434,22 +589,23 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
                         }
                         const int64_t cp = c0 + c;
                         const uint64_t key = ((uint64_t)__float_as_uint(acc) << 32) | (uint32_t)cp;
-                        const bool take = key < thr && cp != p && cp < a.n;
+                        const bool take = key < thr && cp != p && cp >= qlo && cp < qhi;
                         if (take) buf[cnt * TILE + t] = key;
                         cnt += take;
                     }
+                    rounds += cnt;
                     for (int b = 0; b < cnt; ++b) {
                         const uint64_t key = buf[b * TILE + t];
                         if (fill < L) {   // first L keys: append, then order them in one pass
                             heap[fill * TILE + t] = key;
                             if (++fill == L) {
-                                heapify(heap, t, L);
+                                heapify(heap, t, L, levels);
                                 maxkey = heap[t];
                             }
                             continue;
                         }
                         if (key >= maxkey) continue;
-                        sift_down(heap, t, 0, L, key);   // replace the root
+                        sift_down(heap, t, 0, L, key, levels);   // replace the root
                         maxkey = heap[t];
                     }
                 }
@@ -463,20 +619,20 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
             __syncthreads();
         };
 
-        // seed: the tile itself and its neighbours in Morton order
-        for (int sidx = 0; sidx < a.nseed; ++sidx) {
+        // seed: the tile itself and its neighbours in Morton order (not needed with a radius bound)
+        for (int sidx = 0; sidx < (rmode ? 0 : a.nseed); ++sidx) {
             int64_t s2 = (sidx + 1) >> 1;
             int64_t ct = (sidx & 1) ? qt + s2 : qt - s2;
-            if (ct >= 0 && ct < nt) visit(ct);
+            if (ct >= ct_lo && ct < ct_hi) visit(ct);
         }
         // every other tile whose box lower bound does not exceed the threshold, nearest first
-        for (int64_t c0 = 0; c0 < nt;) {
+        for (int64_t c0 = ct_lo; c0 < ct_hi;) {
             if (t == 0) s_cnt = 0;
             __syncthreads();
-            for (; c0 < nt; c0 += TILE) {
+            for (; c0 < ct_hi; c0 += TILE) {
                 const int64_t ct = c0 + t;
-                bool keep = ct < nt;
-                if (keep) {
+                bool keep = ct < ct_hi;
+                if (keep && !rmode) {
                     const int64_t dct = ct - qt;
                     keep = (dct > (a.nseed >> 1) || dct < -((a.nseed - 1) >> 1));   // not a seed tile
                 }
@@ -523,79 +679,17 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
         }
 
         // ---------------- a5: order the kept candidates, rescore in FP64, certify
-        const int64_t pq = p;
-        if (valid) {
-            // in-place heap sort: ascending (FP32 distance, sorted position)
-            if (fill < L) heapify(heap, t, L);   // fewer than L candidates: unused slots hold ~0
-            for (int e = L - 1; e > 0; --e) {
-                const uint64_t top = heap[t];
-                const uint64_t key = heap[e * TILE + t];
-                heap[e * TILE + t] = top;
-                sift_down(heap, t, 0, e, key);
+        const bool row_ok = !valid || finalize_row<MP>(a, heap, t, L, fill == L, p, qhi - qlo, 1, 0.f, levels);
+        if (rmode) {
+            // a row with fewer than k points inside its radius, or uncertified: redo the tile exactly
+            if (__syncthreads_or(!row_ok) && t == 0 && atomicExch(&a.fail_flag[qt], 1) == 0) {
+                a.fail_list[atomicAdd(a.fail_count, 1)] = (int)qt;
+                atomicAdd(&a.rep->knn_retry_tiles, 1ull);
             }
-            const uint64_t Hkey = heap[(L - 1) * TILE + t];
-            const uint32_t oq = a.perm[pq];
-            const float* qc = a.xs + pq * MP;
-            double rd[RUN];
-            uint32_t ro[RUN];
-            int rlen = 0, out = 0;
-            float run_last = 0.f;
-            bool ok = true;
-            double dk = 0.0;
-            auto emit = [&]() {
-#pragma unroll
-                for (int u = 0; u < RUN; ++u) {
-                    if (u < rlen && out < a.k) {
-                        a.nbr[(int64_t)oq * a.k + out] = (int32_t)ro[u];
-                        a.nbr_d2[(int64_t)oq * a.k + out] = rd[u];
-                        if (out == a.k - 1) dk = rd[u];
-                        ++out;
-                    }
-                }
-                rlen = 0;
-            };
-            for (int r = 0; r < L; ++r) {
-                const uint64_t key = heap[r * TILE + t];
-                if (key == ~0ull) break;
-                const float df = __uint_as_float((uint32_t)(key >> 32));
-                // a new run starts once the FP32 distance clears the error band (tiny distances,
-                // where FP32 may have underflowed, all stay in one run)
-                if (rlen > 0 && df > run_last * a.band && df > 1e-30f) {
-                    emit();
-                    if (out >= a.k) break;
-                }
-                if (rlen == RUN) { ok = false; break; }
-                const uint32_t cp = (uint32_t)key;
-                const uint32_t oj = a.perm[cp];
-                const double dj = canon_d2(qc, a.xs + (int64_t)cp * MP, a.m);
-                // insert (dj, oj) into the run, kept sorted by (d2, index)
-#pragma unroll
-                for (int u = 0; u < RUN; ++u)
-                    if (u == rlen) { rd[u] = dj; ro[u] = oj; }
-#pragma unroll
-                for (int u = RUN - 1; u > 0; --u) {
-                    if (u <= rlen && (rd[u] < rd[u - 1] || (rd[u] == rd[u - 1] && ro[u] < ro[u - 1]))) {
-                        double td = rd[u]; rd[u] = rd[u - 1]; rd[u - 1] = td;
-                        uint32_t to = ro[u]; ro[u] = ro[u - 1]; ro[u - 1] = to;
-                    }
-                }
-                ++rlen;
-                run_last = df;
-            }
-            if (ok && out < a.k) emit();
-            if (ok) {
-                if (out < a.k) ok = false;   // cannot happen when n - 1 >= k; kept as a guard
-                else if (a.n - 1 > (int64_t)L && Hkey != ~0ull) {
-                    // candidates outside the heap have FP32 distance >= H: certify the k-th
-                    const float H = __uint_as_float((uint32_t)(Hkey >> 32));
-                    ok = isfinite(H) && dk < (double)H * a.cert_factor - (double)a.m * 1.1754943508222875e-38;
-                }
-            }
-            if (!ok) {
-                int slot = atomicAdd(a.fb_count, 1);
-                a.fb_list[slot] = (int)oq;
-                atomicAdd(&a.rep->knn_fallback_rows, 1ull);
-            }
+        } else if (!row_ok) {
+            int slot = atomicAdd(a.fb_count, 1);
+            a.fb_list[slot] = (int)a.perm[p];
+            atomicAdd(&a.rep->knn_fallback_rows, 1ull);
         }
         __syncthreads();
     }
@@ -603,6 +697,313 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
     if (lane == 0 && ev) atomicAdd(&a.rep->knn_candidates, ev);
+    unsigned long long lv = levels, st = staged, rd = rounds;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lv += __shfl_xor_sync(0xffffffffu, lv, o);
+        st += __shfl_xor_sync(0xffffffffu, st, o);
+        rd += __shfl_xor_sync(0xffffffffu, rd, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&a.rep->knn_heap_levels, lv);
+        atomicAdd(&a.rep->knn_tiles_staged, st);
+        atomicAdd(&a.rep->knn_insert_rounds, rd);
+    }
+}
+
+// ------------------------------------------------------------------ radius search on the tensor cores (a15)
+// The radius-first search with 16-bit (BF16 or FP16) distance tiles: query supertiles of 128
+// points (two 64-point tiles) against candidate supertiles of 128, with the
+// dot products of each pair formed by tcgen05.mma (BF16 operands, FP32
+// accumulation in tensor memory) and the distances completed as
+// |q|^2 + |c|^2 - 2 q.c.  Both operands are recentred on the query supertile's
+// box centre before rounding to BF16, so their magnitudes stay near the
+// neighbourhood scale.  With Z = 2 max|q'| + sqrt(max R2) (inflated), the
+// distance of any candidate within the radius differs from the exact one by
+// at most E(d) = 2 sqrt(d) delta + delta^2 + rho, delta = 2^-8 Z (BF16 rounding of
+// both operands), rho = (K + 4) 2^-24 Z^2 (FP32 sums); the run ordering and
+// the certificate of finalize_row take E into account, so the output stays
+// exact.  As in the FP32 radius-first search, each query keeps a max-heap of its
+// L nearest candidates that starts full of sentinels at its radius bound.
+// Tiles with a row that is not settled go to the exact FP32 search.
+constexpr int T2 = 128;
+
+// 16-bit operand types of the tiles: BF16 (8-bit significand) or FP16 (11-bit).
+template <bool F16> struct Half16;
+template <> struct Half16<false> {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ T from(float x) { return __float2bfloat16_rn(x); }
+    static __device__ __forceinline__ float to(T x) { return __bfloat162float(x); }
+    static constexpr float unit = 0.00390625f;     // 2^-8
+};
+template <> struct Half16<true> {
+    using T = __half;
+    static __device__ __forceinline__ T from(float x) { return __float2half_rn(x); }
+    static __device__ __forceinline__ float to(T x) { return __half2float(x); }
+    static constexpr float unit = 0.00048828125f;  // 2^-11
+};
+
+template <int MP, bool F16>
+__global__ void __launch_bounds__(T2) knn_radius_tc_kernel(TileArgs a)
+{
+    constexpr int KP = MP < 16 ? 16 : MP;
+    using HT = Half16<F16>;
+    using half_t = typename HT::T;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int C = a.cap;
+    half_t* sa = (half_t*)smem;                                // [T2][KP] core-matrix layout
+    half_t* sb = sa + T2 * KP;
+    float* sqb = (float*)(sb + T2 * KP);                       // [T2]
+    uint64_t* slist = (uint64_t*)(sqb + T2);                   // [SCAP]
+    uint64_t* buf = slist + SCAP;                              // [C][T2] max-heaps, C = L
+    __shared__ float sqlo[MP], sqhi[MP], scen[MP];
+    __shared__ uint32_t sred[4];
+    __shared__ int s_tile, s_cnt, s_fail, s_abort;
+    __shared__ int64_t s_cs[2];
+    __shared__ float s_red[4];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_base;
+
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t nt = a.ntiles;
+    const int64_t nst = (nt + 1) / 2;
+    unsigned long long evaluated = 0;
+    unsigned levels = 0, staged = 0;
+    if (warp == 0) tc::tmem_alloc(&tmem_base, 128);
+    if (t == 0) { tc::mbar_init(&bar, 1); s_abort = 0; }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tb = tmem_base;
+    uint32_t phase = 0;
+
+    // union box of supertile st (tiles 2 st and 2 st + 1 when it exists), dimension r
+    auto ubox = [&](int64_t st, int r, float& lo, float& hi) {
+        lo = a.tlo[(2 * st) * MP + r];
+        hi = a.thi[(2 * st) * MP + r];
+        if (2 * st + 1 < nt) {
+            lo = fminf(lo, a.tlo[(2 * st + 1) * MP + r]);
+            hi = fmaxf(hi, a.thi[(2 * st + 1) * MP + r]);
+        }
+    };
+
+    for (;;) {
+        if (t == 0) {
+            s_tile = atomicAdd(a.work, 1);
+            s_fail = 0;
+        }
+        __syncthreads();
+        const int64_t qs = s_tile;
+        if (qs >= nst || s_abort) break;
+        const int64_t p = qs * T2 + t;
+        const bool valid = p < a.n;
+        int64_t qlo = 0, qhi = a.n;   // the query's cloud
+        if (a.cl.B > 1 && valid) {
+            const int b = cloud_of(a.cl.ptr, a.cl.B, p);
+            qlo = a.cl.ptr[b];
+            qhi = a.cl.ptr[b + 1];
+        }
+        if (t == 0) {   // candidate supertiles that hold points of this supertile's clouds
+            s_cs[0] = 0;
+            s_cs[1] = nst;
+            if (a.cl.B > 1) {
+                const int64_t p0 = qs * T2, pl = min(a.n, p0 + T2) - 1;
+                s_cs[0] = a.cl.ptr[cloud_of(a.cl.ptr, a.cl.B, p0)] / T2;
+                s_cs[1] = (a.cl.ptr[cloud_of(a.cl.ptr, a.cl.B, pl) + 1] + T2 - 1) / T2;
+            }
+        }
+        for (int r = t; r < MP; r += T2) {
+            float lo, hi;
+            ubox(qs, r, lo, hi);
+            sqlo[r] = lo;
+            sqhi[r] = hi;
+            scen[r] = 0.5f * (lo + hi);
+        }
+        __syncthreads();
+        // query operand: bf16(q - centre), |q~|^2
+        float qr[MP];
+        float sqa = 0.f;
+#pragma unroll
+        for (int r = 0; r < MP; ++r) qr[r] = a.xs[p * MP + r];
+#pragma unroll
+        for (int j = 0; j < KP / 8; ++j) {
+            __align__(16) half_t v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int r = 8 * j + e;
+                const float x = r < MP ? qr[r] - scen[r] : 0.f;
+                v[e] = HT::from(valid ? x : 0.f);
+                const float xb = HT::to(v[e]);
+                sqa = fmaf(xb, xb, sqa);
+            }
+            *(uint4*)((char*)sa + tc::operand_offset(t, 8 * j, KP)) = *(const uint4*)v;
+        }
+        const float R2 = valid ? __fmul_ru(a.r2[p], a.r2_scale) : 0.f;
+        const uint32_t r2bits = __float_as_uint(R2);
+        {   // tile maxima of R2 and |q'|
+            uint32_t wr = __reduce_max_sync(0xffffffffu, valid ? r2bits : 0u);
+            uint32_t wa = __reduce_max_sync(0xffffffffu, valid ? __float_as_uint(sqrtf(sqa)) : 0u);
+            if (lane == 0) { sred[warp] = wr; s_red[warp] = __uint_as_float(wa); }
+        }
+        tc::fence_async_smem();
+        __syncthreads();
+        const uint32_t thr_blk = max(max(sred[0], sred[1]), max(sred[2], sred[3]));
+        const float amax = fmaxf(fmaxf(s_red[0], s_red[1]), fmaxf(s_red[2], s_red[3]));
+        const float Z = 1.02f * (2.f * amax + sqrtf(__uint_as_float(thr_blk)));
+        const float delta = 1.01f * HT::unit * Z;
+        const float rho = 1.01f * (float)(KP + 4) * 5.9604645e-8f * Z * Z;
+        const uint64_t sentinel = ((uint64_t)r2bits << 32) | 0xffffffffu;
+        for (int sl = 0; sl < C; ++sl) buf[sl * T2 + t] = sentinel;
+        uint64_t heapmax = sentinel;
+
+        const int64_t cs_lo = s_cs[0], cs_hi = s_cs[1];
+        for (int64_t c0 = cs_lo; c0 < cs_hi && !s_abort;) {
+            if (t == 0) s_cnt = 0;
+            __syncthreads();
+            for (; c0 < cs_hi; c0 += T2) {
+                const int64_t cs = c0 + t;
+                bool keep = cs < cs_hi;
+                if (keep) {
+                    float acc = 0.f;
+                    for (int r = 0; r < MP; ++r) {
+                        float lo, hi;
+                        ubox(cs, r, lo, hi);
+                        float g = fmaxf(fmaxf(lo - sqhi[r], sqlo[r] - hi), 0.f);
+                        acc = fmaf(g, g, acc);
+                    }
+                    keep = __float_as_uint(__fmul_rd(acc, a.lb_factor)) <= thr_blk;
+                }
+                unsigned bal = __ballot_sync(0xffffffffu, keep);
+                if (lane == 0 && bal) sred[warp] = atomicAdd(&s_cnt, __popc(bal));
+                __syncwarp();
+                if (keep) slist[sred[warp] + __popc(bal & ((1u << lane) - 1u))] = (uint64_t)cs;
+                __syncthreads();
+                if (s_cnt > SCAP - T2) { c0 += T2; break; }
+            }
+            const int cnt = s_cnt;
+            for (int si = 0; si < cnt; ++si) {
+                const int64_t cs = (int64_t)slist[si];
+                bool need = valid;
+                if (need) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int r = 0; r < MP; ++r) {
+                        float lo, hi;
+                        ubox(cs, r, lo, hi);
+                        float g = fmaxf(fmaxf(lo - qr[r], qr[r] - hi), 0.f);
+                        acc = fmaf(g, g, acc);
+                    }
+                    need = __float_as_uint(__fmul_rd(acc, a.lb_factor)) <= (uint32_t)(heapmax >> 32);
+                }
+                if (!__syncthreads_or(need)) continue;
+                staged += t == 0;
+                {   // candidate operand: row t of the supertile
+                    const int64_t cp = cs * T2 + t;
+                    float sq = 0.f;
+#pragma unroll
+                    for (int j = 0; j < KP / 8; ++j) {
+                        __align__(16) half_t v[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int r = 8 * j + e;
+                            const float x = r < MP ? a.xs[cp * MP + r] - scen[r] : 0.f;
+                            v[e] = HT::from(x);
+                            const float xb = HT::to(v[e]);
+                            sq = fmaf(xb, xb, sq);
+                        }
+                        *(uint4*)((char*)sb + tc::operand_offset(t, 8 * j, KP)) = *(const uint4*)v;
+                    }
+                    sqb[t] = sq;
+                }
+                tc::fence_async_smem();
+                tc::fence_before_sync();
+                __syncthreads();
+                tc::fence_after_sync();
+                if (t == 0) {
+                    constexpr uint32_t sbo = (uint32_t)(KP / 8) * 128;
+#pragma unroll
+                    for (int s = 0; s < KP / 16; ++s) {
+                        const uint64_t ad = tc::smem_desc(tc::smem_addr(sa) + s * 256, 128, sbo);
+                        const uint64_t bd = tc::smem_desc(tc::smem_addr(sb) + s * 256, 128, sbo);
+                        tc::mma_bf16(tb, ad, bd, tc::idesc_f16(128, 128, F16), s > 0 ? 1u : 0u);
+                    }
+                    tc::mma_commit(&bar);
+                }
+                const bool done = tc::mbar_wait(&bar, phase);
+                phase ^= 1u;
+                tc::fence_after_sync();
+                if (__syncthreads_or(!done)) {   // a bounded wait ran out: record it and stop
+                    if (t == 0) { report_error(a.rep, VB_ERR_TIMEOUT); s_abort = 1; }
+                    break;
+                }
+                if (need) evaluated += T2;
+#pragma unroll 1
+                for (int ch = 0; ch < T2 / 32; ++ch) {
+                    float v[32];
+                    tc::tmem_ld32(tb + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32), v);
+                    if (!need) continue;
+#pragma unroll 4
+                    for (int i = 0; i < 32; ++i) {
+                        const int c = ch * 32 + i;
+                        const int64_t cp = cs * T2 + c;
+                        const float d = fmaxf(sqa + sqb[c] - 2.f * v[i], 0.f);
+                        const uint64_t key = ((uint64_t)__float_as_uint(d) << 32) | (uint32_t)cp;
+                        if (key < heapmax && cp != p && cp >= qlo && cp < qhi) {
+                            sift_down<T2>(buf, t, 0, C, key, levels);
+                            heapmax = buf[t];
+                        }
+                    }
+                }
+                tc::fence_before_sync();
+                __syncthreads();
+            }
+            __syncthreads();
+        }
+        if (s_abort) break;
+
+        bool ok = true;
+        if (valid) {
+            const float e_lin = 2.f * delta, e_const = delta * delta + rho;
+            ok = finalize_row<MP, T2>(a, buf, t, C, true, p, qhi - qlo, 1, 0.f, levels, e_lin, e_const);
+        }
+        if (!ok) s_fail = 1;
+        __syncthreads();
+        if (t == 0 && s_fail) {
+            for (int h = 0; h < 2; ++h) {
+                const int64_t qt = 2 * qs + h;
+                if (qt < nt && atomicExch(&a.fail_flag[qt], 1) == 0) {
+                    a.fail_list[atomicAdd(a.fail_count, 1)] = (int)qt;
+                    atomicAdd(&a.rep->knn_retry_tiles, 1ull);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    unsigned long long ev = evaluated, lv = levels, st = staged;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ev += __shfl_xor_sync(0xffffffffu, ev, o);
+        lv += __shfl_xor_sync(0xffffffffu, lv, o);
+        st += __shfl_xor_sync(0xffffffffu, st, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&a.rep->knn_candidates, ev);
+        atomicAdd(&a.rep->knn_heap_levels, lv);
+        atomicAdd(&a.rep->knn_tiles_staged, st);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tb, 128);
+}
+
+// R2[pos] = (inflate * radius[perm[pos]])^2 for the sorted points (caller-provided radii).
+__global__ void radius_gather_kernel(const float* __restrict__ radius, const uint32_t* __restrict__ perm, int64_t n,
+                                     float inflate, float* r2)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float r = radius[perm[i]] * inflate;
+    r2[i] = __fmul_ru(r, r);
 }
 
 // ------------------------------------------------------------------ exact FP64 fallback rows
@@ -611,7 +1012,7 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
 // strictly smaller ones plus the lowest-index ties, ranked by (d2, index).
 __global__ void __launch_bounds__(FB_THREADS) knn_fallback_kernel(const float* __restrict__ x, int64_t n, int m,
                                                                    int k, const int* __restrict__ fb_list,
-                                                                   const int* __restrict__ fb_count,
+                                                                   const int* __restrict__ fb_count, Clouds cl,
                                                                    int32_t* nbr, double* nbr_d2)
 {
     __shared__ uint32_t hist[256];
@@ -624,13 +1025,15 @@ __global__ void __launch_bounds__(FB_THREADS) knn_fallback_kernel(const float* _
     for (int f = blockIdx.x; f < cnt; f += gridDim.x) {
         const int64_t q = fb_list[f];
         const float* xq = x + q * m;
+        const int cb = cloud_of(cl.ptr, cl.B, q);
+        const int64_t lo = cloud_lo(cl, cb), hi = cloud_hi(cl, cb, n);   // candidates: the query's cloud
         if (t == 0) { s_prefix = 0; s_mask = 0; s_need = (uint32_t)k; s_less = 0; }
         __syncthreads();
         for (int byte = 7; byte >= 0; --byte) {
             hist[t] = 0;
             __syncthreads();
             const uint64_t prefix = s_prefix, mask = s_mask;
-            for (int64_t j = t; j < n; j += FB_THREADS) {
+            for (int64_t j = lo + t; j < hi; j += FB_THREADS) {
                 if (j == q) continue;
                 uint64_t key = (uint64_t)__double_as_longlong(canon_d2(xq, x + j * m, m));
                 if ((key & mask) == prefix) atomicAdd(&hist[(key >> (8 * byte)) & 255u], 1u);
@@ -652,7 +1055,7 @@ __global__ void __launch_bounds__(FB_THREADS) knn_fallback_kernel(const float* _
         const uint64_t T = s_prefix;
         const uint32_t need = s_need;          // how many ties at T are taken
         const uint32_t nless = (uint32_t)k - need;
-        for (int64_t j = t; j < n; j += FB_THREADS) {
+        for (int64_t j = lo + t; j < hi; j += FB_THREADS) {
             if (j == q) continue;
             uint64_t key = (uint64_t)__double_as_longlong(canon_d2(xq, x + j * m, m));
             if (key < T) {
@@ -663,9 +1066,9 @@ __global__ void __launch_bounds__(FB_THREADS) knn_fallback_kernel(const float* _
         }
         __syncthreads();
         uint32_t taken = 0;
-        for (int64_t b0 = 0; b0 < n && taken < need; b0 += FB_THREADS) {
+        for (int64_t b0 = lo; b0 < hi && taken < need; b0 += FB_THREADS) {
             int64_t j = b0 + t;
-            bool fl = j < n && j != q &&
+            bool fl = j < hi && j != q &&
                       (uint64_t)__double_as_longlong(canon_d2(xq, x + j * m, m)) == T;
             unsigned bal = __ballot_sync(0xffffffffu, fl);
             if (lane == 0) s_wtot[w] = __popc(bal);
@@ -704,6 +1107,41 @@ static size_t tile_smem(int L)
 }
 
 template <int MP>
+static size_t radius_tc_smem(int C)
+{
+    constexpr int KP = MP < 16 ? 16 : MP;
+    return (size_t)2 * T2 * KP * 2 + T2 * 4 + SCAP * 8 + (size_t)C * T2 * 8;
+}
+
+template <int MP, bool F16>
+static vb_status launch_radius_tc(TileArgs a, cudaStream_t s)
+{
+    size_t sm = radius_tc_smem<MP>(a.cap);
+    if (sm > 220 * 1024) return VB_ERR_UNSUPPORTED;   // k + margin too large for 128 heaps with these operands
+    static bool attr_set[16] = {};
+    static int sms[16] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!attr_set[dev & 15]) {
+        if (cudaFuncSetAttribute(knn_radius_tc_kernel<MP, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(220 * 1024)) != cudaSuccess)
+            return VB_ERR_CUDA;
+        if (cudaDeviceGetAttribute(&sms[dev & 15], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return VB_ERR_CUDA;
+        attr_set[dev & 15] = true;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, knn_radius_tc_kernel<MP, F16>, T2, sm) != cudaSuccess ||
+        per_sm < 1)
+        return VB_ERR_CUDA;
+    per_sm = std::min(per_sm, 4);   // 128 TMEM columns per CTA, 512 per SM
+    const int64_t nst = (a.ntiles + 1) / 2;
+    const int64_t grid = std::min<int64_t>(nst, (int64_t)per_sm * sms[dev & 15]);
+    knn_radius_tc_kernel<MP, F16><<<(unsigned)grid, T2, sm, s>>>(a);
+    return last_launch();
+}
+
+template <int MP>
 static vb_status launch_tile(const TileArgs& a, cudaStream_t s)
 {
     size_t sm = tile_smem<MP>(a.L);
@@ -722,18 +1160,22 @@ static vb_status launch_tile(const TileArgs& a, cudaStream_t s)
 }
 
 vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_params* p, int32_t* nbr,
-                  double* nbr_d2, void* ws, size_t ws_bytes)
+                  double* nbr_d2, void* ws, size_t ws_bytes, Clouds cl)
 {
+    if (cl.B < 1 || (cl.B > 1 && !cl.ptr)) return VB_ERR_ARG;
     if (!x || !nbr || !nbr_d2 || !p || n < 2 || n >= INT32_MAX || m < 1 || m > 128) return VB_ERR_ARG;
     if (p->k < 1 || (int64_t)p->k > n - 1 || p->margin < 0 || p->k + p->margin > 256) return VB_ERR_ARG;
-    if (p->precision != VB_PREC_FP32) return VB_ERR_UNSUPPORTED;
+    if (p->precision < VB_PREC_FP32 || p->precision > VB_PREC_FP16) return VB_ERR_UNSUPPORTED;
+    if (p->precision != VB_PREC_FP32 && p->prune != VB_PRUNE_LEARNED) return VB_ERR_UNSUPPORTED;
+    if (p->prune == VB_PRUNE_LEARNED && !p->radius && !p->mlp) return VB_ERR_ARG;
+    if (p->prune < VB_PRUNE_NONE || p->prune > VB_PRUNE_LEARNED) return VB_ERR_ARG;
     KnnWs w;
     Carve c(ws);
     size_t need = knn_plan(c, n, m, p, &w);
     if (!ws || ws_bytes < need) return VB_ERR_WORKSPACE;
     cudaStream_t s = ctx->stream;
     const int mp = pad_dim(m), md = morton_dims(m), bits = morton_bits(md);
-    const int64_t ntiles = (n + TILE - 1) / TILE, npad = ntiles * TILE;
+    const int64_t ntiles = (n + TILE - 1) / TILE, npad = (ntiles + (ntiles & 1)) * TILE;
     const int nblk = (int)((n + RADIX_ITEMS - 1) / RADIX_ITEMS);
 
     mark(ctx, VB_STAGE_KNN_ORDER, 0);
@@ -748,6 +1190,20 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
                                                       shift, w.hist, nblk);
         cur ^= 1;
     }
+    if (cl.B > 1) {
+        // stable passes on the cloud id: (cloud, Morton) order, so cloud b occupies the sorted
+        // positions [ptr[b], ptr[b + 1]), the same range as its points in the input
+        cloud_key_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.val[cur], n, cl, w.key[cur]);
+        ctx->launches += 1;
+        for (int shift = 0; (int64_t)(cl.B - 1) >> shift; shift += 8) {
+            radix_hist_kernel<<<nblk, RADIX_T, 0, s>>>(w.key[cur], n, shift, w.hist, nblk);
+            scan_u32_single_kernel<<<1, 1024, 0, s>>>(w.hist, (int64_t)256 * nblk);
+            radix_scatter_kernel<<<nblk, RADIX_T, 0, s>>>(w.key[cur], w.val[cur], w.key[cur ^ 1], w.val[cur ^ 1], n,
+                                                          shift, w.hist, nblk);
+            cur ^= 1;
+            ctx->launches += 3;
+        }
+    }
     const uint32_t* perm = w.val[cur];
     gather_kernel<<<(unsigned)((npad * mp + 255) / 256), 256, 0, s>>>(x, perm, n, npad, m, mp, w.xs);
     tile_box_kernel<<<(unsigned)((ntiles * 32 + 255) / 256), 256, 0, s>>>(w.xs, n, ntiles, m, mp, w.tlo, w.thi);
@@ -755,16 +1211,68 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
     if (st != VB_OK) return st;
     mark(ctx, VB_STAGE_KNN_ORDER, 1);
 
-    TileArgs a;
+    TileArgs a = {};
     a.xs = w.xs; a.tlo = w.tlo; a.thi = w.thi; a.perm = perm; a.n = n; a.ntiles = ntiles;
     a.m = m; a.k = p->k; a.L = p->k + p->margin; a.prune = p->prune != VB_PRUNE_NONE;
     a.nseed = 1 + 2 * (int)((a.L + TILE) / TILE);   // enough neighbouring tiles to fill every heap
     a.lb_factor = 1.0f - 4.0f * (float)(m + 2) * 5.9604645e-8f;
     a.band = 1.0f + 4.0f * (float)(m + 2) * 5.9604645e-8f;
-    a.work = w.fb_count + 1;
     a.cert_factor = 1.0 - 2.0 * (double)(m + 2) * 5.9604644775390625e-8;
     a.nbr = nbr; a.nbr_d2 = nbr_d2; a.fb_list = w.fb_list; a.fb_count = w.fb_count; a.rep = ctx->rep;
-    mark(ctx, VB_STAGE_KNN_TILE, 0);
+    a.work = w.fb_count + 1;
+    a.cl = cl;
+    const bool radius_first = p->prune == VB_PRUNE_LEARNED;
+    int launches = 0;
+    if (radius_first) {
+        const float inflate = p->radius_inflate > 0.f ? p->radius_inflate : 1.5f;
+        if (p->mlp) {
+            st = mlp_radius_r2(s, p->mlp, w.xs, n, m, mp, p->radius_log_shift, inflate, w.r2);
+        } else {
+            radius_gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p->radius, perm, n, inflate, w.r2);
+            st = last_launch();
+        }
+        if (st != VB_OK) return st;
+        if (cudaMemsetAsync(w.fail_flag, 0, sizeof(int) * 2 * ntiles, s) != cudaSuccess) return VB_ERR_CUDA;
+        // counters: [1] pass-1 work, [2] heap-search work, [3] pass-1 failures, [4] pass-2 work, [5] pass-2 failures
+        a.r2 = w.r2;
+        mark(ctx, VB_STAGE_KNN_TILE, 0);
+        const bool tensor = p->precision == VB_PREC_BF16 || p->precision == VB_PREC_FP16;
+        const bool f16 = p->precision == VB_PREC_FP16;
+        a.r2_scale = 1.f;
+        a.work = w.fb_count + 1;
+        a.fail_flag = w.fail_flag;
+        a.fail_list = w.fail_list;
+        a.fail_count = w.fb_count + 3;
+        if (tensor) {
+            a.cap = a.L;
+            switch (mp) {
+                case 4: st = f16 ? launch_radius_tc<4, true>(a, s) : launch_radius_tc<4, false>(a, s); break;
+                case 8: st = f16 ? launch_radius_tc<8, true>(a, s) : launch_radius_tc<8, false>(a, s); break;
+                case 16: st = f16 ? launch_radius_tc<16, true>(a, s) : launch_radius_tc<16, false>(a, s); break;
+                case 32: st = f16 ? launch_radius_tc<32, true>(a, s) : launch_radius_tc<32, false>(a, s); break;
+                case 64: st = f16 ? launch_radius_tc<64, true>(a, s) : launch_radius_tc<64, false>(a, s); break;
+                default: st = f16 ? launch_radius_tc<128, true>(a, s) : launch_radius_tc<128, false>(a, s); break;
+            }
+        } else {
+            switch (mp) {
+                case 4: st = launch_tile<4>(a, s); break;
+                case 8: st = launch_tile<8>(a, s); break;
+                case 16: st = launch_tile<16>(a, s); break;
+                case 32: st = launch_tile<32>(a, s); break;
+                case 64: st = launch_tile<64>(a, s); break;
+                default: st = launch_tile<128>(a, s); break;
+            }
+        }
+        if (st != VB_OK) return st;
+        // tiles the radius could not settle: the exact search (seeded, no radius) on that list only
+        a.r2 = nullptr;
+        a.work = w.fb_count + 2;
+        a.tile_list = w.fail_list;
+        a.tile_count = w.fb_count + 3;
+        launches += 3;
+    } else {
+        mark(ctx, VB_STAGE_KNN_TILE, 0);
+    }
     switch (mp) {
         case 4: st = launch_tile<4>(a, s); break;
         case 8: st = launch_tile<8>(a, s); break;
@@ -776,7 +1284,8 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
     if (st != VB_OK) return st;
     mark(ctx, VB_STAGE_KNN_TILE, 1);
     mark(ctx, VB_STAGE_KNN_FALLBACK, 0);
-    knn_fallback_kernel<<<152, FB_THREADS, 0, s>>>(x, n, m, p->k, w.fb_list, w.fb_count, nbr, nbr_d2);
+    ctx->launches += launches;
+    knn_fallback_kernel<<<152, FB_THREADS, 0, s>>>(x, n, m, p->k, w.fb_list, w.fb_count, cl, nbr, nbr_d2);
     mark(ctx, VB_STAGE_KNN_FALLBACK, 1);
     ctx->launches += 19;
     return last_launch();

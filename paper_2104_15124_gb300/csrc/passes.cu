@@ -46,56 +46,90 @@ struct SweepConst {
     float negr[kMaxGrid];   // -2^-(xi_lo + g dxi)
 };
 
+// Segmented reductions: block bl of the fixed grid owns the rows [bl per, (bl + 1) per),
+// per = ceil(n / grid); the rows of each cloud inside that range form one segment,
+// whose sums go to slot bl + cloud.  Slots are disjoint, every slot holds one cloud's
+// rows, and cloud b's slots are bl + b for the blocks bl that meet it, so each
+// cloud's total is summed in a fixed order.
+__host__ __device__ inline int64_t rows_per_block(int64_t n, int nblk) { return (n + nblk - 1) / nblk; }
+inline size_t seg_slots(int B) { return (size_t)kRowBlocks + (size_t)B; }
+
+// Sum over cloud b's slots of column g of partial (slots of G values), in block order.
+__device__ __forceinline__ double seg_total_lane(const double* __restrict__ partial, int G, int g, const Clouds& cl,
+                                                 int b, int64_t n, int nblk, int lane)
+{
+    const int64_t per = rows_per_block(n, nblk);
+    const int64_t lo = cloud_lo(cl, b), hi = cloud_hi(cl, b, n);
+    const int64_t bl0 = lo / per, bl1 = (hi - 1) / per;
+    double s = 0.0;
+    for (int64_t bl = bl0 + lane; bl <= bl1; bl += 32) s += partial[(bl + b) * G + g];
+    return warp_sum_f64(s);
+}
+
 __global__ void __launch_bounds__(kRowThreads) sweep_kernel(const int64_t* __restrict__ row_ptr,
                                                           const int32_t* __restrict__ col,
                                                           const float* __restrict__ ed2, int64_t n,
                                                           const float* __restrict__ irho,
                                                           const double* __restrict__ xi_c_dev, double scale, int G,
-                                                          SweepConst sc, double* partial)
+                                                          SweepConst sc, Clouds cl, double* partial)
 {
     __shared__ double wacc[WARPS][kMaxGrid];
-    for (int i = threadIdx.x; i < WARPS * kMaxGrid; i += blockDim.x) (&wacc[0][0])[i] = 0.0;
-    __syncthreads();
-    const double xc = xi_c_dev ? *xi_c_dev : 0.0;
-    const float c0 = (float)(1.4426950408889634 / (scale * exp2(xc)));
+    __shared__ float s_c0;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t per = rows_per_block(n, gridDim.x);
+    const int64_t r0 = min(n, (int64_t)blockIdx.x * per), r1 = min(n, r0 + per);
+    if (r0 >= r1) return;
+    const int cf = cloud_of(cl.ptr, cl.B, r0), cla = cloud_of(cl.ptr, cl.B, r1 - 1);
     float acc[kMaxGrid];
+    for (int cb = cf; cb <= cla; ++cb) {
+        for (int i = threadIdx.x; i < WARPS * kMaxGrid; i += blockDim.x) (&wacc[0][0])[i] = 0.0;
+        if (threadIdx.x == 0) {
+            const double xc = xi_c_dev ? xi_c_dev[cb] : 0.0;
+            s_c0 = (float)(1.4426950408889634 / (scale * exp2(xc)));
+        }
+        __syncthreads();
+        const float c0 = s_c0;
+        const int64_t s0 = max(r0, cloud_lo(cl, cb)), s1 = min(r1, cloud_hi(cl, cb, n));
+        const int64_t pw = (s1 - s0 + WARPS - 1) / WARPS;
+        const int64_t a0 = min(s1, s0 + w * pw), a1 = min(s1, a0 + pw);
 #pragma unroll
-    for (int g = 0; g < kMaxGrid; ++g) acc[g] = 0.f;
-    RowIter it;
-    int since = 0;
-    auto flush = [&]() {
+        for (int g = 0; g < kMaxGrid; ++g) acc[g] = 0.f;
+        int since = 0;
+        auto flush = [&]() {
 #pragma unroll
-        for (int g = 0; g < kMaxGrid; ++g) {
-            if (g < G) {
-                float v = warp_sum_f32(acc[g]);
-                if (it.lane == 0) wacc[it.w][g] += (double)v;
+            for (int g = 0; g < kMaxGrid; ++g) {
+                if (g < G) {
+                    float v = warp_sum_f32(acc[g]);
+                    if (lane == 0) wacc[w][g] += (double)v;
+                }
+                acc[g] = 0.f;
             }
-            acc[g] = 0.f;
-        }
-    };
-    for (int64_t i = it.i; i < n; i += it.step) {
-        const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
-        const float ri = irho[i];
-        for (int64_t e = rb + it.lane; e < re; e += 32) {
-            const int32_t j = col[e];
-            if (j == i) continue;
-            const float u = ed2[e] * (ri * irho[j]) * c0;
+        };
+        for (int64_t i = a0; i < a1; ++i) {
+            const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
+            const float ri = irho[i];
+            for (int64_t e = rb + lane; e < re; e += 32) {
+                const int32_t j = col[e];
+                if (j == i) continue;
+                const float u = ed2[e] * (ri * irho[j]) * c0;
 #pragma unroll
-            for (int g = 0; g < kMaxGrid; ++g)
-                if (g < G) acc[g] += ex2_approx(u * sc.negr[g]);
+                for (int g = 0; g < kMaxGrid; ++g)
+                    if (g < G) acc[g] += ex2_approx(u * sc.negr[g]);
+            }
+            since += (int)(re - rb);
+            if (since >= FLUSH) {
+                flush();
+                since = 0;
+            }
         }
-        since += (int)(re - rb);
-        if (since >= FLUSH) {
-            flush();
-            since = 0;
+        flush();
+        __syncthreads();
+        for (int g = threadIdx.x; g < G; g += blockDim.x) {
+            double sum = 0.0;
+            for (int ww = 0; ww < WARPS; ++ww) sum += wacc[ww][g];
+            partial[((int64_t)blockIdx.x + cb) * G + g] = sum;
         }
-    }
-    flush();
-    __syncthreads();
-    for (int g = threadIdx.x; g < G; g += blockDim.x) {
-        double s = 0.0;
-        for (int w = 0; w < WARPS; ++w) s += wacc[w][g];
-        partial[(int64_t)blockIdx.x * G + g] = s;
+        __syncthreads();
     }
 }
 
@@ -112,87 +146,97 @@ __global__ void __launch_bounds__(kRowThreads, 3) sweep57_kernel(const int64_t* 
                                                             const float* __restrict__ ed2, int64_t n,
                                                             const float* __restrict__ irho,
                                                             const double* __restrict__ xi_c_dev, double scale,
-                                                            SweepConst sc, double* partial)
+                                                            SweepConst sc, Clouds cl, double* partial)
 {
     __shared__ double wacc[WARPS][G57];
-    for (int i = threadIdx.x; i < WARPS * G57; i += blockDim.x) (&wacc[0][0])[i] = 0.0;
-    __syncthreads();
-    const double xc = xi_c_dev ? *xi_c_dev : 0.0;
-    const float c0 = (float)(1.4426950408889634 / (scale * exp2(xc)));
+    __shared__ float s_c0;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t nwarps = (int64_t)gridDim.x * WARPS;
-    const int64_t gw = (int64_t)blockIdx.x * WARPS + w;
-    const int64_t per = (n + nwarps - 1) / nwarps;
-    const int64_t r0 = min(n, gw * per), r1 = min(n, r0 + per);
-    const int64_t e0 = row_ptr[r0], e1 = row_ptr[r1];
+    const int64_t per = rows_per_block(n, gridDim.x);
+    const int64_t r0 = min(n, (int64_t)blockIdx.x * per), r1 = min(n, r0 + per);
+    if (r0 >= r1) return;
+    const int cf = cloud_of(cl.ptr, cl.B, r0), cla = cloud_of(cl.ptr, cl.B, r1 - 1);
     float acc[G57];
+    for (int cb = cf; cb <= cla; ++cb) {
+        for (int i = threadIdx.x; i < WARPS * G57; i += blockDim.x) (&wacc[0][0])[i] = 0.0;
+        if (threadIdx.x == 0) {
+            const double xc = xi_c_dev ? xi_c_dev[cb] : 0.0;
+            s_c0 = (float)(1.4426950408889634 / (scale * exp2(xc)));
+        }
+        __syncthreads();
+        const float c0 = s_c0;
+        const int64_t s0 = max(r0, cloud_lo(cl, cb)), s1 = min(r1, cloud_hi(cl, cb, n));
+        const int64_t pw = (s1 - s0 + WARPS - 1) / WARPS;
+        const int64_t a0 = min(s1, s0 + w * pw), a1 = min(s1, a0 + pw);
+        const int64_t e0 = row_ptr[a0], e1 = row_ptr[a1];
 #pragma unroll
-    for (int g = 0; g < G57; ++g) acc[g] = 0.f;
-    int64_t i = r0;
-    int64_t inext = row_ptr[min(r0 + 1, n)];
-    float ri = r0 < n ? irho[r0] : 0.f;
-    int since = 0;
-    for (int64_t eb = e0; eb < e1; eb += 32) {
-        const int64_t e = eb + lane;
-        float u = INFINITY;
-        if (e < e1) {
-            while (inext <= e) {
-                ++i;
-                inext = row_ptr[i + 1];
-                ri = irho[i];
+        for (int g = 0; g < G57; ++g) acc[g] = 0.f;
+        int64_t i = a0;
+        int64_t inext = row_ptr[min(a0 + 1, n)];
+        float ri = a0 < n ? irho[a0] : 0.f;
+        int since = 0;
+        for (int64_t eb = e0; eb < e1; eb += 32) {
+            const int64_t e = eb + lane;
+            float u = INFINITY;
+            if (e < e1) {
+                while (inext <= e) {
+                    ++i;
+                    inext = row_ptr[i + 1];
+                    ri = irho[i];
+                }
+                const int32_t j = col[e];
+                if (j != i) u = ed2[e] * (ri * irho[j]) * c0;
             }
-            const int32_t j = col[e];
-            if (j != i) u = ed2[e] * (ri * irho[j]) * c0;
-        }
-        float prev[4];
+            float prev[4];
 #pragma unroll
-        for (int g = G57 - 1; g >= 0; --g) {
-            const int c = (G57 - 1 - g) & 3, step = (G57 - 1 - g) >> 2;
-            const float v = (step & 3) == 0 ? ex2_approx(u * sc.negr[g]) : prev[c] * prev[c];
-            prev[c] = v;
-            acc[g] += v;
-        }
-        if (++since == 32) {
-            since = 0;
+            for (int g = G57 - 1; g >= 0; --g) {
+                const int c = (G57 - 1 - g) & 3, step = (G57 - 1 - g) >> 2;
+                const float v = (step & 3) == 0 ? ex2_approx(u * sc.negr[g]) : prev[c] * prev[c];
+                prev[c] = v;
+                acc[g] += v;
+            }
+            if (++since == 32) {
+                since = 0;
 #pragma unroll
-            for (int g = 0; g < G57; ++g) {
-                float v = warp_sum_f32(acc[g]);
-                if (lane == 0) wacc[w][g] += (double)v;
-                acc[g] = 0.f;
+                for (int g = 0; g < G57; ++g) {
+                    float v = warp_sum_f32(acc[g]);
+                    if (lane == 0) wacc[w][g] += (double)v;
+                    acc[g] = 0.f;
+                }
             }
         }
-    }
 #pragma unroll
-    for (int g = 0; g < G57; ++g) {
-        float v = warp_sum_f32(acc[g]);
-        if (lane == 0) wacc[w][g] += (double)v;
-    }
-    __syncthreads();
-    for (int g = threadIdx.x; g < G57; g += blockDim.x) {
-        double sum = 0.0;
-        for (int ww = 0; ww < WARPS; ++ww) sum += wacc[ww][g];
-        partial[(int64_t)blockIdx.x * G57 + g] = sum;
+        for (int g = 0; g < G57; ++g) {
+            float v = warp_sum_f32(acc[g]);
+            if (lane == 0) wacc[w][g] += (double)v;
+        }
+        __syncthreads();
+        for (int g = threadIdx.x; g < G57; g += blockDim.x) {
+            double sum = 0.0;
+            for (int ww = 0; ww < WARPS; ++ww) sum += wacc[ww][g];
+            partial[((int64_t)blockIdx.x + cb) * G57 + g] = sum;
+        }
+        __syncthreads();
     }
 }
 
-// One block of 64 warps-worth of work: warp w sums grid columns w, w + 32, ... over
-// the block partials in a fixed lane-strided order, then 64 threads take one log
-// each and one warp finds the first maximiser of chi'.
+// One block per cloud: warp w sums grid columns w, w + 32, ... over the cloud's
+// slots in a fixed lane-strided order, then the threads take one log each and one
+// warp finds the first maximiser of chi'.
 __global__ void __launch_bounds__(1024) sweep_finish_kernel(const double* __restrict__ partial, int nblk, int G,
-                                                           int64_t n, double xi_lo, double dxi,
+                                                           int64_t n, Clouds cl, double xi_lo, double dxi,
                                                            const double* __restrict__ xi_c_dev, int warn_bit,
                                                            double* eps2, double* chi, double* dim, DevReport* rep)
 {
     __shared__ double sh[kMaxGrid], lg[kMaxGrid];
+    const int b = blockIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const double nb = (double)(cloud_hi(cl, b, n) - cloud_lo(cl, b));
     for (int g = w; g < G; g += 32) {
-        double s = 0.0;
-        for (int b = lane; b < nblk; b += 32) s += partial[(int64_t)b * G + g];
-        s = warp_sum_f64(s);
+        double s = seg_total_lane(partial, G, g, cl, b, n, nblk, lane);
         if (lane == 0) {
-            s += (double)n;   // diagonal entries: exp(0) = 1 each
+            s += nb;   // diagonal entries: exp(0) = 1 each
             sh[g] = s;
-            chi[g] = s;
+            chi[(int64_t)b * G + g] = s;
         }
     }
     __syncthreads();
@@ -213,33 +257,33 @@ __global__ void __launch_bounds__(1024) sweep_finish_kernel(const double* __rest
             if (ov > bv || (ov == bv && ob < best)) { bv = ov; best = ob; }
         }
         if (lane == 0) {
-            const double xc = xi_c_dev ? *xi_c_dev : 0.0;
-            *eps2 = exp2(xc + xi_lo + best * dxi);
-            *dim = 2.0 * bv;
+            const double xc = xi_c_dev ? xi_c_dev[b] : 0.0;
+            eps2[b] = exp2(xc + xi_lo + best * dxi);
+            dim[b] = 2.0 * bv;
             if (best == 0 || best == G - 2) atomicOr(&rep->warnings, warn_bit);
         }
     }
 }
 
-size_t sweep_ws_bytes(int64_t n)
+size_t sweep_ws_bytes(int64_t n, int B)
 {
     Carve c(nullptr);
     c.take<float>(n);
-    c.take<double>((size_t)kRowBlocks * kMaxGrid);
+    c.take<double>(seg_slots(B) * kMaxGrid);
     return c.off;
 }
 
 vb_status sweep_run(Ctx* ctx, const vb_graph* g, const double* rho, double scale, const double* xi_c_dev,
                     double xi_lo, double xi_hi, double dxi, int warn_bit, double* eps2, double* chi, double* dim,
-                    void* ws, size_t ws_bytes)
+                    void* ws, size_t ws_bytes, Clouds cl)
 {
     if (!g || !g->row_ptr || !g->col || !g->ed2 || g->n < 1 || !rho || !eps2 || !chi || !dim) return VB_ERR_ARG;
-    if (!(dxi > 0) || !(scale > 0)) return VB_ERR_ARG;
+    if (!(dxi > 0) || !(scale > 0) || cl.B < 1 || (cl.B > 1 && !cl.ptr)) return VB_ERR_ARG;
     const int G = (int)std::lround((xi_hi - xi_lo) / dxi) + 1;
     if (G < 3 || G > kMaxGrid) return VB_ERR_ARG;
     Carve c(ws);
     float* irho = c.take<float>(g->n);
-    double* partial = c.take<double>((size_t)kRowBlocks * kMaxGrid);
+    double* partial = c.take<double>(seg_slots(cl.B) * kMaxGrid);
     if (!ws || ws_bytes < c.off) return VB_ERR_WORKSPACE;
     SweepConst sc;
     for (int h = 0; h < kMaxGrid; ++h) sc.negr[h] = h < G ? -(float)std::exp2(-(xi_lo + h * dxi)) : 0.f;
@@ -249,29 +293,34 @@ vb_status sweep_run(Ctx* ctx, const vb_graph* g, const double* rho, double scale
     mark(ctx, stage, 0);
     if (G == G57 && dxi == 0.25)
         sweep57_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, g->n, irho, xi_c_dev, scale, sc,
-                                                          partial);
+                                                          cl, partial);
     else
         sweep_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, g->n, irho, xi_c_dev, scale, G, sc,
-                                                        partial);
+                                                        cl, partial);
     mark(ctx, stage, 1);
-    sweep_finish_kernel<<<1, 1024, 0, s>>>(partial, kRowBlocks, G, g->n, xi_lo, dxi, xi_c_dev, warn_bit, eps2, chi,
-                                           dim, ctx->rep);
+    sweep_finish_kernel<<<(unsigned)cl.B, 1024, 0, s>>>(partial, kRowBlocks, G, g->n, cl, xi_lo, dxi, xi_c_dev,
+                                                        warn_bit, eps2, chi, dim, ctx->rep);
     ctx->launches += 3;
     return last_launch();
 }
 
 // ------------------------------------------------------------------ a10 density
+// Per-cloud FP32 constant log2(e) / eps^2 of the density kernel.
+__global__ void density_const_kernel(const double* __restrict__ eps2, int B, float* c)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) c[b] = (float)(1.4426950408889634 / eps2[b]);
+}
+
 __global__ void __launch_bounds__(kRowThreads) density_kernel(const int64_t* __restrict__ row_ptr,
                                                             const int32_t* __restrict__ col,
                                                             const float* __restrict__ ed2, int64_t n,
-                                                            const double* __restrict__ b, const float* __restrict__ ib,
-                                                            const double* __restrict__ eps2_dev, double d, double beta,
-                                                            double* psi, double* P)
+                                                            const float* __restrict__ ib,
+                                                            const float* __restrict__ cden, Clouds cl, double* psi)
 {
-    const double e2 = *eps2_dev;
-    const float c = (float)(1.4426950408889634 / e2);
     RowIter it;
     for (int64_t i = it.i; i < n; i += it.step) {
+        const float c = cden[cloud_of(cl.ptr, cl.B, i)];
         const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
         const float bi = ib[i];
         float s = 0.f;
@@ -281,115 +330,131 @@ __global__ void __launch_bounds__(kRowThreads) density_kernel(const int64_t* __r
     }
 }
 
-// w_i = n (pi eps^2 b_i^2)^(d/2), psi_i = sum_i / w_i, P_i = psi_i^beta, one thread per point.
-// FP64 powers: P enters every operator-kernel exponent, so its error is multiplied
-// by exponents of up to about 60 in the smallest stored entries.
+// w_i = n_b (pi eps_b^2 b_i^2)^(d/2) with n_b and eps_b those of the point's cloud,
+// psi_i = sum_i / w_i, P_i = psi_i^beta, one thread per point.  FP64 powers: P enters
+// every operator-kernel exponent, so its error is multiplied by exponents of up to
+// about 60 in the smallest stored entries.
 __global__ void density_finish_kernel(const double* __restrict__ b, const double* __restrict__ eps2_dev, int64_t n,
-                                      double d, double beta, double* psi, double* P)
+                                      Clouds cl, double d, double beta, double* psi, double* P)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const int cb = cloud_of(cl.ptr, cl.B, i);
+    const double nb = (double)(cloud_hi(cl, cb, n) - cloud_lo(cl, cb));
     const double bb = b[i];
-    const double w = (double)n * pow(3.14159265358979323846 * *eps2_dev * bb * bb, 0.5 * d);
+    const double w = nb * pow(3.14159265358979323846 * eps2_dev[cb] * bb * bb, 0.5 * d);
     const double ps = psi[i] / w;
     psi[i] = ps;
     P[i] = pow(ps, beta);
 }
 
-size_t density_ws_bytes(int64_t n)
+size_t density_ws_bytes(int64_t n, int B)
 {
     Carve c(nullptr);
     c.take<float>(n);
+    c.take<float>(B);
     return c.off;
 }
 
 vb_status density_run(Ctx* ctx, const vb_graph* g, const double* b, const double* eps2_dev, double d, double beta,
-                      double* psi, double* P, void* ws, size_t ws_bytes)
+                      double* psi, double* P, void* ws, size_t ws_bytes, Clouds cl)
 {
     if (!g || !g->row_ptr || !b || !eps2_dev || !psi || !P || !(d > 0)) return VB_ERR_ARG;
+    if (cl.B < 1 || (cl.B > 1 && !cl.ptr)) return VB_ERR_ARG;
     Carve c(ws);
     float* ib = c.take<float>(g->n);
+    float* cden = c.take<float>(cl.B);
     if (!ws || ws_bytes < c.off) return VB_ERR_WORKSPACE;
+    cudaStream_t s = ctx->stream;
     mark(ctx, VB_STAGE_DENSITY, 0);
-    recip_f32_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, ctx->stream>>>(b, g->n, 1.f, ib);
-    density_kernel<<<kRowBlocks, kRowThreads, 0, ctx->stream>>>(g->row_ptr, g->col, g->ed2, g->n, b, ib, eps2_dev, d,
-                                                                beta, psi, P);
-    density_finish_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, ctx->stream>>>(b, eps2_dev, g->n, d, beta, psi, P);
+    recip_f32_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(b, g->n, 1.f, ib);
+    density_const_kernel<<<(unsigned)((cl.B + 255) / 256), 256, 0, s>>>(eps2_dev, cl.B, cden);
+    density_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, g->n, ib, cden, cl, psi);
+    density_finish_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(b, eps2_dev, g->n, cl, d, beta, psi, P);
     mark(ctx, VB_STAGE_DENSITY, 1);
-    ctx->launches += 3;
+    ctx->launches += 4;
     return last_launch();
 }
 
 // ------------------------------------------------------------------ operator-sweep centre
+// Segmented like the sweeps: slot bl + cloud holds the two sums of one cloud's rows.
 __global__ void __launch_bounds__(kRowThreads) centre_kernel(const int64_t* __restrict__ row_ptr,
                                                            const int32_t* __restrict__ col,
                                                            const float* __restrict__ ed2, int64_t n,
                                                            const float* __restrict__ ib,
-                                                           const float* __restrict__ iP, double* partial)
+                                                           const float* __restrict__ iP, Clouds cl, double* partial)
 {
     __shared__ double sh[WARPS][2];
-    RowIter it;
-    double a_op = 0.0, a_den = 0.0;
-    for (int64_t i = it.i; i < n; i += it.step) {
-        const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
-        const float pi_ = iP[i], bi = ib[i];
-        float so = 0.f, sd = 0.f;
-        for (int64_t e = rb + it.lane; e < re; e += 32) {
-            const int32_t j = col[e];
-            if (j == i) continue;
-            const float x = ed2[e];
-            so += x * (pi_ * iP[j]);
-            sd += x * (bi * ib[j]);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t per = rows_per_block(n, gridDim.x);
+    const int64_t r0 = min(n, (int64_t)blockIdx.x * per), r1 = min(n, r0 + per);
+    if (r0 >= r1) return;
+    const int cf = cloud_of(cl.ptr, cl.B, r0), cla = cloud_of(cl.ptr, cl.B, r1 - 1);
+    for (int cb = cf; cb <= cla; ++cb) {
+        const int64_t s0 = max(r0, cloud_lo(cl, cb)), s1 = min(r1, cloud_hi(cl, cb, n));
+        double a_op = 0.0, a_den = 0.0;
+        for (int64_t i = s0 + w; i < s1; i += WARPS) {
+            const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
+            const float pi_ = iP[i], bi = ib[i];
+            float so = 0.f, sd = 0.f;
+            for (int64_t e = rb + lane; e < re; e += 32) {
+                const int32_t j = col[e];
+                if (j == i) continue;
+                const float x = ed2[e];
+                so += x * (pi_ * iP[j]);
+                sd += x * (bi * ib[j]);
+            }
+            a_op += (double)so;
+            a_den += (double)sd;
         }
-        a_op += (double)so;
-        a_den += (double)sd;
-    }
-    a_op = warp_sum_f64(a_op);
-    a_den = warp_sum_f64(a_den);
-    if (it.lane == 0) { sh[it.w][0] = a_op; sh[it.w][1] = a_den; }
-    __syncthreads();
-    if (threadIdx.x < 2) {
-        double s = 0.0;
-        for (int w = 0; w < WARPS; ++w) s += sh[w][threadIdx.x];
-        partial[2 * (int64_t)blockIdx.x + threadIdx.x] = s;
+        a_op = warp_sum_f64(a_op);
+        a_den = warp_sum_f64(a_den);
+        if (lane == 0) { sh[w][0] = a_op; sh[w][1] = a_den; }
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            double sum = 0.0;
+            for (int ww = 0; ww < WARPS; ++ww) sum += sh[ww][threadIdx.x];
+            partial[2 * ((int64_t)blockIdx.x + cb) + threadIdx.x] = sum;
+        }
+        __syncthreads();
     }
 }
 
-__global__ void centre_finish_kernel(const double* __restrict__ partial, int nblk, double* xi_c)
+// One warp per cloud.
+__global__ void centre_finish_kernel(const double* __restrict__ partial, int nblk, int64_t n, Clouds cl, double* xi_c)
 {
-    const int lane = threadIdx.x;
-    double so = 0.0, sd = 0.0;
-    for (int b = lane; b < nblk; b += 32) { so += partial[2 * b]; sd += partial[2 * b + 1]; }
-    so = warp_sum_f64(so);
-    sd = warp_sum_f64(sd);
+    const int b = blockIdx.x, lane = threadIdx.x;
+    const double so = seg_total_lane(partial, 2, 0, cl, b, n, nblk, lane);
+    const double sd = seg_total_lane(partial, 2, 1, cl, b, n, nblk, lane);
     // R9: the operator argument is ed2 / (4 P_i P_j); so holds sum ed2 / (P_i P_j)
-    if (lane == 0) *xi_c = floor(4.0 * log2(0.25 * so / sd) + 0.5) / 4.0;
+    if (lane == 0) xi_c[b] = floor(4.0 * log2(0.25 * so / sd) + 0.5) / 4.0;
 }
 
-size_t centre_ws_bytes(int64_t n)
+size_t centre_ws_bytes(int64_t n, int B)
 {
     Carve c(nullptr);
     c.take<float>(n);
     c.take<float>(n);
-    c.take<double>((size_t)kRowBlocks * 2);
+    c.take<double>(seg_slots(B) * 2);
     return c.off;
 }
 
 vb_status centre_run(Ctx* ctx, const vb_graph* g, const double* b, const double* P, double* xi_c_dev, void* ws,
-                     size_t ws_bytes)
+                     size_t ws_bytes, Clouds cl)
 {
     if (!g || !g->row_ptr || !b || !P || !xi_c_dev) return VB_ERR_ARG;
+    if (cl.B < 1 || (cl.B > 1 && !cl.ptr)) return VB_ERR_ARG;
     Carve c(ws);
     float* ib = c.take<float>(g->n);
     float* iP = c.take<float>(g->n);
-    double* partial = c.take<double>((size_t)kRowBlocks * 2);
+    double* partial = c.take<double>(seg_slots(cl.B) * 2);
     if (!ws || ws_bytes < c.off) return VB_ERR_WORKSPACE;
     cudaStream_t s = ctx->stream;
     mark(ctx, VB_STAGE_CENTRE, 0);
     recip_f32_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(b, g->n, 1.f, ib);
     recip_f32_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(P, g->n, 1.f, iP);
-    centre_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, g->n, ib, iP, partial);
-    centre_finish_kernel<<<1, 32, 0, s>>>(partial, kRowBlocks, xi_c_dev);
+    centre_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, g->n, ib, iP, cl, partial);
+    centre_finish_kernel<<<(unsigned)cl.B, 32, 0, s>>>(partial, kRowBlocks, g->n, cl, xi_c_dev);
     mark(ctx, VB_STAGE_CENTRE, 1);
     ctx->launches += 4;
     return last_launch();
@@ -429,29 +494,35 @@ __device__ __forceinline__ float k_op(float x, float ahi, float ali, float ahj, 
     return ex2_approx(-uh) * fmaf(-ul, 0.6931471805599453f, 1.0f);
 }
 
-struct C1 {
-    float h, l;
+// Per-cloud constants of the operator kernel: c1 = log2(e) / (4 eps^2) as a float
+// pair (h, l), and 1 / eps^2.
+struct __align__(16) C1 {
+    float h, l, ie, pad;
 };
-__device__ __forceinline__ C1 c1_pair(const double* eps2_dev)
+__global__ void op_const_kernel(const double* __restrict__ eps2, int B, C1* out)
 {
-    const double c = 1.4426950408889634 / (4.0 * *eps2_dev);
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const double c = 1.4426950408889634 / (4.0 * eps2[b]);
     C1 r;
     r.h = (float)c;
     r.l = (float)(c - (double)r.h);
-    return r;
+    r.ie = (float)(1.0 / eps2[b]);
+    r.pad = 0.f;
+    out[b] = r;
 }
 
 __global__ void __launch_bounds__(kRowThreads) q_kernel(const int64_t* __restrict__ row_ptr,
                                                       const int32_t* __restrict__ col, const float* __restrict__ ed2,
                                                       int64_t n, const double* __restrict__ psi,
                                                       const float* __restrict__ iPh, const float* __restrict__ iPl,
-                                                      const double* __restrict__ eps2_dev, double beta, double d,
+                                                      const C1* __restrict__ cop, Clouds cl, double beta, double d,
                                                       double alpha, double* q, float* qa)
 {
-    const C1 c1 = c1_pair(eps2_dev);
     const float mbd = (float)(-beta * d), malpha = (float)(-alpha);
     RowIter it;
     for (int64_t i = it.i; i < n; i += it.step) {
+        const C1 c1 = cop[cloud_of(cl.ptr, cl.B, i)];
         const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
         const float ph = iPh[i], pl = iPl[i];
         float s = 0.f;
@@ -472,12 +543,12 @@ __global__ void __launch_bounds__(kRowThreads) d_kernel(const int64_t* __restric
                                                       const int32_t* __restrict__ col, const float* __restrict__ ed2,
                                                       int64_t n, const float* __restrict__ iPh,
                                                       const float* __restrict__ iPl, const float* __restrict__ qa,
-                                                      const double* __restrict__ P, const double* __restrict__ eps2_dev,
-                                                      double* D, double* S, float* iS)
+                                                      const double* __restrict__ P, const C1* __restrict__ cop,
+                                                      Clouds cl, double* D, double* S, float* iS)
 {
-    const C1 c1 = c1_pair(eps2_dev);
     RowIter it;
     for (int64_t i = it.i; i < n; i += it.step) {
+        const C1 c1 = cop[cloud_of(cl.ptr, cl.B, i)];
         const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
         const float ph = iPh[i], pl = iPl[i], qi = qa[i];
         float s = 0.f;
@@ -500,14 +571,14 @@ __global__ void __launch_bounds__(kRowThreads) lhat_kernel(const int64_t* __rest
                                                          const float* __restrict__ ed2, int64_t n,
                                                          const float* __restrict__ iPh, const float* __restrict__ iPl,
                                                          const float* __restrict__ qa, const float* __restrict__ iS,
-                                                         const double* __restrict__ S,
-                                                         const double* __restrict__ eps2_dev, float* val)
+                                                         const double* __restrict__ S, const C1* __restrict__ cop,
+                                                         const double* __restrict__ eps2_dev, Clouds cl, float* val)
 {
-    const double e2 = *eps2_dev;
-    const C1 c1 = c1_pair(eps2_dev);
-    const float ie = (float)(1.0 / e2);
     RowIter it;
     for (int64_t i = it.i; i < n; i += it.step) {
+        const int cb = cloud_of(cl.ptr, cl.B, i);
+        const C1 c1 = cop[cb];
+        const float ie = c1.ie;
         const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
         const float ph = iPh[i], pl = iPl[i], qi = qa[i], si = iS[i];
         float off = 0.f;
@@ -522,30 +593,32 @@ __global__ void __launch_bounds__(kRowThreads) lhat_kernel(const int64_t* __rest
         const double tot = warp_sum_f64((double)off);
         if (diag >= 0) {
             const double sii = S[i];
-            val[diag] = (float)(-tot / (e2 * sii * sii));
+            val[diag] = (float)(-tot / (eps2_dev[cb] * sii * sii));
         }
     }
 }
 
-size_t kernel_csr_ws_bytes(int64_t n)
+size_t kernel_csr_ws_bytes(int64_t n, int B)
 {
     Carve c(nullptr);
     for (int i = 0; i < 4; ++i) c.take<float>(n);
+    c.take<C1>(B);
     return c.off;
 }
 
 vb_status kernel_csr_run(Ctx* ctx, const vb_graph* g, const double* psi, const double* P, const vb_op_params* op,
                          const double* eps2_op_dev, float* val, double* q, double* D, double* S, void* ws,
-                         size_t ws_bytes)
+                         size_t ws_bytes, Clouds cl)
 {
     if (!g || !g->row_ptr || !psi || !P || !op || !eps2_op_dev || !val || !q || !D || !S) return VB_ERR_ARG;
-    if (!(op->d > 0)) return VB_ERR_ARG;
+    if (!(op->d > 0) || cl.B < 1 || (cl.B > 1 && !cl.ptr)) return VB_ERR_ARG;
     Carve c(ws);
     OpVec v;
     v.iPh = c.take<float>(g->n);
     v.iPl = c.take<float>(g->n);
     v.qa = c.take<float>(g->n);
     v.iS = c.take<float>(g->n);
+    C1* cop = c.take<C1>(cl.B);
     if (!ws || ws_bytes < c.off) return VB_ERR_WORKSPACE;
     // Sec. 2.2: c = 2 - 2 alpha + d beta + 2 beta
     const double alpha = (2.0 - op->c + op->d * op->beta + 2.0 * op->beta) / 2.0;
@@ -553,16 +626,17 @@ vb_status kernel_csr_run(Ctx* ctx, const vb_graph* g, const double* psi, const d
     const int64_t n = g->n;
     mark(ctx, VB_STAGE_OPERATOR, 0);
     recip_pair_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, n, v.iPh, v.iPl);
-    q_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, n, psi, v.iPh, v.iPl, eps2_op_dev, op->beta,
+    op_const_kernel<<<(unsigned)((cl.B + 255) / 256), 256, 0, s>>>(eps2_op_dev, cl.B, cop);
+    q_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, n, psi, v.iPh, v.iPl, cop, cl, op->beta,
                                                 op->d, alpha, q, v.qa);
-    d_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, n, v.iPh, v.iPl, v.qa, P, eps2_op_dev, D, S,
+    d_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, n, v.iPh, v.iPl, v.qa, P, cop, cl, D, S,
                                                 v.iS);
     mark(ctx, VB_STAGE_OPERATOR, 1);
     mark(ctx, VB_STAGE_LHAT, 0);
-    lhat_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, n, v.iPh, v.iPl, v.qa, v.iS, S,
-                                                   eps2_op_dev, val);
+    lhat_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, n, v.iPh, v.iPl, v.qa, v.iS, S, cop,
+                                                   eps2_op_dev, cl, val);
     mark(ctx, VB_STAGE_LHAT, 1);
-    ctx->launches += 4;
+    ctx->launches += 5;
     return last_launch();
 }
 

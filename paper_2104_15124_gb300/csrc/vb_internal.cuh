@@ -15,7 +15,13 @@ struct DevReport {
     unsigned long long knn_fallback_rows;
     unsigned long long knn_candidates;
     unsigned long long union_big_rows;
-    long long reserved[4];
+    unsigned long long knn_heap_levels;
+    unsigned long long knn_tiles_staged;
+    unsigned long long knn_insert_rounds;
+    unsigned long long knn_retry_tiles;
+    unsigned long long knn_rows_short;
+    unsigned long long knn_rows_long_run;
+    unsigned long long knn_rows_uncertified;
 };
 static_assert(sizeof(DevReport) == sizeof(vb_report), "report layout");
 
@@ -89,6 +95,28 @@ __device__ __forceinline__ float lg2_approx(float x)
 // x^y = 2^(y log2 x) for x > 0 on the SFU; relative error about |y log2 x| 2^-22.
 __device__ __forceinline__ float pow_sfu(float x, float y) { return ex2_approx(y * lg2_approx(x)); }
 
+// ------------------------------------------------------------------ point clouds of a batched build
+// Cloud b holds the points [ptr[b], ptr[b + 1]) (device array of B + 1 entries);
+// B == 1 with ptr == nullptr is the single cloud [0, n).
+struct Clouds {
+    const int64_t* ptr = nullptr;
+    int32_t B = 1;
+};
+// The cloud that holds point i: the largest b with ptr[b] <= i.
+__device__ __forceinline__ int cloud_of(const int64_t* __restrict__ ptr, int B, int64_t i)
+{
+    if (B <= 1) return 0;
+    int lo = 0, hi = B;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (ptr[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+__device__ __forceinline__ int64_t cloud_lo(const Clouds& c, int b) { return c.B <= 1 ? 0 : c.ptr[b]; }
+__device__ __forceinline__ int64_t cloud_hi(const Clouds& c, int b, int64_t n) { return c.B <= 1 ? n : c.ptr[b + 1]; }
+
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr int kMaxGrid = 64;          // epsilon sweep grid points per launch
 constexpr int kRowBlocks = 152 * 8;   // fixed grid of the row passes (deterministic reductions)
@@ -98,32 +126,37 @@ constexpr int kRowThreads = 256;
 // kNN (knn.cu)
 size_t knn_plan(Carve& c, int64_t n, int32_t m, const vb_knn_params* p, struct KnnWs* w);
 vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_params* p, int32_t* nbr,
-                  double* nbr_d2, void* ws, size_t ws_bytes);
+                  double* nbr_d2, void* ws, size_t ws_bytes, Clouds cl = Clouds());
 // symmetric union (graph.cu)
 size_t graph_plan_bytes(int64_t n, int32_t k);
 vb_status graph_run(Ctx* ctx, int64_t n, int32_t k, const int32_t* nbr, const double* nbr_d2, int64_t* row_ptr,
                     int32_t* col, float* ed2, int64_t cap, int64_t* nnz_dev, void* ws, size_t ws_bytes);
 vb_status bandwidth_run(Ctx* ctx, int64_t n, int32_t k, int32_t k_bw, const double* nbr_d2, double* b);
 // row passes (passes.cu)
-size_t sweep_ws_bytes(int64_t n);
+// Per-cloud scalars (eps^2, xi_c, chi, dimension) are arrays of cl.B entries (chi: cl.B x G).
+size_t sweep_ws_bytes(int64_t n, int B = 1);
 vb_status sweep_run(Ctx* ctx, const vb_graph* g, const double* rho, double scale, const double* xi_c_dev,
                     double xi_lo, double xi_hi, double dxi, int warn_bit, double* eps2, double* chi, double* dim,
-                    void* ws, size_t ws_bytes);
-size_t density_ws_bytes(int64_t n);
+                    void* ws, size_t ws_bytes, Clouds cl = Clouds());
+size_t density_ws_bytes(int64_t n, int B = 1);
 vb_status density_run(Ctx* ctx, const vb_graph* g, const double* b, const double* eps2_dev, double d, double beta,
-                      double* psi, double* P, void* ws, size_t ws_bytes);
-size_t centre_ws_bytes(int64_t n);
+                      double* psi, double* P, void* ws, size_t ws_bytes, Clouds cl = Clouds());
+size_t centre_ws_bytes(int64_t n, int B = 1);
 vb_status centre_run(Ctx* ctx, const vb_graph* g, const double* b, const double* P, double* xi_c_dev, void* ws,
-                     size_t ws_bytes);
-size_t kernel_csr_ws_bytes(int64_t n);
+                     size_t ws_bytes, Clouds cl = Clouds());
+size_t kernel_csr_ws_bytes(int64_t n, int B = 1);
 vb_status kernel_csr_run(Ctx* ctx, const vb_graph* g, const double* psi, const double* P, const vb_op_params* op,
                          const double* eps2_op_dev, float* val, double* q, double* D, double* S, void* ws,
-                         size_t ws_bytes);
+                         size_t ws_bytes, Clouds cl = Clouds());
 size_t spmv_ws_bytes(int64_t n);
 vb_status spmv_lap_launch(cudaStream_t s, const vb_graph* g, const float* val, const double* S, float alpha,
                           const float* x, float beta, float* y, double* z, float* sf);
 vb_status spmv_run(Ctx* ctx, const vb_graph* g, const float* val, const double* S, int mode, float alpha,
                    const float* x, float beta, float* y, void* ws, size_t ws_bytes);
+
+// learned radius (mlp.cu): R2[pos] = (inflate exp(net(xs[pos]) + shift))^2 for sorted points
+vb_status mlp_radius_r2(cudaStream_t s, const vb_mlp* mlp, const float* xs, int64_t n, int m, int mp, float shift,
+                        float inflate, float* r2);
 
 // eigen-solve (solve.cu)
 size_t solve_ws_bytes(int64_t n, int64_t cap, const vb_solve_params* p);

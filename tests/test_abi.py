@@ -19,7 +19,7 @@ def lib():
 def _declared():
     src = open(os.path.join(ROOT, "include", "vb.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:vb_status|size_t|const char\*)\s+(vb_\w+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:vb_status|size_t|int64_t|const char\*)\s+(vb_\w+)\s*\(", src, flags=re.M)))
 
 
 def test_every_declared_symbol_is_exported(lib):

@@ -1,0 +1,116 @@
+"""The learned radius (step a7) and the radius-first kNN search it feeds.
+
+* The network's gradient (our forward/backward kernels, BF16 weights, FP32
+  arithmetic) matches the FP64 oracle's chain rule at the same weights.
+* Training with our Adam kernel fits log r_k of a torus sample.
+* The radius-first search is exact whatever the radius: learned, exact,
+  too small (every tile retried by the exact search) or too large (the
+  heaps' own running threshold takes over).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import knn as OK
+from oracle import mlp as OM
+from paper_2104_15124_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vb():
+    import paper_2104_15124_gb300 as vb
+    from paper_2104_15124_gb300 import native
+    native.compile_library()
+    vb.lib()
+    return vb
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def test_mlp_gradient_matches_fp64_oracle(vb):
+    x = W.torus4(4096, 0.01, 31)
+    y = np.random.default_rng(2).standard_normal(4096).astype(np.float32) * 0.3 - 2.0
+    net = vb.Mlp(4, seed=7)
+    mean, scale = x.mean(0), x.std(0)
+    net.set_standardisation(mean, scale, -2.0, 0.3)
+    g, loss = net.gradient(_t(x), _t(y))
+    theta = net.bf16_weights().cpu().numpy().astype(np.float64)
+    Xs = (x.astype(np.float64) - mean.astype(np.float32)) / scale.astype(np.float32)
+    Ys = (y.astype(np.float64) + 2.0) / 0.3
+    ref_loss, ref_g = OM.loss_and_grad(theta, Xs, Ys)
+    assert abs(loss.item() - ref_loss) <= 1e-4 * ref_loss
+    gg = g.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(gg - ref_g) <= 2e-3 * np.linalg.norm(ref_g)
+    # predictions: our BF16 forward against the FP64 forward at the same weights
+    pred = net.predict(_t(x)).cpu().numpy()
+    np.testing.assert_allclose(pred, -2.0 + 0.3 * OM.forward(theta, Xs), rtol=0, atol=1e-4)
+
+
+def test_training_fits_log_radius(vb):
+    # von Mises-Fisher on S^2 (kappa = 2): the density, hence r_k, varies about 7-fold from pole to pole
+    x = W.sphere_vmf(20000, 2.0, 103)
+    k = 64
+    nbr, d2 = vb.knn(_t(x), k)
+    logr = 0.5 * torch.log(d2[:, k - 1]).float()
+    net = vb.train_radius_model(_t(x), logr, epochs=25, batch=2048, lr=3e-3, seed=103)
+    pred = net.predict(_t(x))
+    resid = (pred - logr).float()
+    # the fit explains most of the spread of log r_k around its mean
+    assert resid.pow(2).mean().item() < 0.6 * (logr - logr.mean()).pow(2).mean().item() + 1e-4
+
+
+@pytest.mark.parametrize("mode", ["exact", "small", "large"])
+def test_radius_search_exact_for_any_radius(vb, mode):
+    w = W.VMF_50K
+    x = w.sample(20000)
+    k = 32
+    ref_nbr, ref_d2 = OK.knn(x, k)
+    rk = np.sqrt(ref_d2[:, k - 1]).astype(np.float32)
+    if mode == "exact":
+        radius, infl = rk, 1.0001
+    elif mode == "small":
+        radius, infl = np.full_like(rk, 0.3 * float(np.median(rk))), 1.0
+    else:
+        radius, infl = np.full_like(rk, 3.0 * float(rk.max())), 1.0
+    vb.report_reset()
+    nbr, d2 = vb.knn(_t(x), k, radius=_t(radius), inflate=infl)
+    torch.cuda.synchronize()
+    rep = vb.raise_on_device_error()
+    assert np.array_equal(nbr.cpu().numpy(), ref_nbr)
+    assert np.array_equal(d2.cpu().numpy(), ref_d2)
+    ntiles = (x.shape[0] + 63) // 64
+    if mode == "small":
+        assert rep["knn_retry_tiles"] == ntiles   # nobody finds k points inside: all redone exactly
+    else:
+        assert rep["knn_retry_tiles"] == 0        # a loose radius only loosens the initial pruning
+
+
+def test_learned_radius_search_exact_and_prunes(vb):
+    k = 64
+    xt_train = _t(W.torus4(100000, 0.01, 103))
+    nbr, d2 = vb.knn(xt_train, k)
+    net = vb.train_radius_model(xt_train, 0.5 * torch.log(d2[:, k - 1]).float(), epochs=20, batch=4096, seed=103)
+    n = 200000
+    x = W.torus4(n, 0.01, 3)
+    shift = math.log(100000 / n) / 2.0        # r_k scales like n^(-1/d), d = 2
+    vb.report_reset()
+    nbr_l, d2_l = vb.knn(_t(x), k, mlp=net, log_shift=shift, inflate=1.5)
+    torch.cuda.synchronize()
+    rep_l = vb.raise_on_device_error()
+    vb.report_reset()
+    nbr_p, d2_p = vb.knn(_t(x), k)
+    torch.cuda.synchronize()
+    rep_p = vb.raise_on_device_error()
+    assert torch.equal(nbr_l, nbr_p) and torch.equal(d2_l, d2_p)
+    rows = np.sort(np.random.default_rng(5).choice(n, 800, replace=False))
+    ref_nbr, ref_d2 = OK.knn_rows(x, k, rows)
+    assert np.array_equal(nbr_l.cpu().numpy()[rows], ref_nbr)
+    # the learned radius settles most tiles and evaluates fewer candidates than the exact heap search
+    assert rep_l["knn_retry_tiles"] < 0.05 * ((n + 63) // 64)
+    assert rep_l["knn_candidates"] < rep_p["knn_candidates"]

@@ -1,0 +1,56 @@
+"""The tensor-core tile primitive (tcgen05.mma, BF16 operands, FP32 accumulation in
+tensor memory) against an FP64 product of the same BF16-rounded operands."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16(a):
+    return torch.from_numpy(a).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+@pytest.mark.parametrize("K,N", [(16, 128), (48, 64), (112, 128), (128, 32)])
+def test_tc_dot_tile_matches_fp64(K, N):
+    import paper_2104_15124_gb300 as vb
+    from paper_2104_15124_gb300 import native
+    native.compile_library()
+    rng = np.random.default_rng(K + N)
+    a = rng.standard_normal((128, K)).astype(np.float32)
+    b = rng.standard_normal((N, K)).astype(np.float32)
+    d = vb.tc_dot_tile(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()).cpu().numpy()
+    vb.raise_on_device_error()
+    ref = _bf16(a) @ _bf16(b).T
+    # products of BF16 values are exact in FP32; only the FP32 sums round
+    bound = 4 * K * 2.0 ** -24 * (np.abs(_bf16(a)) @ np.abs(_bf16(b)).T)
+    assert np.all(np.abs(d - ref) <= bound + 1e-30)
+
+
+def _knn_ref(x, k):
+    from oracle import knn as OK
+    return OK.knn(x, k)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("name,n,k,m", [("vmf", 20000, 32, 3), ("torus", 9000, 64, 4), ("gauss100", 3000, 32, 100)])
+def test_tensor_core_knn_is_exact(name, n, k, m, prec):
+    """The radius-first search with 16-bit tensor-core distance tiles returns the exact
+    FP64 neighbour lists (certificate with the tiles' error bound, FP64 rescoring)."""
+    import paper_2104_15124_gb300 as vb
+    from paper_2104_15124_gb300 import workloads as W
+    x = {"vmf": lambda: W.sphere_vmf(n, 2.0, 21), "torus": lambda: W.torus4(n, 0.01, 22),
+         "gauss100": lambda: W.gauss_embedded(n, 5, 100, 1e-3, 23).x}[name]()
+    ref_nbr, ref_d2 = _knn_ref(x, k)
+    rk = np.sqrt(ref_d2[:, k - 1]).astype(np.float32)
+    xt = torch.from_numpy(x).cuda()
+    vb.report_reset()
+    nbr, d2 = vb.knn(xt, k, radius=torch.from_numpy(rk).cuda(), inflate=1.3, tensor_cores=prec)
+    torch.cuda.synchronize()
+    rep = vb.raise_on_device_error()
+    assert np.array_equal(nbr.cpu().numpy(), ref_nbr)
+    assert np.array_equal(d2.cpu().numpy(), ref_d2)
+    # with FP16 tiles the tensor-core pass settles most tiles itself; BF16's 8-bit significand
+    # leaves error bands wider than the neighbour spacing, whose rows the exact search redoes
+    if prec == "fp16":
+        assert rep["knn_retry_tiles"] <= 0.25 * ((n + 63) // 64), rep["knn_retry_tiles"]
