@@ -145,7 +145,26 @@ typedef struct {
     const vb_mlp* mlp;       /* VB_PRUNE_LEARNED: learned radius model (NULL = use `radius`) */
     float radius_inflate;    /* factor applied to every radius guess (0 = 1.5) */
     float radius_log_shift;  /* added to the model's predicted log radius, e.g. ln(n_train / n) / d */
+    const float* cloud_log_shift;  /* batched build with a model: device array of B shifts added per
+                                      cloud, e.g. ln(n_train / n_b) / d (NULL = none) */
+    int32_t seed_tiles;      /* exact FP32 search: neighbouring tiles on each side of a query tile that are
+                                searched before any pruning (0 = enough to fill every heap) */
 } vb_knn_params;
+
+/* Launch-shape autotuner (a16).  Times vb_knn on the caller's input for every
+ * candidate shape -- heap depth k + margin with margin in {4, 8, 16, 32} and
+ * seed_tiles in {1, 2, 3} for the FP32 search, the margin alone for 16-bit tiles --
+ * with CUDA events on the context's stream (synchronising), and writes the
+ * fastest into *best (a copy of *p with margin and seed_tiles set) and its time
+ * into *best_ms.  Results are cached for the process by (m, k, precision, prune,
+ * floor(log2 n)); a cached key returns at once without running anything (then
+ * *best_ms = 0).  nbr / nbr_d2 / ws as for vb_knn, sized for k; every result is
+ * exact, so the outputs hold the neighbour lists afterwards.  cloud_ptr_dev / B
+ * describe a batch as in vb_build_batch (NULL / 1 for one cloud); the cache key
+ * then uses the mean cloud size. */
+vb_status vb_knn_autotune(vb_ctx* ctx, const float* x, int64_t n, int32_t m, const int64_t* cloud_ptr_dev,
+                          int32_t B, const vb_knn_params* p, int32_t* nbr, double* nbr_d2, void* ws,
+                          size_t ws_bytes, vb_knn_params* best, float* best_ms);
 
 /* Workspace bytes vb_knn() needs for n points in R^m. */
 size_t vb_knn_workspace(int64_t n, int32_t m, const vb_knn_params* p);
@@ -376,6 +395,29 @@ typedef struct {
 size_t vb_build_workspace(int64_t n, int32_t m, const vb_build_params* p);
 vb_status vb_build(vb_ctx* ctx, const float* x, int64_t n, int32_t m, const vb_build_params* p,
                    const vb_build_out* out, void* ws, size_t ws_bytes);
+
+/* ------------------------------------------------- batched build (a16)
+ * B independent point clouds in one build: cloud b is the rows
+ * [cloud_ptr[b], cloud_ptr[b + 1]) of x, and every step of vb_build is applied
+ * to each cloud on its own (Sec. 4 steps 1-3 per cloud: neighbours only within
+ * the cloud, its own n_b in the density, its own bandwidth sweeps).  Each stage
+ * is one launch over all clouds: the kNN sorts by (cloud, Morton key) and each
+ * query tile searches only the tiles of its clouds; every reduction is
+ * segmented per cloud with a fixed order, so a cloud's results do not depend on
+ * the other clouds beyond rounding order of its own sums.  No host
+ * synchronisation happens inside, so the call can be recorded in a CUDA graph.
+ *   cloud_ptr_host: B + 1 host int64 (read during the call for validation: 0 =
+ *     cloud_ptr[0] < ... < cloud_ptr[B] = n, every n_b >= knn.k + 1);
+ *   cloud_ptr_dev: the same values on the device (used by the kernels; it must
+ *     stay valid until the work completes).
+ * Outputs as in vb_build over all n points; the CSR is block-diagonal with global
+ * column indices; eps2_den, dim_den, xi_c, eps2_op, dim_op hold B values and
+ * chi_den, chi_op B x G (row b = cloud b).  With pin_eps, eps2_den / eps2_op
+ * hold the B pinned values.  VB_ERR_ARG for an invalid cloud_ptr. */
+size_t vb_build_batch_workspace(int64_t n, int32_t m, int32_t B, const vb_build_params* p);
+vb_status vb_build_batch(vb_ctx* ctx, const float* x, int64_t n, int32_t m, const int64_t* cloud_ptr_host,
+                         const int64_t* cloud_ptr_dev, int32_t B, const vb_build_params* p,
+                         const vb_build_out* out, void* ws, size_t ws_bytes);
 
 #ifdef __cplusplus
 }

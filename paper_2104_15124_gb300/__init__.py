@@ -13,6 +13,8 @@ import dataclasses
 import os
 import threading
 
+import numpy as np
+
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -42,7 +44,8 @@ c_i32, c_i64, c_f32, c_f64, c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_floa
 
 class KnnParams(ctypes.Structure):
     _fields_ = [("k", c_i32), ("margin", c_i32), ("precision", c_i32), ("prune", c_i32), ("radius", c_p),
-                ("mlp", c_p), ("radius_inflate", c_f32), ("radius_log_shift", c_f32)]
+                ("mlp", c_p), ("radius_inflate", c_f32), ("radius_log_shift", c_f32), ("cloud_log_shift", c_p),
+                ("seed_tiles", c_i32)]
 
 
 class GraphC(ctypes.Structure):
@@ -93,6 +96,8 @@ _SIGS = {
     "vb_profile_read": (c_i32, [c_p, ctypes.POINTER(c_f32), ctypes.POINTER(c_i64)]),
     "vb_knn_workspace": (c_sz, [c_i64, c_i32, ctypes.POINTER(KnnParams)]),
     "vb_knn": (c_i32, [c_p, c_p, c_i64, c_i32, ctypes.POINTER(KnnParams), c_p, c_p, c_p, c_sz]),
+    "vb_knn_autotune": (c_i32, [c_p, c_p, c_i64, c_i32, c_p, c_i32, ctypes.POINTER(KnnParams), c_p, c_p, c_p,
+                                c_sz, ctypes.POINTER(KnnParams), ctypes.POINTER(c_f32)]),
     "vb_graph_workspace": (c_sz, [c_i64, c_i32]),
     "vb_graph_build": (c_i32, [c_p, c_i64, c_i32, c_p, c_p, c_p, c_p, c_p, c_i64, c_p, c_p, c_sz]),
     "vb_bandwidth": (c_i32, [c_p, c_i64, c_i32, c_i32, c_p, c_p]),
@@ -122,6 +127,9 @@ _SIGS = {
     "vb_tc_dot_tile": (c_i32, [c_p, c_p, c_p, c_i32, c_i32, c_p]),
     "vb_build_workspace": (c_sz, [c_i64, c_i32, ctypes.POINTER(BuildParams)]),
     "vb_build": (c_i32, [c_p, c_p, c_i64, c_i32, ctypes.POINTER(BuildParams), ctypes.POINTER(BuildOut), c_p, c_sz]),
+    "vb_build_batch_workspace": (c_sz, [c_i64, c_i32, c_i32, ctypes.POINTER(BuildParams)]),
+    "vb_build_batch": (c_i32, [c_p, c_p, c_i64, c_i32, ctypes.POINTER(c_i64), c_p, c_i32, ctypes.POINTER(BuildParams),
+                               ctypes.POINTER(BuildOut), c_p, c_sz]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -477,48 +485,113 @@ class Build:
 
 class Builder:
     """Holds the output and workspace buffers of vb_build for one problem size, so
-    repeated builds (and timing loops) allocate nothing."""
+    repeated builds (and timing loops) allocate nothing.
+
+    With cloud_ptr (B + 1 offsets of the rows of each point cloud) it runs the
+    batched build vb_build_batch: every per-cloud scalar output then holds B
+    values (chi: B x G) and the CSR is block-diagonal.  cloud_log_shift (B floats)
+    adds a per-cloud term to a learned radius.  graph() records one build in a
+    CUDA graph for replay."""
 
     def __init__(self, n: int, m: int, k: int, d: float, c: float, beta: float = -0.25, margin: int = 16,
                  k_bw: int | None = None, prune: bool = True, device=None, grid=(XI_LO, XI_HI, DXI),
                  mlp: "Mlp | None" = None, log_shift: float = 0.0, inflate: float = 0.0,
-                 tensor_cores: str | None = None):
+                 tensor_cores: str | None = None, cloud_ptr=None, cloud_log_shift=None):
         dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.n, self.m, self.k, self.device = n, m, k, dev
         self.mlp = mlp   # kept alive: the C parameters point at it
         G = int(round((grid[1] - grid[0]) / grid[2])) + 1
+        self.batched = cloud_ptr is not None
+        if self.batched:
+            cp = np.asarray(cloud_ptr, dtype=np.int64)
+            if cp.ndim != 1 or len(cp) < 2 or cp[0] != 0 or cp[-1] != n or np.any(np.diff(cp) < k + 1):
+                raise ValueError("cloud_ptr must rise from 0 to n with at least k + 1 points per cloud")
+            self.B = len(cp) - 1
+            self._cp_host = (c_i64 * len(cp))(*cp.tolist())
+            self.cloud_ptr = torch.from_numpy(cp).to(dev)
+        else:
+            self.B = 1
+        B = self.B
+        self._shift = None
+        if cloud_log_shift is not None:
+            self._shift = torch.as_tensor(np.asarray(cloud_log_shift, dtype=np.float32)).to(dev).contiguous()
+            if self._shift.numel() != B:
+                raise ValueError("cloud_log_shift needs one value per cloud")
         mode = VB_PRUNE_LEARNED if mlp is not None else (VB_PRUNE_EXACT if prune else VB_PRUNE_NONE)
         prec = {None: VB_PREC_FP32, "bf16": VB_PREC_BF16, "fp16": VB_PREC_FP16}[tensor_cores]
         self.params = BuildParams(KnnParams(k, margin, prec, mode, c_p(0),
-                                            c_p(0) if mlp is None else c_p(mlp.handle()), inflate, log_shift),
+                                            c_p(0) if mlp is None else c_p(mlp.handle()), inflate, log_shift,
+                                            _p(self._shift)),
                                   0 if k_bw is None else k_bw, OpParams(c, beta, d), grid[0], grid[1], grid[2], 0)
         cap = n * (2 * k + 1)
         f64 = lambda s: torch.empty(s, dtype=torch.float64, device=dev)
         g = Graph(n, torch.empty(n + 1, dtype=torch.int64, device=dev), torch.empty(cap, dtype=torch.int32, device=dev),
                   torch.empty(cap, dtype=torch.float32, device=dev), torch.empty(1, dtype=torch.int64, device=dev))
+        chi = (B, G) if self.batched else G
         self.out = Build(nbr=torch.empty((n, k), dtype=torch.int32, device=dev), nbr_d2=f64((n, k)), b=f64(n), graph=g,
-                         eps2_den=f64(1), chi_den=f64(G), dim_den=f64(1), psi=f64(n), P=f64(n), xi_c=f64(1),
-                         eps2_op=f64(1), chi_op=f64(G), dim_op=f64(1),
+                         eps2_den=f64(B), chi_den=f64(chi), dim_den=f64(B), psi=f64(n), P=f64(n), xi_c=f64(B),
+                         eps2_op=f64(B), chi_op=f64(chi), dim_op=f64(B),
                          val=torch.empty(cap, dtype=torch.float32, device=dev), q=f64(n), D=f64(n), S=f64(n))
         o = self.out
         self.cout = BuildOut(_p(o.nbr), _p(o.nbr_d2), _p(o.b), _p(g.row_ptr), _p(g.col), _p(g.ed2), cap, _p(g.nnz_dev),
                              _p(o.eps2_den), _p(o.chi_den), _p(o.dim_den), _p(o.psi), _p(o.P), _p(o.xi_c),
                              _p(o.eps2_op), _p(o.chi_op), _p(o.dim_op), _p(o.val), _p(o.q), _p(o.D), _p(o.S))
-        self.ws = _ws(lib().vb_build_workspace(n, m, ctypes.byref(self.params)), dev)
+        if self.batched:
+            nbytes = lib().vb_build_batch_workspace(n, m, B, ctypes.byref(self.params))
+        else:
+            nbytes = lib().vb_build_workspace(n, m, ctypes.byref(self.params))
+        self.ws = _ws(nbytes, dev)
 
-    def __call__(self, x: torch.Tensor, eps2_den: float | None = None, eps2_op: float | None = None) -> Build:
+    def __call__(self, x: torch.Tensor, eps2_den=None, eps2_op=None) -> Build:
+        """One build of x; eps2_den / eps2_op (a float, or B values) pin both bandwidths."""
         if x.shape != (self.n, self.m) or x.dtype != torch.float32:
             raise ValueError("x must be float32 [n, m] matching the builder")
         pin = eps2_den is not None or eps2_op is not None
         if pin:
             if eps2_den is None or eps2_op is None:
                 raise ValueError("pin both eps2_den and eps2_op")
-            self.out.eps2_den.fill_(eps2_den)
-            self.out.eps2_op.fill_(eps2_op)
+            for dst, v in ((self.out.eps2_den, eps2_den), (self.out.eps2_op, eps2_op)):
+                if isinstance(v, (int, float)):
+                    dst.fill_(float(v))
+                else:
+                    dst.copy_(torch.as_tensor(np.asarray(v, dtype=np.float64)).reshape(dst.shape))
         self.params.pin_eps = 1 if pin else 0
-        _check(lib().vb_build(c_p(_ctx(self.device)), _p(x), self.n, self.m, ctypes.byref(self.params),
-                              ctypes.byref(self.cout), _p(self.ws), self.ws.numel()), "vb_build")
+        h = c_p(_ctx(self.device))
+        if self.batched:
+            rc = lib().vb_build_batch(h, _p(x), self.n, self.m, self._cp_host, _p(self.cloud_ptr), self.B,
+                                      ctypes.byref(self.params), ctypes.byref(self.cout), _p(self.ws), self.ws.numel())
+            _check(rc, "vb_build_batch")
+        else:
+            _check(lib().vb_build(h, _p(x), self.n, self.m, ctypes.byref(self.params), ctypes.byref(self.cout),
+                                  _p(self.ws), self.ws.numel()), "vb_build")
         return self.out
+
+    def autotune(self, x: torch.Tensor) -> dict:
+        """Chooses the kNN launch shape (heap margin, seed window) for this builder by
+        timing the candidates on x (vb_knn_autotune; cached per shape key), and keeps it
+        for every later build.  Synchronises; not for use inside a timed region."""
+        best = KnnParams()
+        ms = c_f32()
+        cp = _p(self.cloud_ptr) if self.batched else c_p(0)
+        _check(lib().vb_knn_autotune(c_p(_ctx(self.device)), _p(x), self.n, self.m, cp, self.B,
+                                     ctypes.byref(self.params.knn),
+                                     _p(self.out.nbr), _p(self.out.nbr_d2), _p(self.ws), self.ws.numel(),
+                                     ctypes.byref(best), ctypes.byref(ms)), "vb_knn_autotune")
+        self.params.knn.margin = best.margin
+        self.params.knn.seed_tiles = best.seed_tiles
+        return {"margin": best.margin, "seed_tiles": best.seed_tiles, "knn_ms": ms.value}
+
+    def graph(self, x: torch.Tensor) -> "torch.cuda.CUDAGraph":
+        """Records one build of x (bandwidths tuned, not pinned) in a CUDA graph;
+        g.replay() then reruns every launch of the build on x's current contents
+        into the same output buffers.  One eager build runs first (it creates the
+        library context and sets the kernels' attributes outside the capture)."""
+        self(x)
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, capture_error_mode="thread_local"):
+            self(x)
+        return g
 
 
 def build(x: torch.Tensor, k: int, d: float, c: float, beta: float = -0.25, margin: int = 16,

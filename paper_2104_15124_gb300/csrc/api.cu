@@ -27,13 +27,45 @@ struct DeviceGuard {
 
 Ctx* C(vb_ctx* c) { return reinterpret_cast<Ctx*>(c); }
 
-size_t build_ws(int64_t n, int32_t m, const vb_build_params* p)
+size_t build_ws(int64_t n, int32_t m, const vb_build_params* p, int B = 1)
 {
     Carve c(nullptr);
     size_t knn = knn_plan(c, n, m, &p->knn, nullptr);
-    size_t s = std::max({knn, graph_plan_bytes(n, p->knn.k), sweep_ws_bytes(n), density_ws_bytes(n),
-                         centre_ws_bytes(n), kernel_csr_ws_bytes(n)});
+    size_t s = std::max({knn, graph_plan_bytes(n, p->knn.k), sweep_ws_bytes(n, B), density_ws_bytes(n, B),
+                         centre_ws_bytes(n, B), kernel_csr_ws_bytes(n, B)});
     return s;
+}
+
+// The chain a0-a13 for one cloud (cl.B == 1) or a batch of clouds.
+vb_status build_run(Ctx* c, const float* x, int64_t n, int32_t m, const vb_build_params* p, const vb_build_out* o,
+                    void* ws, size_t ws_bytes, Clouds cl)
+{
+    const int32_t k = p->knn.k;
+    const int32_t k_bw = p->k_bw > 0 ? p->k_bw : k;
+    if (k_bw > k) return VB_ERR_ARG;
+    if (!ws || ws_bytes < build_ws(n, m, p, cl.B)) return VB_ERR_WORKSPACE;
+    vb_status st = knn_run(c, x, n, m, &p->knn, o->nbr, o->nbr_d2, ws, ws_bytes, cl);
+    if (st) return st;
+    st = graph_run(c, n, k, o->nbr, o->nbr_d2, o->row_ptr, o->col, o->ed2, o->cap, o->nnz, ws, ws_bytes);
+    if (st) return st;
+    st = bandwidth_run(c, n, k, k_bw, o->nbr_d2, o->b);
+    if (st) return st;
+    vb_graph gr{n, o->row_ptr, o->col, o->ed2};
+    if (!p->pin_eps) {
+        st = sweep_run(c, &gr, o->b, 1.0, nullptr, p->xi_lo, p->xi_hi, p->dxi, 1, o->eps2_den, o->chi_den, o->dim_den,
+                       ws, ws_bytes, cl);
+        if (st) return st;
+    }
+    st = density_run(c, &gr, o->b, o->eps2_den, p->op.d, p->op.beta, o->psi, o->P, ws, ws_bytes, cl);
+    if (st) return st;
+    st = centre_run(c, &gr, o->b, o->P, o->xi_c, ws, ws_bytes, cl);
+    if (st) return st;
+    if (!p->pin_eps) {
+        st = sweep_run(c, &gr, o->P, 4.0, o->xi_c, p->xi_lo, p->xi_hi, p->dxi, 2, o->eps2_op, o->chi_op, o->dim_op, ws,
+                       ws_bytes, cl);
+        if (st) return st;
+    }
+    return kernel_csr_run(c, &gr, o->psi, o->P, &p->op, o->eps2_op, o->val, o->q, o->D, o->S, ws, ws_bytes, cl);
 }
 
 }  // namespace
@@ -280,32 +312,30 @@ vb_status vb_build(vb_ctx* ctx, const float* x, int64_t n, int32_t m, const vb_b
     Ctx* c = C(ctx);
     DeviceGuard g(c->device);
     if (!g.ok) return VB_ERR_CUDA;
-    const int32_t k = p->knn.k;
-    const int32_t k_bw = p->k_bw > 0 ? p->k_bw : k;
-    if (k_bw > k) return VB_ERR_ARG;
-    if (!ws || ws_bytes < build_ws(n, m, p)) return VB_ERR_WORKSPACE;
-    vb_status st = knn_run(c, x, n, m, &p->knn, o->nbr, o->nbr_d2, ws, ws_bytes);
-    if (st) return st;
-    st = graph_run(c, n, k, o->nbr, o->nbr_d2, o->row_ptr, o->col, o->ed2, o->cap, o->nnz, ws, ws_bytes);
-    if (st) return st;
-    st = bandwidth_run(c, n, k, k_bw, o->nbr_d2, o->b);
-    if (st) return st;
-    vb_graph gr{n, o->row_ptr, o->col, o->ed2};
-    if (!p->pin_eps) {
-        st = sweep_run(c, &gr, o->b, 1.0, nullptr, p->xi_lo, p->xi_hi, p->dxi, 1, o->eps2_den, o->chi_den, o->dim_den,
-                       ws, ws_bytes);
-        if (st) return st;
-    }
-    st = density_run(c, &gr, o->b, o->eps2_den, p->op.d, p->op.beta, o->psi, o->P, ws, ws_bytes);
-    if (st) return st;
-    st = centre_run(c, &gr, o->b, o->P, o->xi_c, ws, ws_bytes);
-    if (st) return st;
-    if (!p->pin_eps) {
-        st = sweep_run(c, &gr, o->P, 4.0, o->xi_c, p->xi_lo, p->xi_hi, p->dxi, 2, o->eps2_op, o->chi_op, o->dim_op, ws,
-                       ws_bytes);
-        if (st) return st;
-    }
-    return kernel_csr_run(c, &gr, o->psi, o->P, &p->op, o->eps2_op, o->val, o->q, o->D, o->S, ws, ws_bytes);
+    return build_run(c, x, n, m, p, o, ws, ws_bytes, Clouds());
+}
+
+size_t vb_build_batch_workspace(int64_t n, int32_t m, int32_t B, const vb_build_params* p)
+{
+    if (!p || B < 1) return 0;
+    return build_ws(n, m, p, B);
+}
+
+vb_status vb_build_batch(vb_ctx* ctx, const float* x, int64_t n, int32_t m, const int64_t* cloud_ptr_host,
+                         const int64_t* cloud_ptr_dev, int32_t B, const vb_build_params* p, const vb_build_out* o,
+                         void* ws, size_t ws_bytes)
+{
+    if (!ctx || !p || !o || !cloud_ptr_host || !cloud_ptr_dev || B < 1) return VB_ERR_ARG;
+    if (cloud_ptr_host[0] != 0 || cloud_ptr_host[B] != n) return VB_ERR_ARG;
+    for (int32_t b = 0; b < B; ++b)
+        if (cloud_ptr_host[b + 1] - cloud_ptr_host[b] < (int64_t)p->knn.k + 1) return VB_ERR_ARG;
+    Ctx* c = C(ctx);
+    DeviceGuard g(c->device);
+    if (!g.ok) return VB_ERR_CUDA;
+    Clouds cl;
+    cl.ptr = cloud_ptr_dev;
+    cl.B = B;
+    return build_run(c, x, n, m, p, o, ws, ws_bytes, cl);
 }
 
 }  // extern "C"

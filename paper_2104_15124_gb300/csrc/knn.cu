@@ -446,6 +446,85 @@ __device__ bool finalize_row(const TileArgs& a, uint64_t* arr, int t, int size, 
     return cert;
 }
 
+// Error model of the 16-bit distance tiles.  Operands are q' = q - c0 and x' = x - c0
+// (c0 the query tile's box centre) rounded to 16 bits with unit roundoff u, plus an
+// absolute term for FP16 subnormals; the approximate distance |q~|^2 + |x~|^2 - 2 q~.x~
+// is formed with FP32 sums and the tensor cores' FP32 accumulation.  For a pair at
+// exact distance d <= D, |x'| <= |q'| + sqrt(D), so with Z = 2 |q'| + sqrt(D):
+//     |d~ - d| <= E_D(d) = 2 sqrt(d) delta + delta^2 + rho,
+//     delta = u Z + delta_abs,  rho = 2 (K + 4) 2^-24 Z^2.
+// Every use below takes D = the current k-th FP64 distance of the row, so the
+// bound covers exactly the candidates that could still enter the row.
+struct Band {
+    float u, dabs, rho_k;   // unit roundoff, absolute term, 2 (K + 4) 2^-24
+    __device__ double E(double qn, double D, double d) const
+    {
+        const double Z = 1.01 * (2.0 * qn + sqrt(D));
+        const double delta = (double)u * Z * 1.01 + (double)dabs;
+        return 1.01 * (2.0 * sqrt(fmax(d, 0.0)) * delta + delta * delta + (double)rho_k * Z * Z);
+    }
+};
+
+// Rescoring for 16-bit distance tiles, whose error band is wide enough that long
+// runs of candidates are indistinguishable.  The kept keys, ascending by
+// approximate distance df, are rescored in FP64 one by one and inserted into the
+// output row, which stays sorted by (d2, index).  A key whose exact distance could
+// still be below the current k-th distance dk has df <= dk + E_dk(dk), so the scan
+// stops once df - E_dk(df) passes dk.  Certificate: every excluded candidate has
+// df >= B (the largest kept key, or the radius sentinel), so none can lie below
+// dk when dk < (B - E_dk(B)) (1 - 2 gamma); far operands clamped to +-30000 in FP16
+// lie at exact distance >= 4e8, which the certificate also requires dk to stay below.
+template <int MP, int COLS>
+__device__ bool finalize_row_band(const TileArgs& a, uint64_t* arr, int t, int size, int64_t pq, int64_t ncl,
+                                  unsigned& levels, const Band& bd, float qn)
+{
+    for (int e = size - 1; e > 0; --e) {
+        const uint64_t top = arr[t];
+        const uint64_t key = arr[e * COLS + t];
+        arr[e * COLS + t] = top;
+        sift_down<COLS>(arr, t, 0, e, key, levels);
+    }
+    const uint64_t Hkey = arr[(size - 1) * COLS + t];
+    const uint32_t oq = a.perm[pq];
+    const float* qc = a.xs + pq * MP;
+    int32_t* on = a.nbr + (int64_t)oq * a.k;
+    double* od = a.nbr_d2 + (int64_t)oq * a.k;
+    const int k = a.k;
+    int out = 0;
+    double dk = INFINITY;
+    for (int r = 0; r < size; ++r) {
+        const uint64_t key = arr[r * COLS + t];
+        if ((uint32_t)key == 0xffffffffu) break;   // sentinel: nothing further was kept
+        if (out == k) {
+            const double df = (double)__uint_as_float((uint32_t)(key >> 32));
+            if ((df - bd.E(qn, dk, df)) * a.cert_factor > dk) break;
+        }
+        const uint32_t cp = (uint32_t)key;
+        const int32_t oj = (int32_t)a.perm[cp];
+        const double dj = canon_d2(qc, a.xs + (int64_t)cp * MP, a.m);
+        if (out == k && !(dj < dk || (dj == dk && oj < on[k - 1]))) continue;
+        int pos = out < k ? out++ : k - 1;
+        while (pos > 0) {
+            const double dp = od[pos - 1];
+            const int32_t ip = on[pos - 1];
+            if (dp < dj || (dp == dj && ip < oj)) break;
+            od[pos] = dp;
+            on[pos] = ip;
+            --pos;
+        }
+        od[pos] = dj;
+        on[pos] = oj;
+        if (out == k) dk = od[k - 1];
+    }
+    if (out < k) { atomicAdd(&a.rep->knn_rows_short, 1ull); return false; }
+    if (ncl - 1 <= (int64_t)size || Hkey == ~0ull) return true;   // every candidate was kept
+    const double B = (double)__uint_as_float((uint32_t)(Hkey >> 32));
+    const bool cert = isfinite(B) && dk < 4e8 &&
+                      dk < (B - bd.E(qn, dk, B)) * a.cert_factor - (double)a.m * 1.1754943508222875e-38;
+    if (!cert) atomicAdd(&a.rep->knn_rows_uncertified, 1ull);
+    return cert;
+}
+
 // Query tiles are taken from a global counter by a persistent grid of 64-thread
 // CTAs, one query per thread.  Shared memory:
 //   heap  [L][64]  u64  max-heap per query of keys (FP32 distance bits << 32 | sorted position)
@@ -711,22 +790,22 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
     }
 }
 
-// ------------------------------------------------------------------ radius search on the tensor cores (a15)
-// The radius-first search with 16-bit (BF16 or FP16) distance tiles: query supertiles of 128
-// points (two 64-point tiles) against candidate supertiles of 128, with the
-// dot products of each pair formed by tcgen05.mma (BF16 operands, FP32
-// accumulation in tensor memory) and the distances completed as
-// |q|^2 + |c|^2 - 2 q.c.  Both operands are recentred on the query supertile's
-// box centre before rounding to BF16, so their magnitudes stay near the
-// neighbourhood scale.  With Z = 2 max|q'| + sqrt(max R2) (inflated), the
-// distance of any candidate within the radius differs from the exact one by
-// at most E(d) = 2 sqrt(d) delta + delta^2 + rho, delta = 2^-8 Z (BF16 rounding of
-// both operands), rho = (K + 4) 2^-24 Z^2 (FP32 sums); the run ordering and
-// the certificate of finalize_row take E into account, so the output stays
-// exact.  As in the FP32 radius-first search, each query keeps a max-heap of its
-// L nearest candidates that starts full of sentinels at its radius bound.
-// Tiles with a row that is not settled go to the exact FP32 search.
+// ------------------------------------------------------------------ 16-bit distance tiles on the tensor cores (a15)
+// Query tiles of 128 points (two 64-point tiles, one TMEM lane and one thread per
+// query) against 64-point candidate tiles: per candidate tile one chain of
+// tcgen05.mma (kind::f16, M = 128, N = 64, K = m padded to 16; BF16 or FP16 operands,
+// FP32 accumulation in tensor memory) gives the 128 x 64 dot products, read back
+// with tcgen05.ld; distances are |q~|^2 + |x~|^2 - 2 q~.x~ with both operands
+// recentred on the query tile's box centre before rounding.  As in the FP32 search,
+// candidate tiles are sorted by box distance, visited nearest first, and skipped
+// once their box distance passes the largest heap bound of the query tile, which
+// tightens after every visit; each query keeps a max-heap of its k + margin
+// smallest keys, started full of sentinels at its radius bound when a radius is
+// given (learned pruning) and at +inf otherwise.  Rows are finished by
+// finalize_row_band; a query tile with a row that is not certified goes to the
+// exact FP32 search.
 constexpr int T2 = 128;
+constexpr float kHalfClamp = 30000.f;   // FP16 operands are clamped here (finite products)
 
 // 16-bit operand types of the tiles: BF16 (8-bit significand) or FP16 (11-bit).
 template <bool F16> struct Half16;
@@ -735,16 +814,20 @@ template <> struct Half16<false> {
     static __device__ __forceinline__ T from(float x) { return __float2bfloat16_rn(x); }
     static __device__ __forceinline__ float to(T x) { return __bfloat162float(x); }
     static constexpr float unit = 0.00390625f;     // 2^-8
+    static constexpr float dabs = 0.f;
+    static constexpr float clampv = 3.0e38f;
 };
 template <> struct Half16<true> {
     using T = __half;
     static __device__ __forceinline__ T from(float x) { return __float2half_rn(x); }
     static __device__ __forceinline__ float to(T x) { return __half2float(x); }
     static constexpr float unit = 0.00048828125f;  // 2^-11
+    static constexpr float dabs = 1.0e-6f;         // >= sqrt(128) 2^-25: subnormal spacing over 128 coordinates
+    static constexpr float clampv = kHalfClamp;
 };
 
 template <int MP, bool F16>
-__global__ void __launch_bounds__(T2) knn_radius_tc_kernel(TileArgs a)
+__global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
 {
     constexpr int KP = MP < 16 ? 16 : MP;
     using HT = Half16<F16>;
@@ -752,40 +835,36 @@ __global__ void __launch_bounds__(T2) knn_radius_tc_kernel(TileArgs a)
     extern __shared__ __align__(1024) unsigned char smem[];
     const int C = a.cap;
     half_t* sa = (half_t*)smem;                                // [T2][KP] core-matrix layout
-    half_t* sb = sa + T2 * KP;
-    float* sqb = (float*)(sb + T2 * KP);                       // [T2]
-    uint64_t* slist = (uint64_t*)(sqb + T2);                   // [SCAP]
-    uint64_t* buf = slist + SCAP;                              // [C][T2] max-heaps, C = L
+    half_t* sb = sa + T2 * KP;                                 // [TILE][KP]
+    float* sqb = (float*)(sb + TILE * KP);                     // [TILE]
+    uint64_t* slist = (uint64_t*)(sqb + TILE);                 // [SCAP]
+    uint64_t* buf = slist + SCAP;                              // [C][T2] max-heaps
     __shared__ float sqlo[MP], sqhi[MP], scen[MP];
-    __shared__ uint32_t sred[4];
+    __shared__ uint32_t sred[4], soff[4];
     __shared__ int s_tile, s_cnt, s_fail, s_abort;
-    __shared__ int64_t s_cs[2];
-    __shared__ float s_red[4];
+    __shared__ int64_t s_ct[2];
+    __shared__ float s_amax[4];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tmem_base;
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t nt = a.ntiles;
     const int64_t nst = (nt + 1) / 2;
+    const bool rmode = a.r2 != nullptr;
+    Band bd;
+    bd.u = HT::unit;
+    bd.dabs = HT::dabs;
+    bd.rho_k = 2.f * (float)(KP + 4) * 5.9604645e-8f;
     unsigned long long evaluated = 0;
     unsigned levels = 0, staged = 0;
-    if (warp == 0) tc::tmem_alloc(&tmem_base, 128);
+    if (warp == 0) tc::tmem_alloc(&tmem_base, TILE);
     if (t == 0) { tc::mbar_init(&bar, 1); s_abort = 0; }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tb = tmem_base;
     uint32_t phase = 0;
-
-    // union box of supertile st (tiles 2 st and 2 st + 1 when it exists), dimension r
-    auto ubox = [&](int64_t st, int r, float& lo, float& hi) {
-        lo = a.tlo[(2 * st) * MP + r];
-        hi = a.thi[(2 * st) * MP + r];
-        if (2 * st + 1 < nt) {
-            lo = fminf(lo, a.tlo[(2 * st + 1) * MP + r]);
-            hi = fmaxf(hi, a.thi[(2 * st + 1) * MP + r]);
-        }
-    };
+    constexpr uint32_t idesc = tc::idesc_f16(T2, TILE, F16);
 
     for (;;) {
         if (t == 0) {
@@ -803,24 +882,27 @@ __global__ void __launch_bounds__(T2) knn_radius_tc_kernel(TileArgs a)
             qlo = a.cl.ptr[b];
             qhi = a.cl.ptr[b + 1];
         }
-        if (t == 0) {   // candidate supertiles that hold points of this supertile's clouds
-            s_cs[0] = 0;
-            s_cs[1] = nst;
+        if (t == 0) {   // candidate tiles that hold points of this query tile's clouds
+            s_ct[0] = 0;
+            s_ct[1] = nt;
             if (a.cl.B > 1) {
                 const int64_t p0 = qs * T2, pl = min(a.n, p0 + T2) - 1;
-                s_cs[0] = a.cl.ptr[cloud_of(a.cl.ptr, a.cl.B, p0)] / T2;
-                s_cs[1] = (a.cl.ptr[cloud_of(a.cl.ptr, a.cl.B, pl) + 1] + T2 - 1) / T2;
+                s_ct[0] = a.cl.ptr[cloud_of(a.cl.ptr, a.cl.B, p0)] / TILE;
+                s_ct[1] = (a.cl.ptr[cloud_of(a.cl.ptr, a.cl.B, pl) + 1] + TILE - 1) / TILE;
             }
         }
-        for (int r = t; r < MP; r += T2) {
-            float lo, hi;
-            ubox(qs, r, lo, hi);
+        for (int r = t; r < MP; r += T2) {   // union box of tiles 2 qs and 2 qs + 1
+            float lo = a.tlo[(2 * qs) * MP + r], hi = a.thi[(2 * qs) * MP + r];
+            if (2 * qs + 1 < nt) {
+                lo = fminf(lo, a.tlo[(2 * qs + 1) * MP + r]);
+                hi = fmaxf(hi, a.thi[(2 * qs + 1) * MP + r]);
+            }
             sqlo[r] = lo;
             sqhi[r] = hi;
             scen[r] = 0.5f * (lo + hi);
         }
         __syncthreads();
-        // query operand: bf16(q - centre), |q~|^2
+        // query operand: 16-bit (q - centre), |q~|^2
         float qr[MP];
         float sqa = 0.f;
 #pragma unroll
@@ -831,142 +913,195 @@ __global__ void __launch_bounds__(T2) knn_radius_tc_kernel(TileArgs a)
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const int r = 8 * j + e;
-                const float x = r < MP ? qr[r] - scen[r] : 0.f;
-                v[e] = HT::from(valid ? x : 0.f);
+                const float x = r < MP && valid ? fminf(fmaxf(qr[r] - scen[r], -HT::clampv), HT::clampv) : 0.f;
+                v[e] = HT::from(x);
                 const float xb = HT::to(v[e]);
                 sqa = fmaf(xb, xb, sqa);
             }
             *(uint4*)((char*)sa + tc::operand_offset(t, 8 * j, KP)) = *(const uint4*)v;
         }
-        const float R2 = valid ? __fmul_ru(a.r2[p], a.r2_scale) : 0.f;
-        const uint32_t r2bits = __float_as_uint(R2);
-        {   // tile maxima of R2 and |q'|
-            uint32_t wr = __reduce_max_sync(0xffffffffu, valid ? r2bits : 0u);
-            uint32_t wa = __reduce_max_sync(0xffffffffu, valid ? __float_as_uint(sqrtf(sqa)) : 0u);
-            if (lane == 0) { sred[warp] = wr; s_red[warp] = __uint_as_float(wa); }
+        const float qn = sqrtf(sqa);
+        const float R2 = rmode && valid ? __fmul_ru(a.r2[p], a.r2_scale) : INFINITY;
+        const uint64_t sentinel = rmode ? (((uint64_t)__float_as_uint(R2) << 32) | 0xffffffffu) : ~0ull;
+        for (int sl = 0; sl < C; ++sl) buf[sl * T2 + t] = sentinel;
+        uint64_t heapmax = sentinel;
+        {
+            const uint32_t wr = __reduce_max_sync(0xffffffffu, valid ? (uint32_t)(sentinel >> 32) : 0u);
+            const uint32_t wa = __reduce_max_sync(0xffffffffu, valid ? __float_as_uint(qn) : 0u);
+            if (lane == 0) { sred[warp] = wr; s_amax[warp] = __uint_as_float(wa); }
         }
         tc::fence_async_smem();
         __syncthreads();
-        const uint32_t thr_blk = max(max(sred[0], sred[1]), max(sred[2], sred[3]));
-        const float amax = fmaxf(fmaxf(s_red[0], s_red[1]), fmaxf(s_red[2], s_red[3]));
-        const float Z = 1.02f * (2.f * amax + sqrtf(__uint_as_float(thr_blk)));
-        const float delta = 1.01f * HT::unit * Z;
-        const float rho = 1.01f * (float)(KP + 4) * 5.9604645e-8f * Z * Z;
-        const uint64_t sentinel = ((uint64_t)r2bits << 32) | 0xffffffffu;
-        for (int sl = 0; sl < C; ++sl) buf[sl * T2 + t] = sentinel;
-        uint64_t heapmax = sentinel;
+        const int64_t ct_lo = s_ct[0], ct_hi = s_ct[1];
+        uint32_t thr_blk = max(max(sred[0], sred[1]), max(sred[2], sred[3]));
+        const float amax = fmaxf(fmaxf(s_amax[0], s_amax[1]), fmaxf(s_amax[2], s_amax[3]));
+        // FP16 range: a query tile whose own extent is not small against the clamp goes to FP32
+        const bool far = F16 && amax > 0.25f * kHalfClamp;
 
-        const int64_t cs_lo = s_cs[0], cs_hi = s_cs[1];
-        for (int64_t c0 = cs_lo; c0 < cs_hi && !s_abort;) {
+        // Visit candidate tile ct for every query that may still gain from it: stage its 16-bit
+        // operand, one MMA chain into tensor memory, then each query folds the 64 distances
+        // into its heap; finally the tile bound tightens.  Returns false once a bounded wait ran out.
+        auto visit = [&](int64_t ct) -> bool {
+            bool need = valid;
+            if (need) {
+                float acc = 0.f;
+#pragma unroll
+                for (int r = 0; r < MP; ++r) {
+                    const float g = fmaxf(fmaxf(a.tlo[ct * MP + r] - qr[r], qr[r] - a.thi[ct * MP + r]), 0.f);
+                    acc = fmaf(g, g, acc);
+                }
+                need = __float_as_uint(__fmul_rd(acc, a.lb_factor)) <= (uint32_t)(heapmax >> 32);
+            }
+            if (!__syncthreads_or(need)) return true;
+            staged += t == 0;
+            if (t < TILE) {   // candidate operand: row t of tile ct
+                const int64_t cp = ct * TILE + t;
+                float sq = 0.f;
+#pragma unroll
+                for (int j = 0; j < KP / 8; ++j) {
+                    __align__(16) half_t v[8];
+#pragma unroll
+                    for (int e2 = 0; e2 < 8; ++e2) {
+                        const int r = 8 * j + e2;
+                        const float x =
+                            r < MP ? fminf(fmaxf(a.xs[cp * MP + r] - scen[r], -HT::clampv), HT::clampv) : 0.f;
+                        v[e2] = HT::from(x);
+                        const float xb = HT::to(v[e2]);
+                        sq = fmaf(xb, xb, sq);
+                    }
+                    *(uint4*)((char*)sb + tc::operand_offset(t, 8 * j, KP)) = *(const uint4*)v;
+                }
+                sqb[t] = sq;
+            }
+            tc::fence_async_smem();
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            if (t == 0) {
+                constexpr uint32_t sbo = (uint32_t)(KP / 8) * 128;
+#pragma unroll
+                for (int s = 0; s < KP / 16; ++s) {
+                    const uint64_t ad = tc::smem_desc(tc::smem_addr(sa) + s * 256, 128, sbo);
+                    const uint64_t bd2 = tc::smem_desc(tc::smem_addr(sb) + s * 256, 128, sbo);
+                    tc::mma_bf16(tb, ad, bd2, idesc, s > 0 ? 1u : 0u);
+                }
+                tc::mma_commit(&bar);
+            }
+            const bool done = tc::mbar_wait(&bar, phase);
+            phase ^= 1u;
+            tc::fence_after_sync();
+            if (__syncthreads_or(!done)) {   // a bounded wait ran out: record it and stop
+                if (t == 0) { report_error(a.rep, VB_ERR_TIMEOUT); s_abort = 1; }
+                return false;
+            }
+            if (need) evaluated += TILE;
+            const uint32_t hb = (uint32_t)(heapmax >> 32);
+            float hmf = hb == 0xffffffffu ? INFINITY : __uint_as_float(hb);
+#pragma unroll 1
+            for (int ch = 0; ch < TILE / 32; ++ch) {
+                float v[32];
+                tc::tmem_ld32(tb + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32), v);
+                if (!need) continue;
+                // distances of the 32 columns (registers only), and the mask of those under the bound
+                uint32_t msk = 0;
+                const float4* sq4 = (const float4*)(sqb + ch * 32);
+#pragma unroll
+                for (int i4 = 0; i4 < 8; ++i4) {
+                    const float4 q4 = sq4[i4];
+                    v[4 * i4 + 0] = fmaf(-2.f, v[4 * i4 + 0], sqa + q4.x);
+                    v[4 * i4 + 1] = fmaf(-2.f, v[4 * i4 + 1], sqa + q4.y);
+                    v[4 * i4 + 2] = fmaf(-2.f, v[4 * i4 + 2], sqa + q4.z);
+                    v[4 * i4 + 3] = fmaf(-2.f, v[4 * i4 + 3], sqa + q4.w);
+                }
+#pragma unroll
+                for (int i = 0; i < 32; ++i) msk |= (v[i] <= hmf ? 1u : 0u) << i;
+                while (msk) {   // the full key test and the heap update
+                    const int i = __ffs(msk) - 1;
+                    msk &= msk - 1u;
+                    float d = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) d = j == i ? v[j] : d;
+                    const int64_t cp = ct * TILE + ch * 32 + i;
+                    const uint64_t key = ((uint64_t)__float_as_uint(fmaxf(d, 0.f)) << 32) | (uint32_t)cp;
+                    if (key < heapmax && cp != p && cp >= qlo && cp < qhi) {
+                        sift_down<T2>(buf, t, 0, C, key, levels);
+                        heapmax = buf[t];
+                    }
+                }
+                const uint32_t h2 = (uint32_t)(heapmax >> 32);
+                hmf = h2 == 0xffffffffu ? INFINITY : __uint_as_float(h2);
+            }
+            tc::fence_before_sync();
+            // tile threshold = largest heap bound among the tile's valid queries
+            const uint32_t wmax = __reduce_max_sync(0xffffffffu, valid ? (uint32_t)(heapmax >> 32) : 0u);
+            if (lane == 0) sred[warp] = wmax;
+            __syncthreads();
+            thr_blk = max(max(sred[0], sred[1]), max(sred[2], sred[3]));
+            return true;
+        };
+
+        // seed tiles (without a radius bound): the query tile's own two tiles and their
+        // neighbours in Morton order, so the heaps fill with near points before any pruning
+        const int64_t sw = (a.nseed - 1) / 2;   // tiles on each side
+        const int64_t s_lo = rmode || far ? 0 : max(ct_lo, 2 * qs - sw);
+        const int64_t s_hi = rmode || far ? 0 : min(ct_hi, 2 * qs + 2 + sw);
+        for (int64_t ct = s_lo; ct < s_hi && !s_abort; ++ct)
+            if (!visit(ct)) break;
+        // every other tile whose box lower bound does not exceed the tile bound, nearest first
+        for (int64_t c0 = ct_lo; c0 < ct_hi && !far && !s_abort;) {
             if (t == 0) s_cnt = 0;
             __syncthreads();
-            for (; c0 < cs_hi; c0 += T2) {
-                const int64_t cs = c0 + t;
-                bool keep = cs < cs_hi;
+            for (; c0 < ct_hi; c0 += T2) {
+                const int64_t ct = c0 + t;
+                bool keep = ct < ct_hi && (ct < s_lo || ct >= s_hi);
+                float lb = 0.f;
                 if (keep) {
                     float acc = 0.f;
                     for (int r = 0; r < MP; ++r) {
-                        float lo, hi;
-                        ubox(cs, r, lo, hi);
-                        float g = fmaxf(fmaxf(lo - sqhi[r], sqlo[r] - hi), 0.f);
+                        const float g = fmaxf(fmaxf(a.tlo[ct * MP + r] - sqhi[r], sqlo[r] - a.thi[ct * MP + r]), 0.f);
                         acc = fmaf(g, g, acc);
                     }
-                    keep = __float_as_uint(__fmul_rd(acc, a.lb_factor)) <= thr_blk;
+                    lb = __fmul_rd(acc, a.lb_factor);
+                    keep = __float_as_uint(lb) <= thr_blk;
                 }
-                unsigned bal = __ballot_sync(0xffffffffu, keep);
-                if (lane == 0 && bal) sred[warp] = atomicAdd(&s_cnt, __popc(bal));
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                if (lane == 0 && bal) soff[warp] = atomicAdd(&s_cnt, __popc(bal));
                 __syncwarp();
-                if (keep) slist[sred[warp] + __popc(bal & ((1u << lane) - 1u))] = (uint64_t)cs;
+                if (keep)
+                    slist[soff[warp] + __popc(bal & ((1u << lane) - 1u))] =
+                        ((uint64_t)__float_as_uint(lb) << 32) | (uint32_t)ct;
                 __syncthreads();
                 if (s_cnt > SCAP - T2) { c0 += T2; break; }
             }
             const int cnt = s_cnt;
+            int P = 1;
+            while (P < cnt) P <<= 1;
+            for (int i = cnt + t; i < P; i += T2) slist[i] = ~0ull;
+            __syncthreads();
+            for (int size = 2; size <= P; size <<= 1) {
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    for (int i = t; i < P / 2; i += T2) {
+                        const int lo = 2 * i - (i & (stride - 1));
+                        const int hi = lo + stride;
+                        const bool up = (lo & size) == 0;
+                        const uint64_t x = slist[lo], y = slist[hi];
+                        if ((x > y) == up) { slist[lo] = y; slist[hi] = x; }
+                    }
+                    __syncthreads();
+                }
+            }
             for (int si = 0; si < cnt; ++si) {
-                const int64_t cs = (int64_t)slist[si];
-                bool need = valid;
-                if (need) {
-                    float acc = 0.f;
-#pragma unroll
-                    for (int r = 0; r < MP; ++r) {
-                        float lo, hi;
-                        ubox(cs, r, lo, hi);
-                        float g = fmaxf(fmaxf(lo - qr[r], qr[r] - hi), 0.f);
-                        acc = fmaf(g, g, acc);
-                    }
-                    need = __float_as_uint(__fmul_rd(acc, a.lb_factor)) <= (uint32_t)(heapmax >> 32);
-                }
-                if (!__syncthreads_or(need)) continue;
-                staged += t == 0;
-                {   // candidate operand: row t of the supertile
-                    const int64_t cp = cs * T2 + t;
-                    float sq = 0.f;
-#pragma unroll
-                    for (int j = 0; j < KP / 8; ++j) {
-                        __align__(16) half_t v[8];
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            const int r = 8 * j + e;
-                            const float x = r < MP ? a.xs[cp * MP + r] - scen[r] : 0.f;
-                            v[e] = HT::from(x);
-                            const float xb = HT::to(v[e]);
-                            sq = fmaf(xb, xb, sq);
-                        }
-                        *(uint4*)((char*)sb + tc::operand_offset(t, 8 * j, KP)) = *(const uint4*)v;
-                    }
-                    sqb[t] = sq;
-                }
-                tc::fence_async_smem();
-                tc::fence_before_sync();
-                __syncthreads();
-                tc::fence_after_sync();
-                if (t == 0) {
-                    constexpr uint32_t sbo = (uint32_t)(KP / 8) * 128;
-#pragma unroll
-                    for (int s = 0; s < KP / 16; ++s) {
-                        const uint64_t ad = tc::smem_desc(tc::smem_addr(sa) + s * 256, 128, sbo);
-                        const uint64_t bd = tc::smem_desc(tc::smem_addr(sb) + s * 256, 128, sbo);
-                        tc::mma_bf16(tb, ad, bd, tc::idesc_f16(128, 128, F16), s > 0 ? 1u : 0u);
-                    }
-                    tc::mma_commit(&bar);
-                }
-                const bool done = tc::mbar_wait(&bar, phase);
-                phase ^= 1u;
-                tc::fence_after_sync();
-                if (__syncthreads_or(!done)) {   // a bounded wait ran out: record it and stop
-                    if (t == 0) { report_error(a.rep, VB_ERR_TIMEOUT); s_abort = 1; }
-                    break;
-                }
-                if (need) evaluated += T2;
-#pragma unroll 1
-                for (int ch = 0; ch < T2 / 32; ++ch) {
-                    float v[32];
-                    tc::tmem_ld32(tb + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32), v);
-                    if (!need) continue;
-#pragma unroll 4
-                    for (int i = 0; i < 32; ++i) {
-                        const int c = ch * 32 + i;
-                        const int64_t cp = cs * T2 + c;
-                        const float d = fmaxf(sqa + sqb[c] - 2.f * v[i], 0.f);
-                        const uint64_t key = ((uint64_t)__float_as_uint(d) << 32) | (uint32_t)cp;
-                        if (key < heapmax && cp != p && cp >= qlo && cp < qhi) {
-                            sift_down<T2>(buf, t, 0, C, key, levels);
-                            heapmax = buf[t];
-                        }
-                    }
-                }
-                tc::fence_before_sync();
-                __syncthreads();
+                const uint64_t e = slist[si];
+                if ((uint32_t)(e >> 32) > thr_blk) break;   // sorted: the rest lie farther
+                if (!visit((int64_t)(uint32_t)e)) break;
             }
             __syncthreads();
         }
         if (s_abort) break;
 
-        bool ok = true;
-        if (valid) {
-            const float e_lin = 2.f * delta, e_const = delta * delta + rho;
-            ok = finalize_row<MP, T2>(a, buf, t, C, true, p, qhi - qlo, 1, 0.f, levels, e_lin, e_const);
-        }
-        if (!ok) s_fail = 1;
+        bool ok = !far;
+        if (valid && ok) ok = finalize_row_band<MP, T2>(a, buf, t, C, p, qhi - qlo, levels, bd, qn);
+        if (valid && !ok) s_fail = 1;
         __syncthreads();
         if (t == 0 && s_fail) {
             for (int h = 0; h < 2; ++h) {
@@ -993,7 +1128,7 @@ __global__ void __launch_bounds__(T2) knn_radius_tc_kernel(TileArgs a)
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tb, 128);
+    if (warp == 0) tc::tmem_dealloc(tb, TILE);
 }
 
 // R2[pos] = (inflate * radius[perm[pos]])^2 for the sorted points (caller-provided radii).
@@ -1107,23 +1242,23 @@ static size_t tile_smem(int L)
 }
 
 template <int MP>
-static size_t radius_tc_smem(int C)
+static size_t tc_smem(int C)
 {
     constexpr int KP = MP < 16 ? 16 : MP;
-    return (size_t)2 * T2 * KP * 2 + T2 * 4 + SCAP * 8 + (size_t)C * T2 * 8;
+    return (size_t)T2 * KP * 2 + TILE * KP * 2 + TILE * 4 + SCAP * 8 + (size_t)C * T2 * 8;
 }
 
 template <int MP, bool F16>
-static vb_status launch_radius_tc(TileArgs a, cudaStream_t s)
+static vb_status launch_tc(TileArgs a, cudaStream_t s)
 {
-    size_t sm = radius_tc_smem<MP>(a.cap);
+    const size_t sm = tc_smem<MP>(a.cap);
     if (sm > 220 * 1024) return VB_ERR_UNSUPPORTED;   // k + margin too large for 128 heaps with these operands
     static bool attr_set[16] = {};
     static int sms[16] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (!attr_set[dev & 15]) {
-        if (cudaFuncSetAttribute(knn_radius_tc_kernel<MP, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(knn_tc_kernel<MP, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(220 * 1024)) != cudaSuccess)
             return VB_ERR_CUDA;
         if (cudaDeviceGetAttribute(&sms[dev & 15], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -1131,13 +1266,13 @@ static vb_status launch_radius_tc(TileArgs a, cudaStream_t s)
         attr_set[dev & 15] = true;
     }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, knn_radius_tc_kernel<MP, F16>, T2, sm) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, knn_tc_kernel<MP, F16>, T2, sm) != cudaSuccess ||
         per_sm < 1)
         return VB_ERR_CUDA;
-    per_sm = std::min(per_sm, 4);   // 128 TMEM columns per CTA, 512 per SM
+    per_sm = std::min(per_sm, 8);   // 64 TMEM columns per CTA, 512 per SM
     const int64_t nst = (a.ntiles + 1) / 2;
     const int64_t grid = std::min<int64_t>(nst, (int64_t)per_sm * sms[dev & 15]);
-    knn_radius_tc_kernel<MP, F16><<<(unsigned)grid, T2, sm, s>>>(a);
+    knn_tc_kernel<MP, F16><<<(unsigned)grid, T2, sm, s>>>(a);
     return last_launch();
 }
 
@@ -1166,7 +1301,7 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
     if (!x || !nbr || !nbr_d2 || !p || n < 2 || n >= INT32_MAX || m < 1 || m > 128) return VB_ERR_ARG;
     if (p->k < 1 || (int64_t)p->k > n - 1 || p->margin < 0 || p->k + p->margin > 256) return VB_ERR_ARG;
     if (p->precision < VB_PREC_FP32 || p->precision > VB_PREC_FP16) return VB_ERR_UNSUPPORTED;
-    if (p->precision != VB_PREC_FP32 && p->prune != VB_PRUNE_LEARNED) return VB_ERR_UNSUPPORTED;
+    if (p->precision != VB_PREC_FP32 && p->prune == VB_PRUNE_NONE) return VB_ERR_UNSUPPORTED;
     if (p->prune == VB_PRUNE_LEARNED && !p->radius && !p->mlp) return VB_ERR_ARG;
     if (p->prune < VB_PRUNE_NONE || p->prune > VB_PRUNE_LEARNED) return VB_ERR_ARG;
     KnnWs w;
@@ -1214,7 +1349,8 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
     TileArgs a = {};
     a.xs = w.xs; a.tlo = w.tlo; a.thi = w.thi; a.perm = perm; a.n = n; a.ntiles = ntiles;
     a.m = m; a.k = p->k; a.L = p->k + p->margin; a.prune = p->prune != VB_PRUNE_NONE;
-    a.nseed = 1 + 2 * (int)((a.L + TILE) / TILE);   // enough neighbouring tiles to fill every heap
+    // enough neighbouring tiles to fill every heap, unless the caller (the autotuner) chose
+    a.nseed = p->seed_tiles > 0 ? 1 + 2 * p->seed_tiles : 1 + 2 * (int)((a.L + TILE) / TILE);
     a.lb_factor = 1.0f - 4.0f * (float)(m + 2) * 5.9604645e-8f;
     a.band = 1.0f + 4.0f * (float)(m + 2) * 5.9604645e-8f;
     a.cert_factor = 1.0 - 2.0 * (double)(m + 2) * 5.9604644775390625e-8;
@@ -1222,21 +1358,25 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
     a.work = w.fb_count + 1;
     a.cl = cl;
     const bool radius_first = p->prune == VB_PRUNE_LEARNED;
+    const bool tensor = p->precision == VB_PREC_BF16 || p->precision == VB_PREC_FP16;
     int launches = 0;
-    if (radius_first) {
-        const float inflate = p->radius_inflate > 0.f ? p->radius_inflate : 1.5f;
-        if (p->mlp) {
-            st = mlp_radius_r2(s, p->mlp, w.xs, n, m, mp, p->radius_log_shift, inflate, w.r2);
-        } else {
-            radius_gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p->radius, perm, n, inflate, w.r2);
-            st = last_launch();
+    if (radius_first || tensor) {
+        if (radius_first) {
+            const float inflate = p->radius_inflate > 0.f ? p->radius_inflate : 1.5f;
+            if (p->mlp) {
+                st = mlp_radius_r2(s, p->mlp, w.xs, n, m, mp, p->radius_log_shift, inflate, w.r2, p->cloud_log_shift,
+                                   cl);
+            } else {
+                radius_gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p->radius, perm, n, inflate, w.r2);
+                st = last_launch();
+            }
+            if (st != VB_OK) return st;
+            launches += 1;
         }
-        if (st != VB_OK) return st;
         if (cudaMemsetAsync(w.fail_flag, 0, sizeof(int) * 2 * ntiles, s) != cudaSuccess) return VB_ERR_CUDA;
-        // counters: [1] pass-1 work, [2] heap-search work, [3] pass-1 failures, [4] pass-2 work, [5] pass-2 failures
-        a.r2 = w.r2;
+        // counters: [1] first-pass work, [2] exact-search work, [3] first-pass failures
+        a.r2 = radius_first ? w.r2 : nullptr;
         mark(ctx, VB_STAGE_KNN_TILE, 0);
-        const bool tensor = p->precision == VB_PREC_BF16 || p->precision == VB_PREC_FP16;
         const bool f16 = p->precision == VB_PREC_FP16;
         a.r2_scale = 1.f;
         a.work = w.fb_count + 1;
@@ -1246,12 +1386,12 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
         if (tensor) {
             a.cap = a.L;
             switch (mp) {
-                case 4: st = f16 ? launch_radius_tc<4, true>(a, s) : launch_radius_tc<4, false>(a, s); break;
-                case 8: st = f16 ? launch_radius_tc<8, true>(a, s) : launch_radius_tc<8, false>(a, s); break;
-                case 16: st = f16 ? launch_radius_tc<16, true>(a, s) : launch_radius_tc<16, false>(a, s); break;
-                case 32: st = f16 ? launch_radius_tc<32, true>(a, s) : launch_radius_tc<32, false>(a, s); break;
-                case 64: st = f16 ? launch_radius_tc<64, true>(a, s) : launch_radius_tc<64, false>(a, s); break;
-                default: st = f16 ? launch_radius_tc<128, true>(a, s) : launch_radius_tc<128, false>(a, s); break;
+                case 4: st = f16 ? launch_tc<4, true>(a, s) : launch_tc<4, false>(a, s); break;
+                case 8: st = f16 ? launch_tc<8, true>(a, s) : launch_tc<8, false>(a, s); break;
+                case 16: st = f16 ? launch_tc<16, true>(a, s) : launch_tc<16, false>(a, s); break;
+                case 32: st = f16 ? launch_tc<32, true>(a, s) : launch_tc<32, false>(a, s); break;
+                case 64: st = f16 ? launch_tc<64, true>(a, s) : launch_tc<64, false>(a, s); break;
+                default: st = f16 ? launch_tc<128, true>(a, s) : launch_tc<128, false>(a, s); break;
             }
         } else {
             switch (mp) {
@@ -1264,12 +1404,12 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
             }
         }
         if (st != VB_OK) return st;
-        // tiles the radius could not settle: the exact search (seeded, no radius) on that list only
+        // tiles the first pass could not settle: the exact FP32 search (seeded, no radius) on that list only
         a.r2 = nullptr;
         a.work = w.fb_count + 2;
         a.tile_list = w.fail_list;
         a.tile_count = w.fb_count + 3;
-        launches += 3;
+        launches += 2;
     } else {
         mark(ctx, VB_STAGE_KNN_TILE, 0);
     }

@@ -103,7 +103,8 @@ __device__ __forceinline__ void standardise(const MlpK& k, const float* x, int l
 
 // ------------------------------------------------------------------ inference
 __global__ void __launch_bounds__(128) mlp_predict_kernel(MlpK k, const float* __restrict__ x, int ld, int64_t n,
-                                                          float* y, int mode, float shift, float inflate)
+                                                          float* y, int mode, float shift, float inflate,
+                                                          const float* __restrict__ cloud_shift, Clouds cl)
 {
     extern __shared__ float W[];
     load_weights(k, W);
@@ -115,7 +116,8 @@ __global__ void __launch_bounds__(128) mlp_predict_kernel(MlpK k, const float* _
         if (mode == 0) {
             y[i] = logr;
         } else {   // squared radius bound for the radius-first kNN search
-            const float r = expf(logr + shift) * inflate;
+            const float sh = cloud_shift ? shift + cloud_shift[cloud_of(cl.ptr, cl.B, i)] : shift;
+            const float r = expf(logr + sh) * inflate;
             y[i] = __fmul_ru(r, r);
         }
     }
@@ -331,10 +333,11 @@ static vb_status grad_run(Ctx* ctx, const vb_mlp* m, const float* x, int ld, con
 }
 
 vb_status mlp_radius_r2(cudaStream_t s, const vb_mlp* mlp, const float* xs, int64_t n, int m, int mp, float shift,
-                        float inflate, float* r2)
+                        float inflate, float* r2, const float* cloud_shift, Clouds cl)
 {
     if (!mlp || mlp->in_dim < 1 || mlp->in_dim > VB_MLP_MAX_IN || mlp->in_dim > m || !mlp->weights) return VB_ERR_ARG;
-    mlp_predict_kernel<<<152 * 4, 128, pred_smem(mlp->in_dim), s>>>(mk(mlp), xs, mp, n, r2, 1, shift, inflate);
+    mlp_predict_kernel<<<152 * 4, 128, pred_smem(mlp->in_dim), s>>>(mk(mlp), xs, mp, n, r2, 1, shift, inflate,
+                                                                     cloud_shift, cl);
     return last_launch();
 }
 
@@ -409,7 +412,8 @@ vb_status vb_mlp_predict(vb_ctx* ctx, const vb_mlp* m, const float* x, int32_t l
     if (!ctx || !m || !x || !y || n < 1 || ld < m->in_dim || m->in_dim < 1 || m->in_dim > VB_MLP_MAX_IN)
         return VB_ERR_ARG;
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
-    mlp_predict_kernel<<<152 * 4, 128, pred_smem(m->in_dim), c->stream>>>(mk(m), x, ld, n, y, 0, 0.f, 1.f);
+    mlp_predict_kernel<<<152 * 4, 128, pred_smem(m->in_dim), c->stream>>>(mk(m), x, ld, n, y, 0, 0.f, 1.f,
+                                                                               nullptr, Clouds());
     c->launches += 1;
     return last_launch();
 }

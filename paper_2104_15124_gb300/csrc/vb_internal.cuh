@@ -154,9 +154,10 @@ vb_status spmv_lap_launch(cudaStream_t s, const vb_graph* g, const float* val, c
 vb_status spmv_run(Ctx* ctx, const vb_graph* g, const float* val, const double* S, int mode, float alpha,
                    const float* x, float beta, float* y, void* ws, size_t ws_bytes);
 
-// learned radius (mlp.cu): R2[pos] = (inflate exp(net(xs[pos]) + shift))^2 for sorted points
+// learned radius (mlp.cu): R2[pos] = (inflate exp(net(xs[pos]) + shift + cloud_shift[cloud]))^2
+// for sorted points (sorted positions keep the clouds' ranges)
 vb_status mlp_radius_r2(cudaStream_t s, const vb_mlp* mlp, const float* xs, int64_t n, int m, int mp, float shift,
-                        float inflate, float* r2);
+                        float inflate, float* r2, const float* cloud_shift = nullptr, Clouds cl = Clouds());
 
 // eigen-solve (solve.cu)
 size_t solve_ws_bytes(int64_t n, int64_t cap, const vb_solve_params* p);
