@@ -27,13 +27,22 @@ struct DeviceGuard {
 
 Ctx* C(vb_ctx* c) { return reinterpret_cast<Ctx*>(c); }
 
+// A batched build keeps the cloud of every point at the front of the workspace.
+size_t cloud_id_bytes(int64_t n, int B) { return B > 1 ? (((size_t)n * sizeof(int32_t) + 255) & ~(size_t)255) : 0; }
+
 size_t build_ws(int64_t n, int32_t m, const vb_build_params* p, int B = 1)
 {
     Carve c(nullptr);
     size_t knn = knn_plan(c, n, m, &p->knn, nullptr);
     size_t s = std::max({knn, graph_plan_bytes(n, p->knn.k), sweep_ws_bytes(n, B), density_ws_bytes(n, B),
                          centre_ws_bytes(n, B), kernel_csr_ws_bytes(n, B)});
-    return s;
+    return s + cloud_id_bytes(n, B);
+}
+
+__global__ void cloud_id_kernel(const int64_t* __restrict__ ptr, int B, int64_t n, int32_t* id)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) id[i] = cloud_of(ptr, B, i);
 }
 
 // The chain a0-a13 for one cloud (cl.B == 1) or a batch of clouds.
@@ -44,6 +53,15 @@ vb_status build_run(Ctx* c, const float* x, int64_t n, int32_t m, const vb_build
     const int32_t k_bw = p->k_bw > 0 ? p->k_bw : k;
     if (k_bw > k) return VB_ERR_ARG;
     if (!ws || ws_bytes < build_ws(n, m, p, cl.B)) return VB_ERR_WORKSPACE;
+    if (cl.B > 1) {
+        int32_t* id = (int32_t*)ws;
+        const size_t off = cloud_id_bytes(n, cl.B);
+        cloud_id_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(cl.ptr, cl.B, n, id);
+        c->launches += 1;
+        cl.id = id;
+        ws = (char*)ws + off;
+        ws_bytes -= off;
+    }
     vb_status st = knn_run(c, x, n, m, &p->knn, o->nbr, o->nbr_d2, ws, ws_bytes, cl);
     if (st) return st;
     st = graph_run(c, n, k, o->nbr, o->nbr_d2, o->row_ptr, o->col, o->ed2, o->cap, o->nnz, ws, ws_bytes);

@@ -3,13 +3,10 @@
 // a6: E = {(i, i)} U {(i, j): j in N_k(i) or i in N_k(j)} as CSR with rows
 //     sorted by column.  Algorithm 1 keeps the diagonal (its inner loop
 //     starts at j = i) and sets K^ij and K^ji together, so every kNN pair
-//     enters in both directions.  Construction: in-degree count (int
-//     atomics) -> exclusive scan -> scatter of own and transposed entries
-//     into raw rows -> per-row sort by column and de-duplication (one warp
-//     per row in shared memory; one block per row for rows longer than the
-//     warp limit) -> scan of the unique counts -> compaction.  The FP32
-//     squared distance of every entry is the FP32 rounding of the canonical
-//     FP64 value, identical for (i, j) and (j, i).
+//     enters in both directions.  The FP32 squared distance of every entry is
+//     the FP32 rounding of the canonical FP64 value, identical for (i, j) and
+//     (j, i).  Construction below (sorted own lists, filtered reverse entries,
+//     merge by rank).
 // a8: b_i^2 = sum_{r=1}^{k_bw} d2(i, I(i, r)) in rank order, FP64 (Eq.
 //     bandwidth parameter).
 #include "vb_internal.cuh"
@@ -18,9 +15,7 @@
 
 namespace vb {
 
-constexpr int ROW_CAP = 512;        // warp path: raw entries per row held in shared memory
-constexpr int BIG_CAP = 8192;       // block path: raw entries per row
-constexpr int SORT_WARPS = 4;
+constexpr int BIG_CAP = 8192;       // block path: reverse entries per row
 constexpr int SCAN_T = 1024;
 constexpr int SCAN_ITEMS = 8;       // counts per thread per scan block
 
@@ -125,14 +120,26 @@ vb_status scan_counts(cudaStream_t s, const int32_t* counts, int64_t n, int64_t*
 }
 
 // ------------------------------------------------------------------ a6
+// Row j of E is the disjoint union of {j}, its own kNN list N(j), and the reverse
+// entries R(j) = {i : j in N(i), i not in N(j)}.  Construction: every kNN list is
+// sorted by column (one warp per row); a reverse candidate (i -> j) is kept when a
+// binary search does not find i in N(j), so mutual pairs enter once; the counts
+// 1 + k + |R(j)| give row_ptr directly (one scan); the kept reverse entries are
+// scattered into a side buffer; finally one warp per row sorts R(j) and places
+// every entry by its rank (own index + reverse entries below it + the diagonal),
+// which merges the three sorted sets with no duplicates left to remove.
+constexpr int RCAP = 256;           // warp path: reverse entries per row held in shared memory
+constexpr int OWN_CAP = 256;        // longest kNN list (k + margin <= 256)
+
 struct GraphWs {
-    int32_t* indeg;    // n, then reused as transposed fill counters
-    int32_t* fill;     // n
-    int32_t* cnt;      // n raw counts, then unique counts
-    int64_t* raw_ptr;  // n + 1
-    int32_t* raw_col;  // n (2k + 1)
-    float* raw_d2;     // n (2k + 1)
-    int32_t* big;      // n (rows for the block path)
+    int32_t* own_col;  // n k: kNN lists sorted by column
+    float* own_d2;     // n k
+    int32_t* rcnt;     // n reverse entries per row
+    int32_t* fill;     // n scatter cursors
+    int32_t* cnt;      // n row lengths
+    int32_t* rev_col;  // n k reverse entries, row j at row_ptr[j] - j (1 + k)
+    float* rev_d2;     // n k
+    int32_t* big;      // n rows for the block path
     int32_t* nbig;     // 1
     void* scan;        // scan_ws_bytes(n)
 };
@@ -140,12 +147,13 @@ struct GraphWs {
 static size_t graph_plan(Carve& c, int64_t n, int32_t k, GraphWs* w)
 {
     GraphWs t;
-    t.indeg = c.take<int32_t>(n);
+    t.own_col = c.take<int32_t>(n * (int64_t)k);
+    t.own_d2 = c.take<float>(n * (int64_t)k);
+    t.rcnt = c.take<int32_t>(n);
     t.fill = c.take<int32_t>(n);
     t.cnt = c.take<int32_t>(n);
-    t.raw_ptr = c.take<int64_t>(n + 1);
-    t.raw_col = c.take<int32_t>(n * (2 * (int64_t)k + 1));
-    t.raw_d2 = c.take<float>(n * (2 * (int64_t)k + 1));
+    t.rev_col = c.take<int32_t>(n * (int64_t)k);
+    t.rev_d2 = c.take<float>(n * (int64_t)k);
     t.big = c.take<int32_t>(n);
     t.nbig = c.take<int32_t>(1);
     t.scan = c.take<char>(scan_ws_bytes(n));
@@ -162,44 +170,6 @@ __global__ void zero_i32_kernel(int32_t* a, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         a[i] = 0;
-}
-
-__global__ void indeg_kernel(const int32_t* __restrict__ nbr, int64_t nk, int32_t* indeg)
-{
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e < nk) atomicAdd(&indeg[nbr[e]], 1);
-}
-
-__global__ void raw_count_kernel(const int32_t* __restrict__ indeg, int64_t n, int k, int32_t* cnt, int32_t* fill)
-{
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) {
-        cnt[i] = 1 + k + indeg[i];
-        fill[i] = 0;
-    }
-}
-
-__global__ void raw_scatter_kernel(const int32_t* __restrict__ nbr, const double* __restrict__ nbr_d2, int64_t n,
-                                   int k, const int64_t* __restrict__ raw_ptr, int32_t* fill, int32_t* raw_col,
-                                   float* raw_d2)
-{
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e < n) {   // diagonal
-        raw_col[raw_ptr[e]] = (int32_t)e;
-        raw_d2[raw_ptr[e]] = 0.f;
-    }
-    if (e >= n * k) return;
-    int64_t i = e / k;
-    int r = (int)(e - i * k);
-    int32_t j = nbr[e];
-    float d = (float)nbr_d2[e];
-    int64_t own = raw_ptr[i] + 1 + r;
-    raw_col[own] = j;
-    raw_d2[own] = d;
-    int slot = atomicAdd(&fill[j], 1);
-    int64_t tr = raw_ptr[j] + 1 + k + slot;
-    raw_col[tr] = (int32_t)i;
-    raw_d2[tr] = d;
 }
 
 // bitonic sort of P (power of two) 64-bit keys in shared memory by `nthr` threads
@@ -219,119 +189,178 @@ __device__ __forceinline__ void bitonic_smem(uint64_t* a, int P, int tid, int nt
     }
 }
 
-// Sort one row's raw entries by column, drop duplicates, write back in place.
-__device__ void sort_dedupe_row(uint64_t* buf, int c, int P, int64_t rb, int32_t* raw_col, float* raw_d2,
-                                int32_t* cnt, int64_t i, int tid, int nthr, bool warp_only, int32_t* s_tot)
+// Number of entries of the ascending list a[0..len) below v.
+__device__ __forceinline__ int lower_bound_i32(const int32_t* a, int len, int32_t v)
 {
-    for (int e = tid; e < P; e += nthr)
-        buf[e] = e < c ? ((uint64_t)(uint32_t)raw_col[rb + e] << 32) | __float_as_uint(raw_d2[rb + e]) : ~0ull;
-    if (warp_only) __syncwarp(); else __syncthreads();
-    bitonic_smem(buf, P, tid, nthr, warp_only);
-    // unique entries: first of each run of equal columns, compacted in order
-    const int lane = tid & 31;
-    int32_t base = 0;
-    for (int e0 = 0; e0 < c; e0 += nthr) {
-        int e = e0 + tid;
-        bool first = e < c && (e == 0 || (buf[e] >> 32) != (buf[e - 1] >> 32));
-        unsigned bal = __ballot_sync(0xffffffffu, first);
-        int32_t off = __popc(bal & ((1u << lane) - 1u));
-        int32_t tot;
-        if (warp_only) {
-            tot = __popc(bal);
-        } else {
-            const int w = tid >> 5, nw = nthr >> 5;
-            if (lane == 0) s_tot[w] = __popc(bal);
-            __syncthreads();
-            tot = 0;
-            for (int ww = 0; ww < nw; ++ww) {
-                if (ww < w) off += s_tot[ww];
-                tot += s_tot[ww];
-            }
-            __syncthreads();
-        }
-        if (first) {
-            raw_col[rb + base + off] = (int32_t)(buf[e] >> 32);
-            raw_d2[rb + base + off] = __uint_as_float((uint32_t)buf[e]);
-        }
-        base += tot;
+    int lo = 0, hi = len;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < v) lo = mid + 1;
+        else hi = mid;
     }
-    if (tid == 0) cnt[i] = base;
+    return lo;
+}
+__device__ __forceinline__ int lower_bound_key(const uint64_t* a, int len, int32_t v)
+{
+    int lo = 0, hi = len;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((int32_t)(a[mid] >> 32) < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
 }
 
-__global__ void __launch_bounds__(SORT_WARPS * 32) row_sort_kernel(const int64_t* __restrict__ raw_ptr, int64_t n,
-                                                                    int32_t* raw_col, float* raw_d2, int32_t* cnt,
-                                                                    int32_t* big, int32_t* nbig, DevReport* rep)
+constexpr int SORT_WARPS = 4;
+
+// Own kNN lists sorted by column, one warp per row; the FP32 value of each entry is the
+// rounding of its canonical FP64 distance (identical for (i, j) and (j, i)).
+__global__ void __launch_bounds__(SORT_WARPS * 32) own_sort_kernel(const int32_t* __restrict__ nbr,
+                                                                    const double* __restrict__ nbr_d2, int64_t n,
+                                                                    int k, int32_t* own_col, float* own_d2)
 {
-    __shared__ uint64_t buf[SORT_WARPS][ROW_CAP];
+    __shared__ uint64_t buf[SORT_WARPS][OWN_CAP];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int P = 32;
+    while (P < k) P <<= 1;
     for (int64_t i = (int64_t)blockIdx.x * SORT_WARPS + w; i < n; i += (int64_t)gridDim.x * SORT_WARPS) {
-        int64_t rb = raw_ptr[i];
-        int c = (int)(raw_ptr[i + 1] - rb);
-        if (c > ROW_CAP) {
-            if (lane == 0) {
-                int s = atomicAdd(nbig, 1);
-                big[s] = (int32_t)i;
-                atomicAdd(&rep->union_big_rows, 1ull);
-            }
-            continue;
+        for (int e = lane; e < P; e += 32)
+            buf[w][e] = e < k ? ((uint64_t)(uint32_t)nbr[i * k + e] << 32) | __float_as_uint((float)nbr_d2[i * k + e])
+                              : ~0ull;
+        __syncwarp();
+        bitonic_smem(buf[w], P, lane, 32, true);
+        for (int e = lane; e < k; e += 32) {
+            own_col[i * k + e] = (int32_t)(buf[w][e] >> 32);
+            own_d2[i * k + e] = __uint_as_float((uint32_t)buf[w][e]);
         }
-        int P = 32;
-        while (P < c) P <<= 1;
-        sort_dedupe_row(buf[w], c, P, rb, raw_col, raw_d2, cnt, i, lane, 32, true, nullptr);
         __syncwarp();
     }
 }
 
-__global__ void __launch_bounds__(1024) big_row_sort_kernel(const int64_t* __restrict__ raw_ptr, int32_t* raw_col,
-                                                           float* raw_d2, int32_t* cnt, const int32_t* __restrict__ big,
-                                                           const int32_t* __restrict__ nbig, DevReport* rep)
+// Reverse candidates (i -> j, j = nbr[i][r]) that are not mutual: counted (pass 0) or
+// scattered into row j's reverse slots (pass 1).
+__global__ void reverse_kernel(const int32_t* __restrict__ nbr, const double* __restrict__ nbr_d2, int64_t n, int k,
+                               const int32_t* __restrict__ own_col, int pass, int32_t* rcnt,
+                               const int64_t* __restrict__ row_ptr, int32_t* fill, int32_t* rev_col, float* rev_d2)
 {
-    extern __shared__ uint64_t bbuf[];
-    __shared__ int32_t s_tot[32];
-    const int nb = *nbig;
-    for (int f = blockIdx.x; f < nb; f += gridDim.x) {
-        int64_t i = big[f];
-        int64_t rb = raw_ptr[i];
-        int c = (int)(raw_ptr[i + 1] - rb);
-        if (c > BIG_CAP) {
-            if (threadIdx.x == 0) {
-                report_error(rep, VB_ERR_UNSUPPORTED);
-                cnt[i] = 0;
-            }
-            continue;
-        }
-        int P = 32;
-        while (P < c) P <<= 1;
-        sort_dedupe_row(bbuf, c, P, rb, raw_col, raw_d2, cnt, i, threadIdx.x, blockDim.x, false, s_tot);
-        __syncthreads();
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * k) return;
+    const int64_t i = e / k;
+    const int32_t j = nbr[e];
+    const int32_t* oj = own_col + (int64_t)j * k;
+    const int pos = lower_bound_i32(oj, k, (int32_t)i);
+    if (pos < k && oj[pos] == (int32_t)i) return;   // mutual: already in row j's own list
+    if (pass == 0) {
+        atomicAdd(&rcnt[j], 1);
+        return;
+    }
+    const int slot = atomicAdd(&fill[j], 1);
+    const int64_t off = row_ptr[j] - (int64_t)j * (1 + k) + slot;
+    rev_col[off] = (int32_t)i;
+    rev_d2[off] = (float)nbr_d2[e];
+}
+
+__global__ void row_len_kernel(const int32_t* __restrict__ rcnt, int64_t n, int k, int32_t* cnt, int32_t* fill)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        cnt[i] = 1 + k + rcnt[i];
+        fill[i] = 0;
     }
 }
 
-__global__ void compact_kernel(const int64_t* __restrict__ raw_ptr, const int64_t* __restrict__ row_ptr, int64_t n,
-                               const int32_t* __restrict__ raw_col, const float* __restrict__ raw_d2, int32_t* col,
-                               float* ed2, int64_t cap, int64_t* nnz_dev, DevReport* rep)
+// Row j: sort R(j) in shared memory, then write every entry at its rank.
+__device__ void merge_row(int64_t j, int k, int r, uint64_t* rb, const int64_t* __restrict__ row_ptr,
+                          const int32_t* __restrict__ own_col, const float* __restrict__ own_d2,
+                          const int32_t* __restrict__ rev_col, const float* __restrict__ rev_d2, int32_t* col,
+                          float* ed2, int tid, int nthr, bool warp_only)
 {
-    const int lane = threadIdx.x & 31;
-    int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    if (wid == 0 && lane == 0) {
+    int P = 32;
+    while (P < r) P <<= 1;
+    const int64_t roff = row_ptr[j] - j * (1 + k);
+    for (int e = tid; e < P; e += nthr)
+        rb[e] = e < r ? ((uint64_t)(uint32_t)rev_col[roff + e] << 32) | __float_as_uint(rev_d2[roff + e]) : ~0ull;
+    if (warp_only) __syncwarp(); else __syncthreads();
+    if (r > 1) bitonic_smem(rb, P, tid, nthr, warp_only);
+    const int64_t ob = row_ptr[j];
+    const int32_t* oc = own_col + j * k;
+    const float* od = own_d2 + j * k;
+    for (int a = tid; a < k; a += nthr) {
+        const int32_t c = oc[a];
+        const int rank = a + lower_bound_key(rb, r, c) + ((int32_t)j < c ? 1 : 0);
+        col[ob + rank] = c;
+        ed2[ob + rank] = od[a];
+    }
+    for (int b = tid; b < r; b += nthr) {
+        const int32_t c = (int32_t)(rb[b] >> 32);
+        const int rank = b + lower_bound_i32(oc, k, c) + ((int32_t)j < c ? 1 : 0);
+        col[ob + rank] = c;
+        ed2[ob + rank] = __uint_as_float((uint32_t)rb[b]);
+    }
+    if (tid == 0) {
+        const int rank = lower_bound_i32(oc, k, (int32_t)j) + lower_bound_key(rb, r, (int32_t)j);
+        col[ob + rank] = (int32_t)j;
+        ed2[ob + rank] = 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(SORT_WARPS * 32) merge_kernel(const int64_t* __restrict__ row_ptr, int64_t n, int k,
+                                                                 const int32_t* __restrict__ own_col,
+                                                                 const float* __restrict__ own_d2,
+                                                                 const int32_t* __restrict__ rev_col,
+                                                                 const float* __restrict__ rev_d2, int32_t* col,
+                                                                 float* ed2, int64_t cap, int32_t* big, int32_t* nbig,
+                                                                 int64_t* nnz_dev, DevReport* rep)
+{
+    __shared__ uint64_t buf[SORT_WARPS][RCAP];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         *nnz_dev = row_ptr[n];
         if (row_ptr[n] > cap) report_error(rep, VB_ERR_BOUNDS);
     }
-    for (int64_t i = wid; i < n; i += nw) {
-        int64_t rb = raw_ptr[i], ob = row_ptr[i], c = row_ptr[i + 1] - ob;
-        if (ob + c > cap) continue;
-        for (int64_t e = lane; e < c; e += 32) {
-            col[ob + e] = raw_col[rb + e];
-            ed2[ob + e] = raw_d2[rb + e];
+    if (row_ptr[n] > cap) return;
+    for (int64_t j = (int64_t)blockIdx.x * SORT_WARPS + w; j < n; j += (int64_t)gridDim.x * SORT_WARPS) {
+        const int r = (int)(row_ptr[j + 1] - row_ptr[j]) - 1 - k;
+        if (r > RCAP) {
+            if (lane == 0) {
+                big[atomicAdd(nbig, 1)] = (int32_t)j;
+                atomicAdd(&rep->union_big_rows, 1ull);
+            }
+            continue;
         }
+        merge_row(j, k, r, buf[w], row_ptr, own_col, own_d2, rev_col, rev_d2, col, ed2, lane, 32, true);
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(1024) big_merge_kernel(const int64_t* __restrict__ row_ptr, int64_t n, int k,
+                                                        const int32_t* __restrict__ own_col,
+                                                        const float* __restrict__ own_d2,
+                                                        const int32_t* __restrict__ rev_col,
+                                                        const float* __restrict__ rev_d2, int32_t* col, float* ed2,
+                                                        int64_t cap, const int32_t* __restrict__ big,
+                                                        const int32_t* __restrict__ nbig, DevReport* rep)
+{
+    extern __shared__ uint64_t bbuf[];
+    if (row_ptr[n] > cap) return;
+    const int nb = *nbig;
+    for (int f = blockIdx.x; f < nb; f += gridDim.x) {
+        const int64_t j = big[f];
+        const int r = (int)(row_ptr[j + 1] - row_ptr[j]) - 1 - k;
+        if (r > BIG_CAP) {   // a hub point in more than BIG_CAP other lists
+            if (threadIdx.x == 0) report_error(rep, VB_ERR_UNSUPPORTED);
+            continue;
+        }
+        merge_row(j, k, r, bbuf, row_ptr, own_col, own_d2, rev_col, rev_d2, col, ed2, threadIdx.x, blockDim.x, false);
+        __syncthreads();
     }
 }
 
 vb_status graph_run(Ctx* ctx, int64_t n, int32_t k, const int32_t* nbr, const double* nbr_d2, int64_t* row_ptr,
                     int32_t* col, float* ed2, int64_t cap, int64_t* nnz_dev, void* ws, size_t ws_bytes)
 {
-    if (n < 2 || k < 1 || k > n - 1 || !nbr || !nbr_d2 || !row_ptr || !col || !ed2 || !nnz_dev) return VB_ERR_ARG;
+    if (n < 2 || k < 1 || k > n - 1 || k > OWN_CAP || !nbr || !nbr_d2 || !row_ptr || !col || !ed2 || !nnz_dev)
+        return VB_ERR_ARG;
     if (cap < n * (2 * (int64_t)k + 1)) return VB_ERR_ARG;
     GraphWs w;
     Carve c(ws);
@@ -340,32 +369,30 @@ vb_status graph_run(Ctx* ctx, int64_t n, int32_t k, const int32_t* nbr, const do
     cudaStream_t s = ctx->stream;
     const int64_t nk = n * k;
     const unsigned gz = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8);
+    const unsigned ge = (unsigned)((nk + 255) / 256);
     mark(ctx, VB_STAGE_GRAPH, 0);
-    zero_i32_kernel<<<gz, 256, 0, s>>>(w.indeg, n);
+    zero_i32_kernel<<<gz, 256, 0, s>>>(w.rcnt, n);
     zero_i32_kernel<<<1, 32, 0, s>>>(w.nbig, 1);
-    indeg_kernel<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(nbr, nk, w.indeg);
-    raw_count_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.indeg, n, k, w.cnt, w.fill);
-    vb_status st = scan_counts(s, w.cnt, n, w.raw_ptr, w.scan);
+    own_sort_kernel<<<152 * 16, SORT_WARPS * 32, 0, s>>>(nbr, nbr_d2, n, k, w.own_col, w.own_d2);
+    reverse_kernel<<<ge, 256, 0, s>>>(nbr, nbr_d2, n, k, w.own_col, 0, w.rcnt, nullptr, nullptr, nullptr, nullptr);
+    row_len_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.rcnt, n, k, w.cnt, w.fill);
+    vb_status st = scan_counts(s, w.cnt, n, row_ptr, w.scan);
     if (st != VB_OK) return st;
-    raw_scatter_kernel<<<(unsigned)((std::max(nk, n) + 255) / 256), 256, 0, s>>>(nbr, nbr_d2, n, k, w.raw_ptr, w.fill,
-                                                                             w.raw_col, w.raw_d2);
-    row_sort_kernel<<<152 * 16, SORT_WARPS * 32, 0, s>>>(w.raw_ptr, n, w.raw_col, w.raw_d2, w.cnt, w.big, w.nbig,
-                                                         ctx->rep);
+    reverse_kernel<<<ge, 256, 0, s>>>(nbr, nbr_d2, n, k, w.own_col, 1, w.rcnt, row_ptr, w.fill, w.rev_col, w.rev_d2);
+    merge_kernel<<<152 * 16, SORT_WARPS * 32, 0, s>>>(row_ptr, n, k, w.own_col, w.own_d2, w.rev_col, w.rev_d2, col, ed2,
+                                                      cap, w.big, w.nbig, nnz_dev, ctx->rep);
     static bool big_attr[16] = {};
     int dev = ctx->device & 15;
     if (!big_attr[dev]) {
-        if (cudaFuncSetAttribute(big_row_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 BIG_CAP * 8) != cudaSuccess)
+        if (cudaFuncSetAttribute(big_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, BIG_CAP * 8) !=
+            cudaSuccess)
             return VB_ERR_CUDA;
         big_attr[dev] = true;
     }
-    big_row_sort_kernel<<<152, 1024, BIG_CAP * 8, s>>>(w.raw_ptr, w.raw_col, w.raw_d2, w.cnt, w.big, w.nbig, ctx->rep);
-    st = scan_counts(s, w.cnt, n, row_ptr, w.scan);
-    if (st != VB_OK) return st;
-    compact_kernel<<<152 * 8, 256, 0, s>>>(w.raw_ptr, row_ptr, n, w.raw_col, w.raw_d2, col, ed2, cap, nnz_dev,
-                                           ctx->rep);
+    big_merge_kernel<<<152, 1024, BIG_CAP * 8, s>>>(row_ptr, n, k, w.own_col, w.own_d2, w.rev_col, w.rev_d2, col, ed2,
+                                                    cap, w.big, w.nbig, ctx->rep);
     mark(ctx, VB_STAGE_GRAPH, 1);
-    ctx->launches += 14;
+    ctx->launches += 12;
     return last_launch();
 }
 

@@ -33,7 +33,8 @@ namespace vb {
 
 constexpr int TILE = 64;            // points per query tile and per candidate tile
 constexpr int RADIX_T = 256;        // threads of the radix kernels
-constexpr int RADIX_ITEMS = 1024;   // keys per radix block (4 rounds of 256)
+constexpr int RADIX_ITEMS = 2048;   // keys per radix block (8 rounds of 256)
+constexpr int USCAN_T = 1024, USCAN_ITEMS = 8, USCAN_CHUNK = USCAN_T * USCAN_ITEMS;   // histogram scan
 constexpr int FB_THREADS = 256;
 
 struct KnnWs {
@@ -41,6 +42,7 @@ struct KnnWs {
     uint32_t* key[2];
     uint32_t* val[2];     // val[0] after the sort = perm (sorted position -> original index)
     uint32_t* hist;       // 256 * nblk
+    uint32_t* hsum;       // block sums of the histogram scan
     float* xs;            // npad * MP sorted coordinates
     float* tlo;           // ntiles * MP
     float* thi;
@@ -73,6 +75,7 @@ size_t knn_plan(Carve& c, int64_t n, int32_t m, const vb_knn_params*, KnnWs* w)
     t.val[0] = c.take<uint32_t>(n);
     t.val[1] = c.take<uint32_t>(n);
     t.hist = c.take<uint32_t>(256 * nblk);
+    t.hsum = c.take<uint32_t>((256 * nblk + USCAN_CHUNK - 1) / USCAN_CHUNK + 1);
     t.xs = c.take<float>(npad * mp);
     t.tlo = c.take<float>(ntiles * mp);
     t.thi = c.take<float>(ntiles * mp);
@@ -156,7 +159,7 @@ __global__ void morton_kernel(const float* __restrict__ x, int64_t n, int m, int
 __global__ void cloud_key_kernel(const uint32_t* __restrict__ val, int64_t n, Clouds cl, uint32_t* key)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) key[i] = (uint32_t)cloud_of(cl.ptr, cl.B, (int64_t)val[i]);
+    if (i < n) key[i] = (uint32_t)cloud_id(cl, (int64_t)val[i]);
 }
 
 __global__ void radix_hist_kernel(const uint32_t* __restrict__ key, int64_t n, int shift, uint32_t* hist, int nblk)
@@ -173,29 +176,92 @@ __global__ void radix_hist_kernel(const uint32_t* __restrict__ key, int64_t n, i
     hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// In-place exclusive scan of len uint32 values by one block of 1024 threads.
-__global__ void scan_u32_single_kernel(uint32_t* a, int64_t len)
+// In-place exclusive scan of len uint32 values: per-block sums of 8192 values, one
+// block scans the block sums, then every block rescans its chunk with its offset.
+__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* sh, uint32_t* total)
 {
-    __shared__ uint32_t part[1024];
-    const int t = threadIdx.x;
-    int64_t chunk = (len + 1023) / 1024;
-    int64_t b = t * chunk, e = min(len, b + chunk);
-    uint32_t s = 0;
-    for (int64_t i = b; i < e; ++i) s += a[i];
-    part[t] = s;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[w] = x;
     __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        uint32_t v = t >= o ? part[t - o] : 0u;
+    if (w == 0) {
+        uint32_t z = sh[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o) z += y;
+        }
+        sh[lane] = z;
+    }
+    __syncthreads();
+    const uint32_t r = x - v + (w ? sh[w - 1] : 0u);
+    if (total) *total = sh[31];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(USCAN_T) uscan_reduce_kernel(const uint32_t* __restrict__ a, int64_t len,
+                                                              uint32_t* bsum)
+{
+    __shared__ uint32_t sh[32];
+    const int64_t base = (int64_t)blockIdx.x * USCAN_CHUNK + (int64_t)threadIdx.x * USCAN_ITEMS;
+    uint32_t v = 0;
+#pragma unroll
+    for (int i = 0; i < USCAN_ITEMS; ++i)
+        if (base + i < len) v += a[base + i];
+    uint32_t tot;
+    block_excl_scan_u32(v, sh, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(USCAN_T) uscan_top_kernel(uint32_t* bsum, int nb)
+{
+    __shared__ uint32_t sh[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nb; b0 += USCAN_T) {
+        const int i = b0 + threadIdx.x;
+        const uint32_t v = i < nb ? bsum[i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_excl_scan_u32(v, sh, &tot);
+        if (i < nb) bsum[i] = carry + ex;
         __syncthreads();
-        part[t] += v;
+        if (threadIdx.x == 0) carry += tot;
         __syncthreads();
     }
-    uint32_t run = part[t] - s;
-    for (int64_t i = b; i < e; ++i) {
-        uint32_t v = a[i];
-        a[i] = run;
-        run += v;
+}
+
+__global__ void __launch_bounds__(USCAN_T) uscan_apply_kernel(uint32_t* a, int64_t len, const uint32_t* __restrict__ bsum)
+{
+    __shared__ uint32_t sh[32];
+    const int64_t base = (int64_t)blockIdx.x * USCAN_CHUNK + (int64_t)threadIdx.x * USCAN_ITEMS;
+    uint32_t v[USCAN_ITEMS];
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < USCAN_ITEMS; ++i) {
+        v[i] = base + i < len ? a[base + i] : 0u;
+        s += v[i];
     }
+    uint32_t run = bsum[blockIdx.x] + block_excl_scan_u32(s, sh, nullptr);
+#pragma unroll
+    for (int i = 0; i < USCAN_ITEMS; ++i) {
+        if (base + i < len) a[base + i] = run;
+        run += v[i];
+    }
+}
+
+static void scan_u32(cudaStream_t s, uint32_t* a, int64_t len, uint32_t* bsum)
+{
+    const int nb = (int)((len + USCAN_CHUNK - 1) / USCAN_CHUNK);
+    uscan_reduce_kernel<<<nb, USCAN_T, 0, s>>>(a, len, bsum);
+    uscan_top_kernel<<<1, USCAN_T, 0, s>>>(bsum, nb);
+    uscan_apply_kernel<<<nb, USCAN_T, 0, s>>>(a, len, bsum);
 }
 
 // Stable scatter: inside a block, rounds of 256 consecutive keys; inside a
@@ -532,7 +598,8 @@ __device__ bool finalize_row_band(const TileArgs& a, uint64_t* arr, int t, int s
 //   cand  [64][MP] f32  staged candidate tile
 //   qs    [MP][64] f32  query coordinates (MP > 16 only)
 //   slist [SCAP]   u64  surviving candidate tiles keyed (box lower bound bits << 32 | tile)
-template <int MP>
+// MR <= MP is the number of coordinates the distance loop reads (the rest are zero padding).
+template <int MP, int MR = MP>
 __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -565,7 +632,7 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
         const bool valid = p < a.n;
         int64_t qlo = 0, qhi = a.n;   // the query's cloud
         if (a.cl.B > 1 && valid) {
-            const int b = cloud_of(a.cl.ptr, a.cl.B, p);
+            const int b = cloud_id(a.cl, p);
             qlo = a.cl.ptr[b];
             qhi = a.cl.ptr[b + 1];
         }
@@ -641,10 +708,13 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
             if (need) {
                 evaluated += TILE;
                 const int64_t c0 = ct * TILE;
+                // the whole candidate tile lies in this query's cloud and is not its own tile
+                const bool whole = ct != qt && c0 >= qlo && c0 + TILE <= qhi;
                 for (int cb = 0; cb < TILE; cb += IB) {
                     // distances of one batch; keys under the current threshold go to buf
                     int cnt = 0;
                     const uint64_t thr = maxkey;
+                    const uint32_t thr_hi = (uint32_t)(thr >> 32);
 #pragma unroll 4
                     for (int c = cb; c < cb + IB; ++c) {
                         float acc = 0.f;
@@ -652,13 +722,13 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
                             const float4* cv = (const float4*)(cand + c * MP);
 #pragma unroll
                             for (int r4 = 0; r4 < MP / 4; ++r4) {
-                                float4 v = cv[r4];
-                                float d0 = qr[4 * r4 + 0] - v.x, d1 = qr[4 * r4 + 1] - v.y;
-                                float d2 = qr[4 * r4 + 2] - v.z, d3 = qr[4 * r4 + 3] - v.w;
-                                acc = fmaf(d0, d0, acc);
-                                acc = fmaf(d1, d1, acc);
-                                acc = fmaf(d2, d2, acc);
-                                acc = fmaf(d3, d3, acc);
+                                const float4 v = cv[r4];
+                                const float d0 = qr[4 * r4 + 0] - v.x, d1 = qr[4 * r4 + 1] - v.y;
+                                const float d2 = qr[4 * r4 + 2] - v.z, d3 = qr[4 * r4 + 3] - v.w;
+                                if (4 * r4 + 0 < MR) acc = fmaf(d0, d0, acc);
+                                if (4 * r4 + 1 < MR) acc = fmaf(d1, d1, acc);
+                                if (4 * r4 + 2 < MR) acc = fmaf(d2, d2, acc);
+                                if (4 * r4 + 3 < MR) acc = fmaf(d3, d3, acc);
                             }
                         } else {
                             for (int r = 0; r < MP; ++r) {
@@ -666,11 +736,14 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
                                 acc = fmaf(d, d, acc);
                             }
                         }
-                        const int64_t cp = c0 + c;
-                        const uint64_t key = ((uint64_t)__float_as_uint(acc) << 32) | (uint32_t)cp;
-                        const bool take = key < thr && cp != p && cp >= qlo && cp < qhi;
-                        if (take) buf[cnt * TILE + t] = key;
-                        cnt += take;
+                        if (__float_as_uint(acc) <= thr_hi) {   // rare once the heap is full
+                            const int64_t cp = c0 + c;
+                            const uint64_t key = ((uint64_t)__float_as_uint(acc) << 32) | (uint32_t)cp;
+                            if (key < thr && (whole || (cp != p && cp >= qlo && cp < qhi))) {
+                                buf[cnt * TILE + t] = key;
+                                ++cnt;
+                            }
+                        }
                     }
                     rounds += cnt;
                     for (int b = 0; b < cnt; ++b) {
@@ -878,7 +951,7 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
         const bool valid = p < a.n;
         int64_t qlo = 0, qhi = a.n;   // the query's cloud
         if (a.cl.B > 1 && valid) {
-            const int b = cloud_of(a.cl.ptr, a.cl.B, p);
+            const int b = cloud_id(a.cl, p);
             qlo = a.cl.ptr[b];
             qhi = a.cl.ptr[b + 1];
         }
@@ -1160,7 +1233,7 @@ __global__ void __launch_bounds__(FB_THREADS) knn_fallback_kernel(const float* _
     for (int f = blockIdx.x; f < cnt; f += gridDim.x) {
         const int64_t q = fb_list[f];
         const float* xq = x + q * m;
-        const int cb = cloud_of(cl.ptr, cl.B, q);
+        const int cb = cloud_id(cl, q);
         const int64_t lo = cloud_lo(cl, cb), hi = cloud_hi(cl, cb, n);   // candidates: the query's cloud
         if (t == 0) { s_prefix = 0; s_mask = 0; s_need = (uint32_t)k; s_less = 0; }
         __syncthreads();
@@ -1254,44 +1327,66 @@ static vb_status launch_tc(TileArgs a, cudaStream_t s)
     const size_t sm = tc_smem<MP>(a.cap);
     if (sm > 220 * 1024) return VB_ERR_UNSUPPORTED;   // k + margin too large for 128 heaps with these operands
     static bool attr_set[16] = {};
-    static int sms[16] = {};
+    static int sms[16] = {}, smem_sm[16] = {}, static_smem[16] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (!attr_set[dev & 15]) {
         if (cudaFuncSetAttribute(knn_tc_kernel<MP, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(220 * 1024)) != cudaSuccess)
+                                 (int)(220 * 1024)) != cudaSuccess ||
+            cudaFuncSetAttribute(knn_tc_kernel<MP, F16>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
             return VB_ERR_CUDA;
-        if (cudaDeviceGetAttribute(&sms[dev & 15], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, knn_tc_kernel<MP, F16>) != cudaSuccess) return VB_ERR_CUDA;
+        static_smem[dev & 15] = (int)fa.sharedSizeBytes;
+        if (cudaDeviceGetAttribute(&sms[dev & 15], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_sm[dev & 15], cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+                cudaSuccess)
             return VB_ERR_CUDA;
         attr_set[dev & 15] = true;
     }
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, knn_tc_kernel<MP, F16>, T2, sm) != cudaSuccess ||
-        per_sm < 1)
-        return VB_ERR_CUDA;
-    per_sm = std::min(per_sm, 8);   // 64 TMEM columns per CTA, 512 per SM
+    // CTAs per SM from shared memory (1 KB reserved per CTA), at most 8 (64 TMEM columns each, 512 per SM);
+    // extra CTAs of this persistent grid would only wait for a free slot
+    const int per_cta = (int)sm + static_smem[dev & 15] + 1024;
+    const int per_sm = std::max(1, std::min(8, smem_sm[dev & 15] / per_cta));
     const int64_t nst = (a.ntiles + 1) / 2;
     const int64_t grid = std::min<int64_t>(nst, (int64_t)per_sm * sms[dev & 15]);
     knn_tc_kernel<MP, F16><<<(unsigned)grid, T2, sm, s>>>(a);
     return last_launch();
 }
 
-template <int MP>
-static vb_status launch_tile(const TileArgs& a, cudaStream_t s)
+template <int MP, int MR = MP>
+static vb_status launch_tile_m(const TileArgs& a, cudaStream_t s)
 {
     size_t sm = tile_smem<MP>(a.L);
     static bool attr_set[16] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (!attr_set[dev & 15]) {
-        if (cudaFuncSetAttribute(knn_tile_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tile_smem<MP>(256)) !=
-            cudaSuccess)
+        if (cudaFuncSetAttribute(knn_tile_kernel<MP, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tile_smem<MP>(256)) != cudaSuccess ||
+            cudaFuncSetAttribute(knn_tile_kernel<MP, MR>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
             return VB_ERR_CUDA;
         attr_set[dev & 15] = true;
     }
-    knn_tile_kernel<MP><<<(unsigned)a.ntiles, TILE, sm, s>>>(a);
+    knn_tile_kernel<MP, MR><<<(unsigned)a.ntiles, TILE, sm, s>>>(a);
     return last_launch();
+}
+
+// m <= 4: the distance loop reads only the m real coordinates of the 4-wide rows.
+template <int MP>
+static vb_status launch_tile(const TileArgs& a, cudaStream_t s)
+{
+    if constexpr (MP == 4) {
+        switch (a.m) {
+            case 1: return launch_tile_m<4, 1>(a, s);
+            case 2: return launch_tile_m<4, 2>(a, s);
+            case 3: return launch_tile_m<4, 3>(a, s);
+            default: return launch_tile_m<4, 4>(a, s);
+        }
+    }
+    return launch_tile_m<MP>(a, s);
 }
 
 vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_params* p, int32_t* nbr,
@@ -1320,7 +1415,7 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
     int cur = 0;
     for (int shift = 0; shift < 32; shift += 8) {
         radix_hist_kernel<<<nblk, RADIX_T, 0, s>>>(w.key[cur], n, shift, w.hist, nblk);
-        scan_u32_single_kernel<<<1, 1024, 0, s>>>(w.hist, (int64_t)256 * nblk);
+        scan_u32(s, w.hist, (int64_t)256 * nblk, w.hsum);
         radix_scatter_kernel<<<nblk, RADIX_T, 0, s>>>(w.key[cur], w.val[cur], w.key[cur ^ 1], w.val[cur ^ 1], n,
                                                       shift, w.hist, nblk);
         cur ^= 1;
@@ -1332,11 +1427,11 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
         ctx->launches += 1;
         for (int shift = 0; (int64_t)(cl.B - 1) >> shift; shift += 8) {
             radix_hist_kernel<<<nblk, RADIX_T, 0, s>>>(w.key[cur], n, shift, w.hist, nblk);
-            scan_u32_single_kernel<<<1, 1024, 0, s>>>(w.hist, (int64_t)256 * nblk);
+            scan_u32(s, w.hist, (int64_t)256 * nblk, w.hsum);
             radix_scatter_kernel<<<nblk, RADIX_T, 0, s>>>(w.key[cur], w.val[cur], w.key[cur ^ 1], w.val[cur ^ 1], n,
                                                           shift, w.hist, nblk);
             cur ^= 1;
-            ctx->launches += 3;
+            ctx->launches += 5;
         }
     }
     const uint32_t* perm = w.val[cur];
@@ -1427,7 +1522,7 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
     ctx->launches += launches;
     knn_fallback_kernel<<<152, FB_THREADS, 0, s>>>(x, n, m, p->k, w.fb_list, w.fb_count, cl, nbr, nbr_d2);
     mark(ctx, VB_STAGE_KNN_FALLBACK, 1);
-    ctx->launches += 19;
+    ctx->launches += 27;   // order: 3 + 4 radix passes x 5 + gather + boxes; search; fallback
     return last_launch();
 }
 

@@ -1,9 +1,12 @@
 // Row passes over the symmetric pattern (steps a9-a14 of the build).
 //
 // Every pass is a fixed grid of warps walking CSR rows (warp w takes rows
-// w, w + W, ...), lanes striding the row's entries.  Per-entry arithmetic is
-// FP32 (ex2 on the SFU); row sums and sweep sums are carried to FP64 in a
-// fixed order, so every result is bitwise reproducible run to run.
+// w, w + W, ...; the reductions take contiguous row ranges per block, split per
+// point cloud), lanes striding the row's entries.  Per-entry arithmetic is FP32
+// (ex2 on the SFU); a row's lane partials are added by a fixed FP32 shuffle tree
+// (GB300's FP64 pipe is narrow: an FP64 tree per row cost more than the row),
+// and sums across rows and blocks are carried in FP64 in a fixed order, so every
+// result is bitwise reproducible run to run.
 //   a9/a11 epsilon sweep (Sec. 2.3): chi_g = sum_E exp(-ed2 / (scale 2^xi_g rho_i rho_j))
 //          for all grid points in one pass; the diagonal contributes n.
 //   a10    density (Sec. 2.1): psi_i = sum_j K_eps^ij / (n (pi eps^2 b_i^2)^(d/2)), P = psi^beta.
@@ -35,6 +38,31 @@ struct RowIter {
     }
 };
 
+// Rows handled by groups of LPR lanes (8, 16 or 32; 16 by default, which suits rows of
+// k + 1 .. 2k + 1 entries for k = 16 .. 128), 32 / LPR rows per warp at a time; the loop
+// over row bases is warp-uniform so the group sums can use full-warp shuffles.  Every
+// entry point uses the same LPR, so a build and its step-by-step calls agree bit for bit.
+template <int LPR>
+struct RowGroup {
+    static constexpr int RPW = 32 / LPR;
+    int64_t base, step;
+    int sub, grp;
+    __device__ RowGroup()
+    {
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        sub = lane % LPR;
+        grp = lane / LPR;
+        base = ((int64_t)blockIdx.x * WARPS + w) * RPW;
+        step = (int64_t)gridDim.x * WARPS * RPW;
+    }
+    static __device__ __forceinline__ float sum(float v)
+    {
+#pragma unroll
+        for (int o = LPR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    }
+};
+
 __global__ void recip_f32_kernel(const double* __restrict__ v, int64_t n, float scale, float* out)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -54,16 +82,35 @@ struct SweepConst {
 __host__ __device__ inline int64_t rows_per_block(int64_t n, int nblk) { return (n + nblk - 1) / nblk; }
 inline size_t seg_slots(int B) { return (size_t)kRowBlocks + (size_t)B; }
 
-// Sum over cloud b's slots of column g of partial (slots of G values), in block order.
-__device__ __forceinline__ double seg_total_lane(const double* __restrict__ partial, int G, int g, const Clouds& cl,
-                                                 int b, int64_t n, int nblk, int lane)
+// Column totals over cloud b's slots (slots of G values) by a block of SEG_T threads:
+// thread t sums column t % 64 over the slots bl = t / 64, t / 64 + SEG_PARTS, ... (reads of
+// consecutive columns are contiguous), then the SEG_PARTS partial sums of every column
+// are added in a fixed order.  out[g] for g < G; every thread must call it.
+constexpr int SEG_T = 1024, SEG_COLS = 64, SEG_PARTS = SEG_T / SEG_COLS;
+__device__ void seg_totals(const double* __restrict__ partial, int G, const Clouds& cl, int b, int64_t n, int nblk,
+                           double* sh /* [SEG_PARTS][SEG_COLS] */, double* out)
 {
     const int64_t per = rows_per_block(n, nblk);
     const int64_t lo = cloud_lo(cl, b), hi = cloud_hi(cl, b, n);
     const int64_t bl0 = lo / per, bl1 = (hi - 1) / per;
-    double s = 0.0;
-    for (int64_t bl = bl0 + lane; bl <= bl1; bl += 32) s += partial[(bl + b) * G + g];
-    return warp_sum_f64(s);
+    const int g = threadIdx.x % SEG_COLS, part = threadIdx.x / SEG_COLS;
+    double s0 = 0.0, s1 = 0.0;
+    if (g < G) {
+        int64_t bl = bl0 + part;
+        for (; bl + SEG_PARTS <= bl1; bl += 2 * SEG_PARTS) {
+            s0 += partial[(bl + b) * G + g];
+            s1 += partial[(bl + SEG_PARTS + b) * G + g];
+        }
+        if (bl <= bl1) s0 += partial[(bl + b) * G + g];
+    }
+    sh[part * SEG_COLS + g] = s0 + s1;
+    __syncthreads();
+    if (threadIdx.x < G) {
+        double t = 0.0;
+        for (int q = 0; q < SEG_PARTS; ++q) t += sh[q * SEG_COLS + threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(kRowThreads) sweep_kernel(const int64_t* __restrict__ row_ptr,
@@ -219,25 +266,22 @@ __global__ void __launch_bounds__(kRowThreads, 3) sweep57_kernel(const int64_t* 
     }
 }
 
-// One block per cloud: warp w sums grid columns w, w + 32, ... over the cloud's
-// slots in a fixed lane-strided order, then the threads take one log each and one
-// warp finds the first maximiser of chi'.
+// One block per cloud: the column totals over the cloud's slots (seg_totals), then
+// the threads take one log each and one warp finds the first maximiser of chi'.
 __global__ void __launch_bounds__(1024) sweep_finish_kernel(const double* __restrict__ partial, int nblk, int G,
                                                            int64_t n, Clouds cl, double xi_lo, double dxi,
                                                            const double* __restrict__ xi_c_dev, int warn_bit,
                                                            double* eps2, double* chi, double* dim, DevReport* rep)
 {
     __shared__ double sh[kMaxGrid], lg[kMaxGrid];
+    __shared__ double part[SEG_PARTS * SEG_COLS];
     const int b = blockIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const double nb = (double)(cloud_hi(cl, b, n) - cloud_lo(cl, b));
-    for (int g = w; g < G; g += 32) {
-        double s = seg_total_lane(partial, G, g, cl, b, n, nblk, lane);
-        if (lane == 0) {
-            s += nb;   // diagonal entries: exp(0) = 1 each
-            sh[g] = s;
-            chi[(int64_t)b * G + g] = s;
-        }
+    seg_totals(partial, G, cl, b, n, nblk, part, sh);
+    if (threadIdx.x < G) {
+        sh[threadIdx.x] += nb;   // diagonal entries: exp(0) = 1 each
+        chi[(int64_t)b * G + threadIdx.x] = sh[threadIdx.x];
     }
     __syncthreads();
     if (threadIdx.x < G) lg[threadIdx.x] = log(sh[threadIdx.x]);
@@ -312,21 +356,24 @@ __global__ void density_const_kernel(const double* __restrict__ eps2, int B, flo
     if (b < B) c[b] = (float)(1.4426950408889634 / eps2[b]);
 }
 
+template <int LPR>
 __global__ void __launch_bounds__(kRowThreads) density_kernel(const int64_t* __restrict__ row_ptr,
                                                             const int32_t* __restrict__ col,
                                                             const float* __restrict__ ed2, int64_t n,
                                                             const float* __restrict__ ib,
                                                             const float* __restrict__ cden, Clouds cl, double* psi)
 {
-    RowIter it;
-    for (int64_t i = it.i; i < n; i += it.step) {
-        const float c = cden[cloud_of(cl.ptr, cl.B, i)];
-        const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
-        const float bi = ib[i];
+    RowGroup<LPR> it;
+    for (int64_t b0 = it.base; b0 < n; b0 += it.step) {
+        const int64_t i = b0 + it.grp;
+        const bool ok = i < n;
+        const float c = ok ? cden[cloud_id(cl, i)] : 0.f;
+        const int64_t rb = ok ? row_ptr[i] : 0, re = ok ? row_ptr[i + 1] : 0;
+        const float bi = ok ? ib[i] : 0.f;
         float s = 0.f;
-        for (int64_t e = rb + it.lane; e < re; e += 32) s += ex2_approx(-(ed2[e] * (bi * ib[col[e]])) * c);
-        double tot = warp_sum_f64((double)s);
-        if (it.lane == 0) psi[i] = tot;
+        for (int64_t e = rb + it.sub; e < re; e += LPR) s += ex2_approx(-(ed2[e] * (bi * ib[col[e]])) * c);
+        const float tot = RowGroup<LPR>::sum(s);
+        if (ok && it.sub == 0) psi[i] = (double)tot;
     }
 }
 
@@ -339,7 +386,7 @@ __global__ void density_finish_kernel(const double* __restrict__ b, const double
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int cb = cloud_of(cl.ptr, cl.B, i);
+    const int cb = cloud_id(cl, i);
     const double nb = (double)(cloud_hi(cl, cb, n) - cloud_lo(cl, cb));
     const double bb = b[i];
     const double w = nb * pow(3.14159265358979323846 * eps2_dev[cb] * bb * bb, 0.5 * d);
@@ -357,7 +404,7 @@ size_t density_ws_bytes(int64_t n, int B)
 }
 
 vb_status density_run(Ctx* ctx, const vb_graph* g, const double* b, const double* eps2_dev, double d, double beta,
-                      double* psi, double* P, void* ws, size_t ws_bytes, Clouds cl)
+                      double* psi, double* P, void* ws, size_t ws_bytes, Clouds cl, int lpr)
 {
     if (!g || !g->row_ptr || !b || !eps2_dev || !psi || !P || !(d > 0)) return VB_ERR_ARG;
     if (cl.B < 1 || (cl.B > 1 && !cl.ptr)) return VB_ERR_ARG;
@@ -369,7 +416,11 @@ vb_status density_run(Ctx* ctx, const vb_graph* g, const double* b, const double
     mark(ctx, VB_STAGE_DENSITY, 0);
     recip_f32_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(b, g->n, 1.f, ib);
     density_const_kernel<<<(unsigned)((cl.B + 255) / 256), 256, 0, s>>>(eps2_dev, cl.B, cden);
-    density_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, g->n, ib, cden, cl, psi);
+    switch (lpr) {
+        case 8: density_kernel<8><<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, g->n, ib, cden, cl, psi); break;
+        case 16: density_kernel<16><<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, g->n, ib, cden, cl, psi); break;
+        default: density_kernel<32><<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, g->n, ib, cden, cl, psi); break;
+    }
     density_finish_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(b, eps2_dev, g->n, cl, d, beta, psi, P);
     mark(ctx, VB_STAGE_DENSITY, 1);
     ctx->launches += 4;
@@ -404,11 +455,11 @@ __global__ void __launch_bounds__(kRowThreads) centre_kernel(const int64_t* __re
                 so += x * (pi_ * iP[j]);
                 sd += x * (bi * ib[j]);
             }
+            so = warp_sum_f32(so);   // FP32 tree over the lanes; the FP64 pipe is narrow
+            sd = warp_sum_f32(sd);
             a_op += (double)so;
             a_den += (double)sd;
         }
-        a_op = warp_sum_f64(a_op);
-        a_den = warp_sum_f64(a_den);
         if (lane == 0) { sh[w][0] = a_op; sh[w][1] = a_den; }
         __syncthreads();
         if (threadIdx.x < 2) {
@@ -420,14 +471,16 @@ __global__ void __launch_bounds__(kRowThreads) centre_kernel(const int64_t* __re
     }
 }
 
-// One warp per cloud.
-__global__ void centre_finish_kernel(const double* __restrict__ partial, int nblk, int64_t n, Clouds cl, double* xi_c)
+// One block per cloud.
+__global__ void __launch_bounds__(SEG_T) centre_finish_kernel(const double* __restrict__ partial, int nblk, int64_t n,
+                                                              Clouds cl, double* xi_c)
 {
-    const int b = blockIdx.x, lane = threadIdx.x;
-    const double so = seg_total_lane(partial, 2, 0, cl, b, n, nblk, lane);
-    const double sd = seg_total_lane(partial, 2, 1, cl, b, n, nblk, lane);
-    // R9: the operator argument is ed2 / (4 P_i P_j); so holds sum ed2 / (P_i P_j)
-    if (lane == 0) xi_c[b] = floor(4.0 * log2(0.25 * so / sd) + 0.5) / 4.0;
+    __shared__ double part[SEG_PARTS * SEG_COLS];
+    __shared__ double tot[2];
+    const int b = blockIdx.x;
+    seg_totals(partial, 2, cl, b, n, nblk, part, tot);
+    // R9: the operator argument is ed2 / (4 P_i P_j); tot[0] holds sum ed2 / (P_i P_j)
+    if (threadIdx.x == 0) xi_c[b] = floor(4.0 * log2(0.25 * tot[0] / tot[1]) + 0.5) / 4.0;
 }
 
 size_t centre_ws_bytes(int64_t n, int B)
@@ -454,7 +507,7 @@ vb_status centre_run(Ctx* ctx, const vb_graph* g, const double* b, const double*
     recip_f32_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(b, g->n, 1.f, ib);
     recip_f32_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(P, g->n, 1.f, iP);
     centre_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, g->n, ib, iP, cl, partial);
-    centre_finish_kernel<<<(unsigned)cl.B, 32, 0, s>>>(partial, kRowBlocks, g->n, cl, xi_c_dev);
+    centre_finish_kernel<<<(unsigned)cl.B, SEG_T, 0, s>>>(partial, kRowBlocks, g->n, cl, xi_c_dev);
     mark(ctx, VB_STAGE_CENTRE, 1);
     ctx->launches += 4;
     return last_launch();
@@ -512,6 +565,7 @@ __global__ void op_const_kernel(const double* __restrict__ eps2, int B, C1* out)
     out[b] = r;
 }
 
+template <int LPR>
 __global__ void __launch_bounds__(kRowThreads) q_kernel(const int64_t* __restrict__ row_ptr,
                                                       const int32_t* __restrict__ col, const float* __restrict__ ed2,
                                                       int64_t n, const double* __restrict__ psi,
@@ -520,18 +574,20 @@ __global__ void __launch_bounds__(kRowThreads) q_kernel(const int64_t* __restric
                                                       double alpha, double* q, float* qa)
 {
     const float mbd = (float)(-beta * d), malpha = (float)(-alpha);
-    RowIter it;
-    for (int64_t i = it.i; i < n; i += it.step) {
-        const C1 c1 = cop[cloud_of(cl.ptr, cl.B, i)];
-        const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
-        const float ph = iPh[i], pl = iPl[i];
+    RowGroup<LPR> it;
+    for (int64_t b0 = it.base; b0 < n; b0 += it.step) {
+        const int64_t i = b0 + it.grp;
+        const bool ok = i < n;
+        const C1 c1 = cop[ok ? cloud_id(cl, i) : 0];
+        const int64_t rb = ok ? row_ptr[i] : 0, re = ok ? row_ptr[i + 1] : 0;
+        const float ph = ok ? iPh[i] : 0.f, pl = ok ? iPl[i] : 0.f;
         float s = 0.f;
-        for (int64_t e = rb + it.lane; e < re; e += 32) {
+        for (int64_t e = rb + it.sub; e < re; e += LPR) {
             const int32_t j = col[e];
             s += k_op(ed2[e], ph, pl, iPh[j], iPl[j], c1.h, c1.l);
         }
-        const double tot = warp_sum_f64((double)s);
-        if (it.lane == 0) {
+        const double tot = (double)RowGroup<LPR>::sum(s);
+        if (ok && it.sub == 0) {
             const float qi = pow_sfu((float)psi[i], mbd) * (float)tot;
             q[i] = (double)qi;
             qa[i] = pow_sfu(qi, malpha);
@@ -539,6 +595,7 @@ __global__ void __launch_bounds__(kRowThreads) q_kernel(const int64_t* __restric
     }
 }
 
+template <int LPR>
 __global__ void __launch_bounds__(kRowThreads) d_kernel(const int64_t* __restrict__ row_ptr,
                                                       const int32_t* __restrict__ col, const float* __restrict__ ed2,
                                                       int64_t n, const float* __restrict__ iPh,
@@ -546,18 +603,20 @@ __global__ void __launch_bounds__(kRowThreads) d_kernel(const int64_t* __restric
                                                       const double* __restrict__ P, const C1* __restrict__ cop,
                                                       Clouds cl, double* D, double* S, float* iS)
 {
-    RowIter it;
-    for (int64_t i = it.i; i < n; i += it.step) {
-        const C1 c1 = cop[cloud_of(cl.ptr, cl.B, i)];
-        const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
-        const float ph = iPh[i], pl = iPl[i], qi = qa[i];
+    RowGroup<LPR> it;
+    for (int64_t b0 = it.base; b0 < n; b0 += it.step) {
+        const int64_t i = b0 + it.grp;
+        const bool ok = i < n;
+        const C1 c1 = cop[ok ? cloud_id(cl, i) : 0];
+        const int64_t rb = ok ? row_ptr[i] : 0, re = ok ? row_ptr[i + 1] : 0;
+        const float ph = ok ? iPh[i] : 0.f, pl = ok ? iPl[i] : 0.f, qi = ok ? qa[i] : 0.f;
         float s = 0.f;
-        for (int64_t e = rb + it.lane; e < re; e += 32) {
+        for (int64_t e = rb + it.sub; e < re; e += LPR) {
             const int32_t j = col[e];
             s += k_op(ed2[e], ph, pl, iPh[j], iPl[j], c1.h, c1.l) * (qi * qa[j]);
         }
-        const double tot = warp_sum_f64((double)s);
-        if (it.lane == 0) {
+        const double tot = (double)RowGroup<LPR>::sum(s);
+        if (ok && it.sub == 0) {
             const double si = P[i] * sqrt(tot);
             D[i] = tot;
             S[i] = si;
@@ -566,6 +625,7 @@ __global__ void __launch_bounds__(kRowThreads) d_kernel(const int64_t* __restric
     }
 }
 
+template <int LPR>
 __global__ void __launch_bounds__(kRowThreads) lhat_kernel(const int64_t* __restrict__ row_ptr,
                                                          const int32_t* __restrict__ col,
                                                          const float* __restrict__ ed2, int64_t n,
@@ -574,23 +634,25 @@ __global__ void __launch_bounds__(kRowThreads) lhat_kernel(const int64_t* __rest
                                                          const double* __restrict__ S, const C1* __restrict__ cop,
                                                          const double* __restrict__ eps2_dev, Clouds cl, float* val)
 {
-    RowIter it;
-    for (int64_t i = it.i; i < n; i += it.step) {
-        const int cb = cloud_of(cl.ptr, cl.B, i);
+    RowGroup<LPR> it;
+    for (int64_t b0 = it.base; b0 < n; b0 += it.step) {
+        const int64_t i = b0 + it.grp;
+        const bool ok = i < n;
+        const int cb = ok ? cloud_id(cl, i) : 0;
         const C1 c1 = cop[cb];
         const float ie = c1.ie;
-        const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
-        const float ph = iPh[i], pl = iPl[i], qi = qa[i], si = iS[i];
+        const int64_t rb = ok ? row_ptr[i] : 0, re = ok ? row_ptr[i + 1] : 0;
+        const float ph = ok ? iPh[i] : 0.f, pl = ok ? iPl[i] : 0.f, qi = ok ? qa[i] : 0.f, si = ok ? iS[i] : 0.f;
         float off = 0.f;
         int64_t diag = -1;
-        for (int64_t e = rb + it.lane; e < re; e += 32) {
+        for (int64_t e = rb + it.sub; e < re; e += LPR) {
             const int32_t j = col[e];
             if (j == i) { diag = e; continue; }
             const float kt = k_op(ed2[e], ph, pl, iPh[j], iPl[j], c1.h, c1.l) * (qi * qa[j]);
             off += kt;
             val[e] = kt * (si * iS[j]) * ie;
         }
-        const double tot = warp_sum_f64((double)off);
+        const double tot = (double)RowGroup<LPR>::sum(off);
         if (diag >= 0) {
             const double sii = S[i];
             val[diag] = (float)(-tot / (eps2_dev[cb] * sii * sii));
@@ -608,7 +670,7 @@ size_t kernel_csr_ws_bytes(int64_t n, int B)
 
 vb_status kernel_csr_run(Ctx* ctx, const vb_graph* g, const double* psi, const double* P, const vb_op_params* op,
                          const double* eps2_op_dev, float* val, double* q, double* D, double* S, void* ws,
-                         size_t ws_bytes, Clouds cl)
+                         size_t ws_bytes, Clouds cl, int lpr)
 {
     if (!g || !g->row_ptr || !psi || !P || !op || !eps2_op_dev || !val || !q || !D || !S) return VB_ERR_ARG;
     if (!(op->d > 0) || cl.B < 1 || (cl.B > 1 && !cl.ptr)) return VB_ERR_ARG;
@@ -627,14 +689,18 @@ vb_status kernel_csr_run(Ctx* ctx, const vb_graph* g, const double* psi, const d
     mark(ctx, VB_STAGE_OPERATOR, 0);
     recip_pair_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, n, v.iPh, v.iPl);
     op_const_kernel<<<(unsigned)((cl.B + 255) / 256), 256, 0, s>>>(eps2_op_dev, cl.B, cop);
-    q_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, n, psi, v.iPh, v.iPl, cop, cl, op->beta,
-                                                op->d, alpha, q, v.qa);
-    d_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, n, v.iPh, v.iPl, v.qa, P, cop, cl, D, S,
-                                                v.iS);
+#define VB_ROWS(K, ...)                                                        \
+    switch (lpr) {                                                             \
+        case 8: K<8><<<kRowBlocks, kRowThreads, 0, s>>>(__VA_ARGS__); break;   \
+        case 16: K<16><<<kRowBlocks, kRowThreads, 0, s>>>(__VA_ARGS__); break; \
+        default: K<32><<<kRowBlocks, kRowThreads, 0, s>>>(__VA_ARGS__); break; \
+    }
+    VB_ROWS(q_kernel, g->row_ptr, g->col, g->ed2, n, psi, v.iPh, v.iPl, cop, cl, op->beta, op->d, alpha, q, v.qa)
+    VB_ROWS(d_kernel, g->row_ptr, g->col, g->ed2, n, v.iPh, v.iPl, v.qa, P, cop, cl, D, S, v.iS)
     mark(ctx, VB_STAGE_OPERATOR, 1);
     mark(ctx, VB_STAGE_LHAT, 0);
-    lhat_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, n, v.iPh, v.iPl, v.qa, v.iS, S, cop,
-                                                   eps2_op_dev, cl, val);
+    VB_ROWS(lhat_kernel, g->row_ptr, g->col, g->ed2, n, v.iPh, v.iPl, v.qa, v.iS, S, cop, eps2_op_dev, cl, val)
+#undef VB_ROWS
     mark(ctx, VB_STAGE_LHAT, 1);
     ctx->launches += 5;
     return last_launch();
@@ -651,7 +717,7 @@ __global__ void __launch_bounds__(kRowThreads) spmv_plain_kernel(const int64_t* 
         const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
         float s = 0.f;
         for (int64_t e = rb + it.lane; e < re; e += 32) s = fmaf(val[e], x[col[e]], s);
-        const double tot = warp_sum_f64((double)s);
+        const double tot = (double)warp_sum_f32(s);
         if (it.lane == 0) y[i] = (float)((double)alpha * tot + (beta != 0.f ? (double)beta * y[i] : 0.0));
     }
 }
@@ -685,7 +751,7 @@ __global__ void __launch_bounds__(kRowThreads) spmv_lap_kernel(const int64_t* __
             if (j == i) continue;
             s = fmaf(val[e] * sf[j], (float)(z[j] - zi), s);
         }
-        const double tot = warp_sum_f64((double)s);
+        const double tot = (double)warp_sum_f32(s);
         if (it.lane == 0) y[i] = (float)((double)alpha * tot + (beta != 0.f ? (double)beta * y[i] : 0.0));
     }
 }

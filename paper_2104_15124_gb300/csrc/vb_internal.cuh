@@ -101,6 +101,7 @@ __device__ __forceinline__ float pow_sfu(float x, float y) { return ex2_approx(y
 struct Clouds {
     const int64_t* ptr = nullptr;
     int32_t B = 1;
+    const int32_t* id = nullptr;   // optional: the cloud of every point (filled once per batched build)
 };
 // The cloud that holds point i: the largest b with ptr[b] <= i.
 __device__ __forceinline__ int cloud_of(const int64_t* __restrict__ ptr, int B, int64_t i)
@@ -113,6 +114,12 @@ __device__ __forceinline__ int cloud_of(const int64_t* __restrict__ ptr, int B, 
         else hi = mid;
     }
     return lo;
+}
+// The same through the per-point table when the build has one.
+__device__ __forceinline__ int cloud_id(const Clouds& c, int64_t i)
+{
+    if (c.B <= 1) return 0;
+    return c.id ? c.id[i] : cloud_of(c.ptr, c.B, i);
 }
 __device__ __forceinline__ int64_t cloud_lo(const Clouds& c, int b) { return c.B <= 1 ? 0 : c.ptr[b]; }
 __device__ __forceinline__ int64_t cloud_hi(const Clouds& c, int b, int64_t n) { return c.B <= 1 ? n : c.ptr[b + 1]; }
@@ -140,14 +147,14 @@ vb_status sweep_run(Ctx* ctx, const vb_graph* g, const double* rho, double scale
                     void* ws, size_t ws_bytes, Clouds cl = Clouds());
 size_t density_ws_bytes(int64_t n, int B = 1);
 vb_status density_run(Ctx* ctx, const vb_graph* g, const double* b, const double* eps2_dev, double d, double beta,
-                      double* psi, double* P, void* ws, size_t ws_bytes, Clouds cl = Clouds());
+                      double* psi, double* P, void* ws, size_t ws_bytes, Clouds cl = Clouds(), int lpr = 16);
 size_t centre_ws_bytes(int64_t n, int B = 1);
 vb_status centre_run(Ctx* ctx, const vb_graph* g, const double* b, const double* P, double* xi_c_dev, void* ws,
                      size_t ws_bytes, Clouds cl = Clouds());
 size_t kernel_csr_ws_bytes(int64_t n, int B = 1);
 vb_status kernel_csr_run(Ctx* ctx, const vb_graph* g, const double* psi, const double* P, const vb_op_params* op,
                          const double* eps2_op_dev, float* val, double* q, double* D, double* S, void* ws,
-                         size_t ws_bytes, Clouds cl = Clouds());
+                         size_t ws_bytes, Clouds cl = Clouds(), int lpr = 16);
 size_t spmv_ws_bytes(int64_t n);
 vb_status spmv_lap_launch(cudaStream_t s, const vb_graph* g, const float* val, const double* S, float alpha,
                           const float* x, float beta, float* y, double* z, float* sf);
