@@ -434,7 +434,10 @@ def main():
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s / a.steps},
             "gpu_launches": int(r0["launches"] * a.steps), "roofline": droof, "kernels": kernels,
             "knn": {"candidate_pairs_per_step": int(cand),
-                    "candidate_pairs_per_s": cand / (stage_ms["knn_tile"] / 1e3) if "knn_tile" in stage_ms else None},
+                    "candidate_pairs_per_s": cand / (stage_ms["knn_tile"] / 1e3) if "knn_tile" in stage_ms else None,
+                    "heap_levels_per_step": rep["knn_heap_levels"] // steps_prof,
+                    "insert_rounds_per_step": rep["knn_insert_rounds"] // steps_prof,
+                    "tiles_staged_per_step": rep["knn_tiles_staged"] // steps_prof},
             "clocks": clocks, "wall_s": r0["wall"]}
     if net is not None:
         line["learned_radius"] = train_note

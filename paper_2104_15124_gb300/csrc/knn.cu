@@ -350,6 +350,29 @@ __device__ __forceinline__ double canon_d2(const float* a, const float* b, int m
     return acc;
 }
 
+// The same sum for a query held in registers (q[0..MP)) and a 16-byte aligned
+// candidate row: the row is read with 16-byte loads, the arithmetic is canon_d2's.
+template <int MP>
+__device__ __forceinline__ double canon_d2_q(const float* q, const float* __restrict__ c, int m)
+{
+    float cv[MP];
+#pragma unroll
+    for (int r4 = 0; r4 < MP / 4; ++r4) {
+        const float4 v = *(const float4*)(c + 4 * r4);
+        cv[4 * r4] = v.x; cv[4 * r4 + 1] = v.y; cv[4 * r4 + 2] = v.z; cv[4 * r4 + 3] = v.w;
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int r = 0; r < MP; ++r) {
+        if (r < m) {
+            const double dl = __dsub_rn((double)q[r], (double)cv[r]);
+            const double sq = __dmul_rn(dl, dl);
+            acc = r == 0 ? sq : __dadd_rn(acc, sq);
+        }
+    }
+    return acc;
+}
+
 struct TileArgs {
     const float* xs;
     const float* tlo;
@@ -379,9 +402,10 @@ struct TileArgs {
     DevReport* rep;
 };
 
-constexpr int IB = 16;        // candidates per insertion batch
-constexpr int SCAP = 512;     // candidate tiles per sorted chunk
+constexpr int IB = 8;         // candidates per insertion batch
+constexpr int SCAP = 256;     // candidate tiles per sorted chunk
 constexpr int RUN = 8;        // longest run of FP32-indistinguishable neighbours ordered in registers
+constexpr int FB = 8;         // keys rescored per batch in the row finish
 
 // Sift key down from node i of the max-heap heap[0..size) (column t of a [.][COLS] array).
 template <int COLS = TILE>
@@ -450,11 +474,17 @@ __device__ bool finalize_row(const TileArgs& a, uint64_t* arr, int t, int size, 
     const uint64_t Hkey = arr[(size - 1) * COLS + t];
     const uint32_t oq = a.perm[pq];
     const float* qc = a.xs + pq * MP;
+    constexpr bool QR = MP <= 16;
+    float qv[QR ? MP : 1];
+    if constexpr (QR) {
+#pragma unroll
+        for (int r = 0; r < MP; ++r) qv[r] = qc[r];
+    }
     uint64_t rd[RUN];   // FP64 distance bits
     uint32_t ro[RUN];
     int rlen = 0, out = 0;
     float run_last = 0.f;
-    bool ok = true;
+    bool ok = true, done = false;
     double dk = 0.0;
     auto emit = [&]() {
 #pragma unroll
@@ -468,35 +498,59 @@ __device__ bool finalize_row(const TileArgs& a, uint64_t* arr, int t, int size, 
         }
         rlen = 0;
     };
-    for (int r = 0; r < size; ++r) {
-        const uint64_t key = arr[r * COLS + t];
-        if ((uint32_t)key == 0xffffffffu) break;   // empty slot or radius sentinel
-        const float df = __uint_as_float((uint32_t)(key >> 32));
-        // a new run starts once the distance clears the error band (tiny distances,
-        // where FP32 may have underflowed, all stay in one run)
-        const float gap = 2.02f * (e_lin * sqrtf(fmaxf(df, 0.f)) + e_const);
-        if (rlen > 0 && df > run_last * a.band + gap && df > 1e-30f) {
-            emit();
-            if (out >= a.k) break;
+    // keys are taken FB at a time: their index and coordinate loads are issued together
+    for (int r0 = 0; r0 < size && !done; r0 += FB) {
+        uint32_t cpb[FB], ojb[FB];
+        uint64_t djb[FB];
+        float dfb[FB];
+#pragma unroll
+        for (int u = 0; u < FB; ++u) {
+            const uint64_t key = r0 + u < size ? arr[(r0 + u) * COLS + t] : ~0ull;
+            cpb[u] = (uint32_t)key;
+            dfb[u] = __uint_as_float((uint32_t)(key >> 32));
         }
-        if (rlen == RUN) { ok = false; break; }
-        const uint32_t cp = (uint32_t)key;
-        const uint32_t oj = a.perm[cp];
-        const uint64_t dj = (uint64_t)__double_as_longlong(canon_d2(qc, a.xs + (int64_t)cp * MP, a.m));
-        // insert (dj, oj) into the run, kept sorted by (d2, index); non-negative doubles
-        // order like their bit patterns, so the comparisons stay on the integer pipe
 #pragma unroll
-        for (int u = 0; u < RUN; ++u)
-            if (u == rlen) { rd[u] = dj; ro[u] = oj; }
-#pragma unroll
-        for (int u = RUN - 1; u > 0; --u) {
-            if (u <= rlen && (rd[u] < rd[u - 1] || (rd[u] == rd[u - 1] && ro[u] < ro[u - 1]))) {
-                uint64_t td = rd[u]; rd[u] = rd[u - 1]; rd[u - 1] = td;
-                uint32_t to = ro[u]; ro[u] = ro[u - 1]; ro[u - 1] = to;
+        for (int u = 0; u < FB; ++u) {
+            ojb[u] = 0;
+            djb[u] = 0;
+            if (cpb[u] != 0xffffffffu) {
+                ojb[u] = a.perm[cpb[u]];
+                double d;
+                if constexpr (QR) d = canon_d2_q<MP>(qv, a.xs + (int64_t)cpb[u] * MP, a.m);
+                else d = canon_d2(qc, a.xs + (int64_t)cpb[u] * MP, a.m);
+                djb[u] = (uint64_t)__double_as_longlong(d);
             }
         }
-        ++rlen;
-        run_last = df;
+#pragma unroll
+        for (int u = 0; u < FB; ++u) {
+            if (done) break;
+            if (cpb[u] == 0xffffffffu) { done = true; break; }   // empty slot or radius sentinel
+            const float df = dfb[u];
+            // a new run starts once the distance clears the error band (tiny distances,
+            // where FP32 may have underflowed, all stay in one run)
+            const float gap = 2.02f * (e_lin * sqrtf(fmaxf(df, 0.f)) + e_const);
+            if (rlen > 0 && df > run_last * a.band + gap && df > 1e-30f) {
+                emit();
+                if (out >= a.k) { done = true; break; }
+            }
+            if (rlen == RUN) { ok = false; done = true; break; }
+            const uint64_t dj = djb[u];
+            const uint32_t oj = ojb[u];
+            // insert (dj, oj) into the run, kept sorted by (d2, index); non-negative doubles
+            // order like their bit patterns, so the comparisons stay on the integer pipe
+#pragma unroll
+            for (int v = 0; v < RUN; ++v)
+                if (v == rlen) { rd[v] = dj; ro[v] = oj; }
+#pragma unroll
+            for (int v = RUN - 1; v > 0; --v) {
+                if (v <= rlen && (rd[v] < rd[v - 1] || (rd[v] == rd[v - 1] && ro[v] < ro[v - 1]))) {
+                    uint64_t td = rd[v]; rd[v] = rd[v - 1]; rd[v - 1] = td;
+                    uint32_t to = ro[v]; ro[v] = ro[v - 1]; ro[v - 1] = to;
+                }
+            }
+            ++rlen;
+            run_last = df;
+        }
     }
     if (ok && out < a.k) emit();
     if (!ok) { atomicAdd(&a.rep->knn_rows_long_run, 1ull); return false; }
@@ -556,31 +610,54 @@ __device__ bool finalize_row_band(const TileArgs& a, uint64_t* arr, int t, int s
     int32_t* on = a.nbr + (int64_t)oq * a.k;
     double* od = a.nbr_d2 + (int64_t)oq * a.k;
     const int k = a.k;
+    constexpr bool QR = MP <= 16;
+    float qv[QR ? MP : 1];
+    if constexpr (QR) {
+#pragma unroll
+        for (int r = 0; r < MP; ++r) qv[r] = qc[r];
+    }
     int out = 0;
     double dk = INFINITY;
-    for (int r = 0; r < size; ++r) {
-        const uint64_t key = arr[r * COLS + t];
-        if ((uint32_t)key == 0xffffffffu) break;   // sentinel: nothing further was kept
-        if (out == k) {
-            const double df = (double)__uint_as_float((uint32_t)(key >> 32));
-            if ((df - bd.E(qn, dk, df)) * a.cert_factor > dk) break;
+    bool done = false;
+    // keys are taken FB at a time: their index and coordinate loads are issued together
+    for (int r0 = 0; r0 < size && !done; r0 += FB) {
+        uint32_t cpb[FB];
+        int32_t ojb[FB];
+        double djb[FB], dfb[FB];
+#pragma unroll
+        for (int u = 0; u < FB; ++u) {
+            const uint64_t key = r0 + u < size ? arr[(r0 + u) * COLS + t] : ~0ull;
+            cpb[u] = (uint32_t)key;
+            dfb[u] = (double)__uint_as_float((uint32_t)(key >> 32));
+            ojb[u] = 0;
+            djb[u] = 0.0;
+            if (cpb[u] != 0xffffffffu) {
+                ojb[u] = (int32_t)a.perm[cpb[u]];
+                if constexpr (QR) djb[u] = canon_d2_q<MP>(qv, a.xs + (int64_t)cpb[u] * MP, a.m);
+                else djb[u] = canon_d2(qc, a.xs + (int64_t)cpb[u] * MP, a.m);
+            }
         }
-        const uint32_t cp = (uint32_t)key;
-        const int32_t oj = (int32_t)a.perm[cp];
-        const double dj = canon_d2(qc, a.xs + (int64_t)cp * MP, a.m);
-        if (out == k && !(dj < dk || (dj == dk && oj < on[k - 1]))) continue;
-        int pos = out < k ? out++ : k - 1;
-        while (pos > 0) {
-            const double dp = od[pos - 1];
-            const int32_t ip = on[pos - 1];
-            if (dp < dj || (dp == dj && ip < oj)) break;
-            od[pos] = dp;
-            on[pos] = ip;
-            --pos;
+#pragma unroll
+        for (int u = 0; u < FB; ++u) {
+            if (done) break;
+            if (cpb[u] == 0xffffffffu) { done = true; break; }   // sentinel: nothing further was kept
+            if (out == k && (dfb[u] - bd.E(qn, dk, dfb[u])) * a.cert_factor > dk) { done = true; break; }
+            const double dj = djb[u];
+            const int32_t oj = ojb[u];
+            if (out == k && !(dj < dk || (dj == dk && oj < on[k - 1]))) continue;
+            int pos = out < k ? out++ : k - 1;
+            while (pos > 0) {
+                const double dp = od[pos - 1];
+                const int32_t ip = on[pos - 1];
+                if (dp < dj || (dp == dj && ip < oj)) break;
+                od[pos] = dp;
+                on[pos] = ip;
+                --pos;
+            }
+            od[pos] = dj;
+            on[pos] = oj;
+            if (out == k) dk = od[k - 1];
         }
-        od[pos] = dj;
-        on[pos] = oj;
-        if (out == k) dk = od[k - 1];
     }
     if (out < k) { atomicAdd(&a.rep->knn_rows_short, 1ull); return false; }
     if (ncl - 1 <= (int64_t)size || Hkey == ~0ull) return true;   // every candidate was kept
