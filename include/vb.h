@@ -229,8 +229,12 @@ typedef struct {
 
 size_t vb_graph_workspace(int64_t n, int32_t k);
 
-/* nbr / nbr_d2 as written by vb_knn().  row_ptr: n + 1 int64; col, ed2: cap
- * entries, cap >= n * (2k + 1); nnz_dev: one int64 receiving nnz. */
+/* nbr / nbr_d2 as written by vb_knn(): exact lists in (d2, index) order (the
+ * construction decides whether a pair is mutual by comparing it with the other
+ * point's k-th entry, which is only valid for such lists).  row_ptr: n + 1 int64;
+ * col, ed2: cap entries, cap >= n * (2k + 1); nnz_dev: one int64 receiving nnz.
+ * VB_ERR_UNSUPPORTED (reported) when a point lies in more than 8192 other lists
+ * beyond its own neighbours. */
 vb_status vb_graph_build(vb_ctx* ctx, int64_t n, int32_t k, const int32_t* nbr, const double* nbr_d2,
                          int64_t* row_ptr, int32_t* col, float* ed2, int64_t cap, int64_t* nnz_dev,
                          void* ws, size_t ws_bytes);

@@ -122,8 +122,10 @@ vb_status scan_counts(cudaStream_t s, const int32_t* counts, int64_t n, int64_t*
 // ------------------------------------------------------------------ a6
 // Row j of E is the disjoint union of {j}, its own kNN list N(j), and the reverse
 // entries R(j) = {i : j in N(i), i not in N(j)}.  Construction: every kNN list is
-// sorted by column (one warp per row); a reverse candidate (i -> j) is kept when a
-// binary search does not find i in N(j), so mutual pairs enter once; the counts
+// sorted by column (one warp per row); a reverse candidate (i -> j) is kept unless i is
+// in N(j), which for exact lists ordered by (d2, index) holds exactly when
+// (d2(i, j), i) <= (d2 and index of j's k-th neighbour), one 16-byte load instead of a
+// search, so mutual pairs enter once; the counts
 // 1 + k + |R(j)| give row_ptr directly (one scan); the kept reverse entries are
 // scattered into a side buffer; finally one warp per row sorts R(j) and places
 // every entry by its rank (own index + reverse entries below it + the diagonal),
@@ -131,7 +133,13 @@ vb_status scan_counts(cudaStream_t s, const int32_t* counts, int64_t n, int64_t*
 constexpr int RCAP = 256;           // warp path: reverse entries per row held in shared memory
 constexpr int OWN_CAP = 256;        // longest kNN list (k + margin <= 256)
 
+struct Kth {
+    double d2;         // j's k-th neighbour distance and index
+    int32_t idx, pad;
+};
+
 struct GraphWs {
+    Kth* kth;          // n
     int32_t* own_col;  // n k: kNN lists sorted by column
     float* own_d2;     // n k
     int32_t* rcnt;     // n reverse entries per row
@@ -147,6 +155,7 @@ struct GraphWs {
 static size_t graph_plan(Carve& c, int64_t n, int32_t k, GraphWs* w)
 {
     GraphWs t;
+    t.kth = c.take<Kth>(n);
     t.own_col = c.take<int32_t>(n * (int64_t)k);
     t.own_d2 = c.take<float>(n * (int64_t)k);
     t.rcnt = c.take<int32_t>(n);
@@ -217,7 +226,7 @@ constexpr int SORT_WARPS = 4;
 // rounding of its canonical FP64 distance (identical for (i, j) and (j, i)).
 __global__ void __launch_bounds__(SORT_WARPS * 32) own_sort_kernel(const int32_t* __restrict__ nbr,
                                                                     const double* __restrict__ nbr_d2, int64_t n,
-                                                                    int k, int32_t* own_col, float* own_d2)
+                                                                    int k, int32_t* own_col, float* own_d2, Kth* kth)
 {
     __shared__ uint64_t buf[SORT_WARPS][OWN_CAP];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -233,6 +242,13 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) own_sort_kernel(const int32_t
             own_col[i * k + e] = (int32_t)(buf[w][e] >> 32);
             own_d2[i * k + e] = __uint_as_float((uint32_t)buf[w][e]);
         }
+        if (lane == 0) {
+            Kth q;
+            q.d2 = nbr_d2[i * k + k - 1];
+            q.idx = nbr[i * k + k - 1];
+            q.pad = 0;
+            kth[i] = q;
+        }
         __syncwarp();
     }
 }
@@ -240,16 +256,16 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) own_sort_kernel(const int32_t
 // Reverse candidates (i -> j, j = nbr[i][r]) that are not mutual: counted (pass 0) or
 // scattered into row j's reverse slots (pass 1).
 __global__ void reverse_kernel(const int32_t* __restrict__ nbr, const double* __restrict__ nbr_d2, int64_t n, int k,
-                               const int32_t* __restrict__ own_col, int pass, int32_t* rcnt,
+                               const Kth* __restrict__ kth, int pass, int32_t* rcnt,
                                const int64_t* __restrict__ row_ptr, int32_t* fill, int32_t* rev_col, float* rev_d2)
 {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n * k) return;
     const int64_t i = e / k;
     const int32_t j = nbr[e];
-    const int32_t* oj = own_col + (int64_t)j * k;
-    const int pos = lower_bound_i32(oj, k, (int32_t)i);
-    if (pos < k && oj[pos] == (int32_t)i) return;   // mutual: already in row j's own list
+    const double d = nbr_d2[e];
+    const Kth q = kth[j];
+    if (d < q.d2 || (d == q.d2 && (int32_t)i <= q.idx)) return;   // mutual: already in row j's own list
     if (pass == 0) {
         atomicAdd(&rcnt[j], 1);
         return;
@@ -257,7 +273,7 @@ __global__ void reverse_kernel(const int32_t* __restrict__ nbr, const double* __
     const int slot = atomicAdd(&fill[j], 1);
     const int64_t off = row_ptr[j] - (int64_t)j * (1 + k) + slot;
     rev_col[off] = (int32_t)i;
-    rev_d2[off] = (float)nbr_d2[e];
+    rev_d2[off] = (float)d;
 }
 
 __global__ void row_len_kernel(const int32_t* __restrict__ rcnt, int64_t n, int k, int32_t* cnt, int32_t* fill)
@@ -373,12 +389,12 @@ vb_status graph_run(Ctx* ctx, int64_t n, int32_t k, const int32_t* nbr, const do
     mark(ctx, VB_STAGE_GRAPH, 0);
     zero_i32_kernel<<<gz, 256, 0, s>>>(w.rcnt, n);
     zero_i32_kernel<<<1, 32, 0, s>>>(w.nbig, 1);
-    own_sort_kernel<<<152 * 16, SORT_WARPS * 32, 0, s>>>(nbr, nbr_d2, n, k, w.own_col, w.own_d2);
-    reverse_kernel<<<ge, 256, 0, s>>>(nbr, nbr_d2, n, k, w.own_col, 0, w.rcnt, nullptr, nullptr, nullptr, nullptr);
+    own_sort_kernel<<<152 * 16, SORT_WARPS * 32, 0, s>>>(nbr, nbr_d2, n, k, w.own_col, w.own_d2, w.kth);
+    reverse_kernel<<<ge, 256, 0, s>>>(nbr, nbr_d2, n, k, w.kth, 0, w.rcnt, nullptr, nullptr, nullptr, nullptr);
     row_len_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.rcnt, n, k, w.cnt, w.fill);
     vb_status st = scan_counts(s, w.cnt, n, row_ptr, w.scan);
     if (st != VB_OK) return st;
-    reverse_kernel<<<ge, 256, 0, s>>>(nbr, nbr_d2, n, k, w.own_col, 1, w.rcnt, row_ptr, w.fill, w.rev_col, w.rev_d2);
+    reverse_kernel<<<ge, 256, 0, s>>>(nbr, nbr_d2, n, k, w.kth, 1, w.rcnt, row_ptr, w.fill, w.rev_col, w.rev_d2);
     merge_kernel<<<152 * 16, SORT_WARPS * 32, 0, s>>>(row_ptr, n, k, w.own_col, w.own_d2, w.rev_col, w.rev_d2, col, ed2,
                                                       cap, w.big, w.nbig, nnz_dev, ctx->rep);
     static bool big_attr[16] = {};
