@@ -132,6 +132,14 @@ vb_status vb_profile_read(vb_ctx* ctx, float* ms, int64_t* launches);
                                tiles are needed; tiles with a row that finds fewer than k points inside its
                                radius, or fails the certificate, are redone by the exact search, so the output
                                stays exact */
+/* Kernel of the 16-bit search.  STAGED: one CTA converts and stages one candidate
+ * tile per step, then MMA, then selection.  PIPELINED: every 64-point tile is
+ * converted once into its MMA operand image; a producer warp stages the images by
+ * bulk copies (TMA) into a shared-memory ring, an MMA warp feeds four tensor-memory
+ * accumulator buffers, and four warps select, all overlapped. */
+#define VB_TC_AUTO      0
+#define VB_TC_STAGED    1
+#define VB_TC_PIPELINED 2
 
 typedef struct vb_mlp vb_mlp;
 
@@ -149,13 +157,17 @@ typedef struct {
                                       cloud, e.g. ln(n_train / n_b) / d (NULL = none) */
     int32_t seed_tiles;      /* exact FP32 search: neighbouring tiles on each side of a query tile that are
                                 searched before any pruning (0 = enough to fill every heap) */
+    int32_t tc_variant;      /* 16-bit tiles: VB_TC_AUTO (pipelined when its shared memory fits, else
+                                staged), VB_TC_STAGED or VB_TC_PIPELINED (VB_ERR_UNSUPPORTED when
+                                k + margin and m leave no room for two ring slots) */
 } vb_knn_params;
 
 /* Launch-shape autotuner (a16).  Times vb_knn on the caller's input for every
  * candidate shape -- heap depth k + margin with margin in {4, 8, 16, 32} and
- * seed_tiles in {1, 2, 3} for the FP32 search, the margin alone for 16-bit tiles --
+ * seed_tiles in {1, 2, 3} for the FP32 search, the margin and the kernel
+ * (tc_variant staged or pipelined) for 16-bit tiles --
  * with CUDA events on the context's stream (synchronising), and writes the
- * fastest into *best (a copy of *p with margin and seed_tiles set) and its time
+ * fastest into *best (a copy of *p with margin, seed_tiles and tc_variant set) and its time
  * into *best_ms.  Results are cached for the process by (m, k, precision, prune,
  * floor(log2 n)); a cached key returns at once without running anything (then
  * *best_ms = 0).  nbr / nbr_d2 / ws as for vb_knn, sized for k; every result is

@@ -51,7 +51,18 @@ struct KnnWs {
     float* r2;            // n (radius search: squared radius bound per sorted point)
     int* fail_flag;       // 2 ntiles: flags of radius passes 1 and 2
     int* fail_list;       // 2 ntiles: tiles left by passes 1 and 2
+    // pipelined 16-bit search only (precision != FP32)
+    unsigned char* blk;   // npad / 64 tile blocks: 16-bit operand image + 64 FP32 norms
+    uint32_t* lbw;        // TCP_MAX_CTAS * ntiles: box bounds of the candidate tiles (per CTA)
+    uint64_t* tlist;      // TCP_MAX_CTAS * ntiles: candidate tiles ordered by bound (per CTA)
+    int* crange;          // 256 ordered ints: per-coordinate min and max of the cloud
 };
+
+constexpr int TCP_MAX_CTAS = 304;   // persistent grid of the pipelined search (2 per SM on 152 SMs)
+static int pad_k16(int m) { return (m + 15) / 16 * 16; }
+// bytes of one 64-point tile block of the pipelined search: operand image, then norms
+__host__ __device__ inline size_t tcp_img_bytes(int kp) { return (size_t)64 * kp * 2; }
+__host__ __device__ inline size_t tcp_blk_bytes(int kp) { return tcp_img_bytes(kp) + 64 * sizeof(float); }
 
 static int pad_dim(int m)
 {
@@ -62,7 +73,7 @@ static int pad_dim(int m)
 static int morton_dims(int m) { return m <= 4 ? m : 3; }
 static int morton_bits(int md) { return md == 1 ? 30 : md == 2 ? 15 : md == 3 ? 10 : 8; }
 
-size_t knn_plan(Carve& c, int64_t n, int32_t m, const vb_knn_params*, KnnWs* w)
+size_t knn_plan(Carve& c, int64_t n, int32_t m, const vb_knn_params* p, KnnWs* w)
 {
     const int mp = pad_dim(m);
     const int64_t ntiles = (n + TILE - 1) / TILE;
@@ -84,6 +95,16 @@ size_t knn_plan(Carve& c, int64_t n, int32_t m, const vb_knn_params*, KnnWs* w)
     t.r2 = c.take<float>(npad);
     t.fail_flag = c.take<int>(2 * ntiles);
     t.fail_list = c.take<int>(2 * ntiles);
+    t.blk = nullptr;
+    t.lbw = nullptr;
+    t.tlist = nullptr;
+    t.crange = nullptr;
+    if (p && p->precision != VB_PREC_FP32) {
+        t.blk = c.take<unsigned char>((size_t)(npad / TILE) * tcp_blk_bytes(pad_k16(m)));
+        t.lbw = c.take<uint32_t>((size_t)TCP_MAX_CTAS * ntiles);
+        t.tlist = c.take<uint64_t>((size_t)TCP_MAX_CTAS * ntiles);
+        t.crange = c.take<int>(256);
+    }
     if (w) *w = t;
     return c.off;
 }
@@ -400,6 +421,12 @@ struct TileArgs {
     int* fail_count;
     Clouds cl;              // batched build: queries only take candidates from their own cloud
     DevReport* rep;
+    // pipelined 16-bit search
+    const unsigned char* blk;   // tile blocks (operand image + norms), tcp_blk_bytes(kp) each
+    int kp;                     // K: m padded to 16
+    int stages;                 // ring slots of staged tile blocks
+    uint32_t* lbw;              // per CTA scratch: ntiles box bounds
+    uint64_t* tlist;            // per CTA scratch: ntiles (bound, tile) keys in bound order
 };
 
 constexpr int IB = 8;         // candidates per insertion batch
@@ -1281,6 +1308,448 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
     if (warp == 0) tc::tmem_dealloc(tb, TILE);
 }
 
+// ------------------------------------------------------------------ pipelined 16-bit distance tiles (a3, a15)
+// The warp-specialised form of the 16-bit search, for inputs wide enough that the
+// contraction is real work.  Each 64-point tile is converted once per call into a
+// tile block: its 16-bit operand (coordinates minus the cloud's mid-range centre,
+// K = m padded to 16, clamped like the staged kernel's) laid out exactly as the
+// no-swizzle K-major core-matrix image the MMA reads, followed by the tile's FP32
+// norms |x~|^2.  A query tile (128 points: two 64-point tiles, one TMEM lane each)
+// then runs as a pipeline of three roles:
+//   warp 4 (producer)  walks the candidate tiles in order of their box lower bound and
+//                      stages each block with one bulk copy (TMA) into a ring of S slots;
+//   warp 5 (MMA)       issues K/16 tcgen05.mma (M = 128, N = 64, FP32 accumulation) per
+//                      tile into one of four 64-column tensor-memory buffers and copies the
+//                      tile's norms beside it;
+//   warps 0-3          one query per thread: read the 64 dot products, form
+//                      |q~|^2 + |x~|^2 - 2 q~.x~ and fold them into the query's max-heap.
+// The producer skips tiles whose bound exceeds the largest heap bound of the query tile
+// (published by the epilogue warps after every tile; a stale value is only larger) and
+// stops at the first counting-sort bin beyond it: the list is ordered by the top bits of
+// the bound, a monotone key, so the stop is exact.  Rows finish as in the staged kernel
+// (finalize_row_band); a row that is not certified sends its tiles to the FP32 search.
+// Every wait is bounded in time (an expired wait records VB_ERR_TIMEOUT and stops the CTA).
+constexpr int TCP_BUF = 4;         // tensor-memory accumulator buffers of 64 columns
+constexpr int TCP_META = 16;       // tile ids in flight (>= slots + buffers + 1)
+constexpr int TCP_THREADS = 192;   // warps 0-3 epilogue, 4 producer, 5 MMA
+constexpr int TCP_BINS = 1024;     // counting-sort bins: FP32 bits of the bound >> 21
+
+__global__ void tcp_range_init_kernel(int* crange)
+{
+    const int r = threadIdx.x;
+    if (r < 128) {
+        crange[r] = 0x7fffffff;
+        crange[128 + r] = (int)0x80000000;
+    }
+}
+
+// Per-coordinate min and max over the sorted coordinates of the n real points.
+__global__ void tcp_range_kernel(const float* __restrict__ xs, int64_t n, int m, int mp, int* crange)
+{
+    const int r = threadIdx.x;
+    if (r >= m) return;
+    int lo = 0x7fffffff, hi = (int)0x80000000;
+    const int64_t p0 = (int64_t)blockIdx.x * 64, p1 = min(n, p0 + 64);
+    for (int64_t p = p0; p < p1; ++p) {
+        const int v = f2ord(xs[p * mp + r]);
+        lo = min(lo, v);
+        hi = max(hi, v);
+    }
+    atomicMin(&crange[r], lo);
+    atomicMax(&crange[128 + r], hi);
+}
+
+// Tile blocks: 16-bit (x - c) of every padded sorted point in the core-matrix image of
+// its tile, and |x~|^2 summed in FP32 from the rounded values (padding rows are zero).
+template <bool F16>
+__global__ void tcp_block_kernel(const float* __restrict__ xs, int64_t n, int64_t npad, int m, int mp, int kp,
+                                 const int* __restrict__ crange, unsigned char* blk)
+{
+    using HT = Half16<F16>;
+    using half_t = typename HT::T;
+    __shared__ float cen[128];
+    for (int r = threadIdx.x; r < 128; r += blockDim.x)
+        cen[r] = r < m ? 0.5f * (ord2f(crange[r]) + ord2f(crange[128 + r])) : 0.f;
+    __syncthreads();
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= npad) return;
+    unsigned char* tb = blk + (p / TILE) * tcp_blk_bytes(kp);
+    const int row = (int)(p % TILE);
+    float sq = 0.f;
+    for (int j = 0; j < kp / 8; ++j) {
+        __align__(16) half_t v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int r = 8 * j + e;
+            const float x = r < m && p < n ? fminf(fmaxf(xs[p * mp + r] - cen[r], -HT::clampv), HT::clampv) : 0.f;
+            v[e] = HT::from(x);
+            const float xb = HT::to(v[e]);
+            sq = fmaf(xb, xb, sq);
+        }
+        *(uint4*)(tb + tc::operand_offset(row, 8 * j, kp)) = *(const uint4*)v;
+    }
+    ((float*)(tb + tcp_img_bytes(kp)))[row] = sq;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of an mbarrier, giving up when another role has stopped the
+// CTA or after about four seconds (then the CTA is stopped and VB_ERR_TIMEOUT recorded).
+__device__ __noinline__ bool tcp_wait(uint64_t* bar, uint32_t parity, volatile int* stop, DevReport* rep)
+{
+    const uint32_t ad = tc::smem_addr(bar);
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(ad), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 31) == 0) {
+            if (*stop) return false;
+            const uint64_t now = global_ns();
+            if (it == 0) t0 = now;
+            else if (now - t0 > 4000000000ull) {
+                *stop = 1;
+                report_error(rep, VB_ERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+template <int MP, bool F16>
+__global__ void __launch_bounds__(TCP_THREADS, 1) knn_tcp_kernel(TileArgs a)
+{
+    using HT = Half16<F16>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int KP = a.kp, S = a.stages, L = a.cap;
+    const uint32_t IMG = (uint32_t)tcp_img_bytes(KP), BLK = (uint32_t)tcp_blk_bytes(KP);
+    unsigned char* sa = smem;                                // query operand: two tile images
+    unsigned char* slots = smem + 2 * IMG;                   // S staged tile blocks
+    uint64_t* heap = (uint64_t*)(slots + (size_t)S * BLK);   // [L][T2] max-heaps
+    uint32_t* hist = (uint32_t*)heap;                        // [2][TCP_BINS] while the tile list is built
+    __shared__ __align__(8) uint64_t full[4], empty[4], tfull[TCP_BUF], tempty[TCP_BUF], qbar, dbar;
+    __shared__ __align__(16) float txn[TCP_BUF][TILE];
+    __shared__ volatile int meta[TCP_META];
+    __shared__ volatile uint32_t sred[4];
+    __shared__ uint64_t pkeys[32];
+    __shared__ volatile int s_stop;
+    __shared__ int s_tile, s_cnt, s_fail;
+    __shared__ int64_t s_ct[2];
+    __shared__ float sqlo[MP], sqhi[MP];
+    __shared__ uint32_t tmem_base;
+
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t nt = a.ntiles;
+    const int64_t nst = (nt + 1) / 2;
+    Band bd;
+    bd.u = HT::unit;
+    bd.dabs = HT::dabs;
+    bd.rho_k = 2.f * (float)(KP + 4) * 5.9604645e-8f;
+    unsigned long long evaluated = 0;
+    unsigned levels = 0, staged = 0;
+    uint32_t pseq = 0, mseq = 0, eseq = 0, qcount = 0;   // role-local sequence numbers
+    if (warp == 5) tc::tmem_alloc(&tmem_base, TCP_BUF * TILE);
+    if (t == 0) {
+        for (int i = 0; i < S; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < TCP_BUF; ++i) {
+            tc::mbar_init(&tfull[i], 2);    // the MMA completion and the MMA warp's own arrival
+            tc::mbar_init(&tempty[i], 4);   // one arrival per epilogue warp
+        }
+        tc::mbar_init(&qbar, 1);
+        tc::mbar_init(&dbar, 1);
+        s_stop = 0;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tb = tmem_base;
+    constexpr uint32_t idesc = tc::idesc_f16(T2, TILE, F16);
+    uint32_t* lbw = a.lbw + (int64_t)blockIdx.x * nt;
+    uint64_t* tl = a.tlist + (int64_t)blockIdx.x * nt;
+
+    for (;;) {
+        if (t == 0) {
+            s_tile = atomicAdd(a.work, 1);
+            s_fail = 0;
+        }
+        __syncthreads();
+        const int64_t qs = s_tile;
+        if (qs >= nst || s_stop) break;
+        const bool epi = warp < 4;
+        const int64_t p = qs * T2 + (epi ? t : 0);
+        const bool valid = epi && p < a.n;
+        int64_t qlo = 0, qhi = a.n;   // the query's cloud
+        if (a.cl.B > 1 && valid) {
+            const int b = cloud_id(a.cl, p);
+            qlo = a.cl.ptr[b];
+            qhi = a.cl.ptr[b + 1];
+        }
+        if (t == 0) {   // candidate tiles that hold points of this query tile's clouds
+            s_ct[0] = 0;
+            s_ct[1] = nt;
+            if (a.cl.B > 1) {
+                const int64_t p0 = qs * T2, pl = min(a.n, p0 + T2) - 1;
+                s_ct[0] = a.cl.ptr[cloud_of(a.cl.ptr, a.cl.B, p0)] / TILE;
+                s_ct[1] = (a.cl.ptr[cloud_of(a.cl.ptr, a.cl.B, pl) + 1] + TILE - 1) / TILE;
+            }
+        }
+        for (int r = t; r < MP; r += TCP_THREADS) {   // union box of tiles 2 qs and 2 qs + 1
+            float lo = a.tlo[(2 * qs) * MP + r], hi = a.thi[(2 * qs) * MP + r];
+            if (2 * qs + 1 < nt) {
+                lo = fminf(lo, a.tlo[(2 * qs + 1) * MP + r]);
+                hi = fmaxf(hi, a.thi[(2 * qs + 1) * MP + r]);
+            }
+            sqlo[r] = lo;
+            sqhi[r] = hi;
+        }
+        for (int i = t; i < 2 * TCP_BINS; i += TCP_THREADS) hist[i] = 0;
+        // query norm (from the tile block) and the heap's starting key
+        float sqa = 0.f;
+        if (valid) sqa = ((const float*)(a.blk + (p / TILE) * (size_t)BLK + IMG))[p % TILE];
+        const float qn = sqrtf(sqa);
+        const float R2 = a.r2 && valid ? __fmul_ru(a.r2[p], a.r2_scale) : INFINITY;
+        const uint64_t sentinel = a.r2 ? (((uint64_t)__float_as_uint(R2) << 32) | 0xffffffffu) : ~0ull;
+        if (epi) {
+            const uint32_t wr = __reduce_max_sync(0xffffffffu, valid ? (uint32_t)(sentinel >> 32) : 0u);
+            if (lane == 0) sred[warp] = wr;
+        }
+        __syncthreads();
+        const int64_t ct_lo = s_ct[0], ct_hi = s_ct[1];
+        // candidate tiles by box lower bound: bounds, bin counts, scan, scatter
+        for (int64_t ct = ct_lo + t; ct < ct_hi; ct += TCP_THREADS) {
+            float acc = 0.f;
+            for (int r = 0; r < a.m; ++r) {
+                const float g = fmaxf(fmaxf(a.tlo[ct * MP + r] - sqhi[r], sqlo[r] - a.thi[ct * MP + r]), 0.f);
+                acc = fmaf(g, g, acc);
+            }
+            const uint32_t lbb = __float_as_uint(__fmul_rd(acc, a.lb_factor));
+            lbw[ct - ct_lo] = lbb;
+            atomicAdd(&hist[min(lbb >> 21, (uint32_t)TCP_BINS - 1)], 1u);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            constexpr int PER = TCP_BINS / 32;
+            uint32_t sum = 0;
+            for (int i = 0; i < PER; ++i) sum += hist[lane * PER + i];
+            uint32_t inc = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += v;
+            }
+            uint32_t run = inc - sum;
+            for (int i = 0; i < PER; ++i) {
+                const uint32_t c = hist[lane * PER + i];
+                hist[TCP_BINS + lane * PER + i] = run;
+                run += c;
+            }
+            if (lane == 31) s_cnt = (int)inc;
+        }
+        __syncthreads();
+        for (int64_t ct = ct_lo + t; ct < ct_hi; ct += TCP_THREADS) {
+            const uint32_t lbb = lbw[ct - ct_lo];
+            const uint32_t pos = atomicAdd(&hist[TCP_BINS + min(lbb >> 21, (uint32_t)TCP_BINS - 1)], 1u);
+            tl[pos] = ((uint64_t)lbb << 32) | (uint32_t)ct;
+        }
+        __syncthreads();   // the list is complete and the bins are free for the heaps
+
+        if (warp == 4) {
+            // ---------------- producer: query operand, then the candidate tiles in bound order
+            // (the list is read 32 keys at a time by the whole warp; lane 0 decides and issues)
+            if (lane == 0) {
+                tc::mbar_arrive_tx(&qbar, 2 * IMG);
+                tc::bulk_g2s(sa, a.blk + (2 * qs) * (size_t)BLK, IMG, &qbar);
+                tc::bulk_g2s(sa + IMG, a.blk + (2 * qs + 1) * (size_t)BLK, IMG, &qbar);
+            }
+            const int cnt = s_cnt;
+            int go = 1;
+            for (int base = 0; go; base += 32) {
+                pkeys[lane] = base + lane < cnt ? tl[base + lane] : ~0ull;
+                __syncwarp();
+                if (lane == 0) {
+                    for (int j = 0; j < 32 && go; ++j) {
+                        const uint64_t key = pkeys[j];
+                        int ct = -1;   // -1: end of this query tile
+                        if (key != ~0ull) {
+                            const uint32_t lbb = (uint32_t)(key >> 32);
+                            const uint32_t thr = max(max(sred[0], sred[1]), max(sred[2], sred[3]));
+                            if (lbb > thr && (lbb >> 21) <= (thr >> 21)) continue;   // skip this tile only
+                            if (lbb <= thr) ct = (int)(uint32_t)key;                 // else: this bin and beyond
+                        }
+                        const int sl = (int)(pseq % (uint32_t)S);
+                        if (!tcp_wait(&empty[sl], ((pseq / (uint32_t)S) & 1u) ^ 1u, &s_stop, a.rep)) {
+                            go = 0;
+                            break;
+                        }
+                        meta[pseq % TCP_META] = ct;
+                        if (ct >= 0) {
+                            tc::mbar_arrive_tx(&full[sl], BLK);
+                            tc::bulk_g2s(slots + (size_t)sl * BLK, a.blk + (size_t)ct * BLK, BLK, &full[sl]);
+                            ++staged;
+                        } else {
+                            tc::mbar_arrive(&full[sl]);
+                            go = 0;
+                        }
+                        ++pseq;
+                    }
+                }
+                go = __shfl_sync(0xffffffffu, go, 0);
+                __syncwarp();
+            }
+        } else if (warp == 5) {
+            // ---------------- MMA issue
+            if (lane == 0) {
+                bool go = tcp_wait(&qbar, qcount & 1u, &s_stop, a.rep);
+                while (go) {
+                    const int sl = (int)(mseq % (uint32_t)S), b = (int)(mseq % TCP_BUF);
+                    if (!tcp_wait(&full[sl], (mseq / (uint32_t)S) & 1u, &s_stop, a.rep)) break;
+                    const int ct = meta[mseq % TCP_META];
+                    if (!tcp_wait(&tempty[b], ((mseq / TCP_BUF) & 1u) ^ 1u, &s_stop, a.rep)) break;
+                    if (ct >= 0) {
+                        const float4* sx = (const float4*)(slots + (size_t)sl * BLK + IMG);
+                        float4* dx = (float4*)txn[b];
+#pragma unroll
+                        for (int i = 0; i < TILE / 4; ++i) dx[i] = sx[i];
+                        tc::fence_after_sync();
+                        const uint32_t sbo = (uint32_t)(KP / 8) * 128;
+                        const uint32_t a0 = tc::smem_addr(sa), b0 = tc::smem_addr(slots + (size_t)sl * BLK);
+                        for (int ks = 0; ks < KP / 16; ++ks)
+                            tc::mma_bf16(tb + (uint32_t)(b * TILE), tc::smem_desc(a0 + ks * 256, 128, sbo),
+                                         tc::smem_desc(b0 + ks * 256, 128, sbo), idesc, ks > 0 ? 1u : 0u);
+                        tc::mma_commit(&empty[sl]);
+                        tc::mma_commit(&tfull[b]);
+                    } else {
+                        tc::mbar_arrive(&empty[sl]);
+                        tc::mbar_arrive(&tfull[b]);
+                    }
+                    tc::mbar_arrive(&tfull[b]);   // orders the norms and the tile id before the epilogue
+                    ++mseq;
+                    if (ct < 0) break;
+                }
+            }
+            __syncwarp();
+        } else {
+            // ---------------- epilogue: one query per thread
+            for (int sl = 0; sl < L; ++sl) heap[sl * T2 + t] = sentinel;
+            uint64_t heapmax = sentinel;
+            uint32_t hb = (uint32_t)(heapmax >> 32);
+            float hmf = hb == 0xffffffffu ? INFINITY : __uint_as_float(hb);
+            const uint32_t lane_addr = tb + ((uint32_t)(warp * 32) << 16);
+            for (;;) {
+                const int b = (int)(eseq % TCP_BUF);
+                int ok = 1;
+                if (lane == 0) ok = tcp_wait(&tfull[b], (eseq / TCP_BUF) & 1u, &s_stop, a.rep) ? 1 : 0;
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) break;
+                __syncwarp();
+                const int ct = meta[eseq % TCP_META];
+                tc::fence_after_sync();
+                float v[TILE];
+                if (ct >= 0) {
+                    tc::tmem_ld32(lane_addr + (uint32_t)(b * TILE), v);
+                    tc::tmem_ld32(lane_addr + (uint32_t)(b * TILE + 32), v + 32);
+                    const float4* x4 = (const float4*)txn[b];
+#pragma unroll
+                    for (int i4 = 0; i4 < TILE / 4; ++i4) {
+                        const float4 q4 = x4[i4];
+                        v[4 * i4 + 0] = fmaf(-2.f, v[4 * i4 + 0], sqa + q4.x);
+                        v[4 * i4 + 1] = fmaf(-2.f, v[4 * i4 + 1], sqa + q4.y);
+                        v[4 * i4 + 2] = fmaf(-2.f, v[4 * i4 + 2], sqa + q4.z);
+                        v[4 * i4 + 3] = fmaf(-2.f, v[4 * i4 + 3], sqa + q4.w);
+                    }
+                }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&tempty[b]);
+                ++eseq;
+                if (ct < 0) break;
+                if (valid) {
+                    evaluated += TILE;
+#pragma unroll
+                    for (int ch = 0; ch < TILE / 32; ++ch) {
+                        uint32_t msk = 0;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) msk |= (v[ch * 32 + i] <= hmf ? 1u : 0u) << i;
+                        while (msk) {   // the full key test and the heap update
+                            const int i = __ffs(msk) - 1;
+                            msk &= msk - 1u;
+                            float d = 0.f;
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) d = j == i ? v[ch * 32 + j] : d;
+                            const int64_t cp = (int64_t)ct * TILE + ch * 32 + i;
+                            const uint64_t key = ((uint64_t)__float_as_uint(fmaxf(d, 0.f)) << 32) | (uint32_t)cp;
+                            if (key < heapmax && cp != p && cp >= qlo && cp < qhi) {
+                                sift_down<T2>(heap, t, 0, L, key, levels);
+                                heapmax = heap[t];
+                            }
+                        }
+                        hb = (uint32_t)(heapmax >> 32);
+                        hmf = hb == 0xffffffffu ? INFINITY : __uint_as_float(hb);
+                    }
+                }
+                const uint32_t wmax = __reduce_max_sync(0xffffffffu, valid ? (uint32_t)(heapmax >> 32) : 0u);
+                if (lane == 0) sred[warp] = wmax;
+            }
+            bool ok = true;
+            if (valid) {
+                ok = !s_stop && !(F16 && qn > 0.25f * kHalfClamp);
+                if (ok) ok = finalize_row_band<MP, T2>(a, heap, t, L, p, qhi - qlo, levels, bd, qn);
+                if (!ok) s_fail = 1;
+            }
+        }
+        ++qcount;
+        __syncthreads();
+        if (s_stop) break;
+        if (t == 0 && s_fail) {
+            for (int h = 0; h < 2; ++h) {
+                const int64_t qt = 2 * qs + h;
+                if (qt < nt && atomicExch(&a.fail_flag[qt], 1) == 0) {
+                    a.fail_list[atomicAdd(a.fail_count, 1)] = (int)qt;
+                    atomicAdd(&a.rep->knn_retry_tiles, 1ull);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // every MMA of this CTA has completed, and no bulk copy is still landing, before exit
+    if (warp == 5 && lane == 0) {
+        tc::mma_commit(&dbar);
+        tc::mbar_wait(&dbar, 0, 1u << 22);
+    }
+    if (warp == 4 && lane == 0 && s_stop) {
+        for (uint32_t q = pseq > (uint32_t)S ? pseq - (uint32_t)S : 0u; q < pseq; ++q)
+            tc::mbar_wait(&full[q % (uint32_t)S], (q / (uint32_t)S) & 1u, 1u << 22);
+        tc::mbar_wait(&qbar, (qcount - 1u) & 1u, 1u << 22);
+    }
+    unsigned long long ev = evaluated, lv = levels, st = staged;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ev += __shfl_xor_sync(0xffffffffu, ev, o);
+        lv += __shfl_xor_sync(0xffffffffu, lv, o);
+        st += __shfl_xor_sync(0xffffffffu, st, o);
+    }
+    if (lane == 0) {
+        if (ev) atomicAdd(&a.rep->knn_candidates, ev);
+        if (lv) atomicAdd(&a.rep->knn_heap_levels, lv);
+        if (st) atomicAdd(&a.rep->knn_tiles_staged, st);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 5) tc::tmem_dealloc(tb, TCP_BUF * TILE);
+}
+
 // R2[pos] = (inflate * radius[perm[pos]])^2 for the sorted points (caller-provided radii).
 __global__ void radius_gather_kernel(const float* __restrict__ radius, const uint32_t* __restrict__ perm, int64_t n,
                                      float inflate, float* r2)
@@ -1432,6 +1901,48 @@ static vb_status launch_tc(TileArgs a, cudaStream_t s)
     return last_launch();
 }
 
+// Pipelined 16-bit search: ring slots as many (2..4) as shared memory allows next to the
+// query operand and the heaps; VB_ERR_UNSUPPORTED when not even two fit.
+template <int MP, bool F16>
+static vb_status launch_tcp(TileArgs a, cudaStream_t s)
+{
+    const size_t img = tcp_img_bytes(a.kp), blk = tcp_blk_bytes(a.kp);
+    const size_t heap = std::max((size_t)a.cap * T2 * sizeof(uint64_t), (size_t)2 * TCP_BINS * sizeof(uint32_t));
+    static bool attr_set[16] = {};
+    static int sms[16] = {}, smem_sm[16] = {}, static_smem[16] = {}, optin[16] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int dv = dev & 15;
+    if (!attr_set[dv]) {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, knn_tcp_kernel<MP, F16>) != cudaSuccess) return VB_ERR_CUDA;
+        static_smem[dv] = (int)fa.sharedSizeBytes;
+        if (cudaDeviceGetAttribute(&sms[dv], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_sm[dv], cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin[dv], cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            return VB_ERR_CUDA;
+        if (cudaFuncSetAttribute(knn_tcp_kernel<MP, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin[dv] - static_smem[dv]) != cudaSuccess ||
+            cudaFuncSetAttribute(knn_tcp_kernel<MP, F16>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+            return VB_ERR_CUDA;
+        attr_set[dv] = true;
+    }
+    int S = 0;
+    for (int c = 4; c >= 2 && !S; --c)
+        if (2 * img + c * blk + heap + (size_t)static_smem[dv] <= (size_t)optin[dv]) S = c;
+    if (!S) return VB_ERR_UNSUPPORTED;
+    a.stages = S;
+    const size_t sm = 2 * img + S * blk + heap;
+    // CTAs per SM: shared memory (1 KB reserved per CTA), at most 2 (256 TMEM columns each)
+    const int per_cta = (int)sm + static_smem[dv] + 1024;
+    const int per_sm = std::max(1, std::min(2, smem_sm[dv] / per_cta));
+    const int64_t nst = (a.ntiles + 1) / 2;
+    const int64_t grid = std::min<int64_t>({nst, (int64_t)per_sm * sms[dv], (int64_t)TCP_MAX_CTAS});
+    knn_tcp_kernel<MP, F16><<<(unsigned)grid, TCP_THREADS, sm, s>>>(a);
+    return last_launch();
+}
+
 template <int MP, int MR = MP>
 static vb_status launch_tile_m(const TileArgs& a, cudaStream_t s)
 {
@@ -1557,7 +2068,33 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
         a.fail_count = w.fb_count + 3;
         if (tensor) {
             a.cap = a.L;
-            switch (mp) {
+            st = VB_ERR_UNSUPPORTED;
+            if (p->tc_variant != VB_TC_STAGED && w.blk) {
+                // tile blocks of the pipelined search: centre, 16-bit images and norms
+                a.kp = pad_k16(m);
+                a.blk = w.blk;
+                a.lbw = w.lbw;
+                a.tlist = w.tlist;
+                tcp_range_init_kernel<<<1, 128, 0, s>>>(w.crange);
+                tcp_range_kernel<<<(unsigned)((n + 63) / 64), 128, 0, s>>>(w.xs, n, m, mp, w.crange);
+                if (f16)
+                    tcp_block_kernel<true><<<(unsigned)((npad + 255) / 256), 256, 0, s>>>(w.xs, n, npad, m, mp, a.kp,
+                                                                                         w.crange, w.blk);
+                else
+                    tcp_block_kernel<false><<<(unsigned)((npad + 255) / 256), 256, 0, s>>>(w.xs, n, npad, m, mp,
+                                                                                          a.kp, w.crange, w.blk);
+                launches += 3;
+                switch (mp) {
+                    case 4: st = f16 ? launch_tcp<4, true>(a, s) : launch_tcp<4, false>(a, s); break;
+                    case 8: st = f16 ? launch_tcp<8, true>(a, s) : launch_tcp<8, false>(a, s); break;
+                    case 16: st = f16 ? launch_tcp<16, true>(a, s) : launch_tcp<16, false>(a, s); break;
+                    case 32: st = f16 ? launch_tcp<32, true>(a, s) : launch_tcp<32, false>(a, s); break;
+                    case 64: st = f16 ? launch_tcp<64, true>(a, s) : launch_tcp<64, false>(a, s); break;
+                    default: st = f16 ? launch_tcp<128, true>(a, s) : launch_tcp<128, false>(a, s); break;
+                }
+                if (st == VB_ERR_UNSUPPORTED && p->tc_variant == VB_TC_PIPELINED) return st;
+            }
+            if (st == VB_ERR_UNSUPPORTED) switch (mp) {
                 case 4: st = f16 ? launch_tc<4, true>(a, s) : launch_tc<4, false>(a, s); break;
                 case 8: st = f16 ? launch_tc<8, true>(a, s) : launch_tc<8, false>(a, s); break;
                 case 16: st = f16 ? launch_tc<16, true>(a, s) : launch_tc<16, false>(a, s); break;

@@ -3,6 +3,7 @@
 // tile, hence how many tiles an SM holds, against how early the pruning bound
 // tightens; the best pair depends on m, k, the precision and the size, so it is
 // measured on the caller's input and cached per (m, k, precision, prune, log2 n).
+// For 16-bit tiles the choice also covers the kernel (staged or pipelined).
 #include "vb_internal.cuh"
 
 #include <map>
@@ -13,7 +14,7 @@ namespace {
 
 using Key = std::tuple<int, int, int, int, int>;
 struct Shape {
-    int margin, seed_tiles;
+    int margin, seed_tiles, tc_variant;
 };
 std::map<Key, Shape> g_cache;
 std::mutex g_mu;
@@ -57,6 +58,7 @@ extern "C" vb_status vb_knn_autotune(vb_ctx* ctx, const float* x, int64_t n, int
         if (it != g_cache.end()) {
             best->margin = it->second.margin;
             best->seed_tiles = it->second.seed_tiles;
+            best->tc_variant = it->second.tc_variant;
             *best_ms = 0.f;
             return VB_OK;
         }
@@ -65,11 +67,14 @@ extern "C" vb_status vb_knn_autotune(vb_ctx* ctx, const float* x, int64_t n, int
     const int margins[] = {4, 8, 16, 32};
     const int seeds_fp32[] = {1, 2, 3};
     const int seeds_tc[] = {0};
+    // 16-bit tiles: both kernels; the FP32 search has one
+    const int variants_tc[] = {VB_TC_PIPELINED, VB_TC_STAGED};
+    const int nv = fp32 ? 1 : 2;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return VB_ERR_CUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return VB_ERR_CUDA; }
     float bms = INFINITY;
-    Shape bs{p->margin, p->seed_tiles};
+    Shape bs{p->margin, p->seed_tiles, p->tc_variant};
     vb_status st = VB_OK;
     const bool prof = c->prof;
     c->prof = false;
@@ -77,10 +82,12 @@ extern "C" vb_status vb_knn_autotune(vb_ctx* ctx, const float* x, int64_t n, int
         if (p->k + mg > 256) continue;
         const int* seeds = fp32 && p->prune != VB_PRUNE_LEARNED ? seeds_fp32 : seeds_tc;
         const int ns = fp32 && p->prune != VB_PRUNE_LEARNED ? 3 : 1;
-        for (int si = 0; si < ns; ++si) {
+        for (int vs = 0; vs < nv * ns; ++vs) {
+            const int vi = vs / ns, si = vs % ns;
             vb_knn_params q = *p;
             q.margin = mg;
             q.seed_tiles = seeds[si];
+            if (!fp32) q.tc_variant = variants_tc[vi];
             float t = INFINITY;
             for (int rep = 0; rep < 3 && st == VB_OK; ++rep) {   // the first run warms up
                 cudaEventRecord(e0, c->stream);
@@ -94,7 +101,7 @@ extern "C" vb_status vb_knn_autotune(vb_ctx* ctx, const float* x, int64_t n, int
             }
             if (st == VB_ERR_UNSUPPORTED) { st = VB_OK; continue; }   // shape too large for this kernel
             if (st != VB_OK) break;
-            if (t < bms) { bms = t; bs = Shape{mg, seeds[si]}; }
+            if (t < bms) { bms = t; bs = Shape{mg, seeds[si], q.tc_variant}; }
         }
         if (st != VB_OK) break;
     }
@@ -107,6 +114,7 @@ extern "C" vb_status vb_knn_autotune(vb_ctx* ctx, const float* x, int64_t n, int
     vb_knn_params q = *p;
     q.margin = bs.margin;
     q.seed_tiles = bs.seed_tiles;
+    q.tc_variant = bs.tc_variant;
     st = knn_run(c, x, n, m, &q, nbr, nbr_d2, ws, ws_bytes, cl);
     if (st != VB_OK) return st;
     {
@@ -115,6 +123,7 @@ extern "C" vb_status vb_knn_autotune(vb_ctx* ctx, const float* x, int64_t n, int
     }
     best->margin = bs.margin;
     best->seed_tiles = bs.seed_tiles;
+    best->tc_variant = bs.tc_variant;
     *best_ms = bms;
     return cuda_status(cudaStreamSynchronize(c->stream));
 }

@@ -32,13 +32,15 @@ def _knn_ref(x, k):
     return OK.knn(x, k)
 
 
+@pytest.mark.parametrize("variant", ["staged", "pipelined"])
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 @pytest.mark.parametrize("with_radius", [False, True])
 @pytest.mark.parametrize("name,n,k,m", [("vmf", 20000, 32, 3), ("torus", 9000, 64, 4), ("gauss100", 3000, 32, 100)])
-def test_tensor_core_knn_is_exact(name, n, k, m, prec, with_radius):
+def test_tensor_core_knn_is_exact(name, n, k, m, prec, with_radius, variant):
     """The search with 16-bit tensor-core distance tiles returns the exact FP64 neighbour
     lists (FP64 rescoring, certificate with the tiles' error bound), with and without a
-    radius guess, and settles most query tiles without the FP32 search."""
+    radius guess, and settles most query tiles without the FP32 search; both kernels
+    (staged, and the pipelined one fed by bulk copies)."""
     import paper_2104_15124_gb300 as vb
     from paper_2104_15124_gb300 import workloads as W
     x = {"vmf": lambda: W.sphere_vmf(n, 2.0, 21), "torus": lambda: W.torus4(n, 0.01, 22),
@@ -49,7 +51,7 @@ def test_tensor_core_knn_is_exact(name, n, k, m, prec, with_radius):
     if with_radius:
         kw = dict(radius=torch.from_numpy(np.sqrt(ref_d2[:, k - 1]).astype(np.float32)).cuda(), inflate=1.3)
     vb.report_reset()
-    nbr, d2 = vb.knn(xt, k, tensor_cores=prec, **kw)
+    nbr, d2 = vb.knn(xt, k, tensor_cores=prec, tc_variant=variant, **kw)
     torch.cuda.synchronize()
     rep = vb.raise_on_device_error()
     assert np.array_equal(nbr.cpu().numpy(), ref_nbr)
@@ -68,8 +70,9 @@ def test_tensor_core_knn_ragged_and_small():
         x = rng.standard_normal((n, m)).astype(np.float32)
         ref_nbr, ref_d2 = OK.knn(x, k)
         for prec in ("fp16", "bf16"):
-            nbr, d2 = vb.knn(torch.from_numpy(x).cuda(), k, tensor_cores=prec)
-            torch.cuda.synchronize()
-            vb.raise_on_device_error()
-            assert np.array_equal(nbr.cpu().numpy(), ref_nbr), (n, m, k, prec)
-            assert np.array_equal(d2.cpu().numpy(), ref_d2), (n, m, k, prec)
+            for variant in ("staged", "pipelined"):
+                nbr, d2 = vb.knn(torch.from_numpy(x).cuda(), k, tensor_cores=prec, tc_variant=variant)
+                torch.cuda.synchronize()
+                vb.raise_on_device_error()
+                assert np.array_equal(nbr.cpu().numpy(), ref_nbr), (n, m, k, prec, variant)
+                assert np.array_equal(d2.cpu().numpy(), ref_d2), (n, m, k, prec, variant)
