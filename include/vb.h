@@ -157,9 +157,12 @@ typedef struct {
                                       cloud, e.g. ln(n_train / n_b) / d (NULL = none) */
     int32_t seed_tiles;      /* exact FP32 search: neighbouring tiles on each side of a query tile that are
                                 searched before any pruning (0 = enough to fill every heap) */
-    int32_t tc_variant;      /* 16-bit tiles: VB_TC_AUTO (pipelined when its shared memory fits, else
-                                staged), VB_TC_STAGED or VB_TC_PIPELINED (VB_ERR_UNSUPPORTED when
-                                k + margin and m leave no room for two ring slots) */
+    int32_t tc_variant;      /* 16-bit tiles: VB_TC_AUTO (FP16: pipelined when its shared memory fits, else
+                                staged; BF16: staged), VB_TC_STAGED or VB_TC_PIPELINED (VB_ERR_UNSUPPORTED
+                                when k + margin and m leave no room for two ring slots).  The pipelined
+                                kernel centres its operands on the whole cloud, not on each query tile,
+                                so its 16-bit error band is wider: exact either way, but with BF16 many
+                                rows go back to the FP32 search */
 } vb_knn_params;
 
 /* Launch-shape autotuner (a16).  Times vb_knn on the caller's input for every

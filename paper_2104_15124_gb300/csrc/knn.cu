@@ -44,6 +44,7 @@ struct KnnWs {
     uint32_t* hist;       // 256 * nblk
     uint32_t* hsum;       // block sums of the histogram scan
     float* xs;            // npad * MP sorted coordinates
+    double* xs64;         // the same in FP64 (exact copies), read by the FP64 rescoring
     float* tlo;           // ntiles * MP
     float* thi;
     int* fb_list;         // n
@@ -88,6 +89,7 @@ size_t knn_plan(Carve& c, int64_t n, int32_t m, const vb_knn_params* p, KnnWs* w
     t.hist = c.take<uint32_t>(256 * nblk);
     t.hsum = c.take<uint32_t>((256 * nblk + USCAN_CHUNK - 1) / USCAN_CHUNK + 1);
     t.xs = c.take<float>(npad * mp);
+    t.xs64 = c.take<double>(npad * mp);
     t.tlo = c.take<float>(ntiles * mp);
     t.thi = c.take<float>(ntiles * mp);
     t.fb_list = c.take<int>(n);
@@ -326,13 +328,15 @@ __global__ void radix_scatter_kernel(const uint32_t* __restrict__ kin, const uin
 }
 
 __global__ void gather_kernel(const float* __restrict__ x, const uint32_t* __restrict__ perm, int64_t n,
-                              int64_t npad, int m, int mp, float* xs)
+                              int64_t npad, int m, int mp, float* xs, double* xs64)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= npad * mp) return;
     int64_t p = i / mp;
     int r = (int)(i - p * mp);
-    xs[i] = (p < n && r < m) ? x[(int64_t)perm[p] * m + r] : 0.f;
+    const float v = (p < n && r < m) ? x[(int64_t)perm[p] * m + r] : 0.f;
+    xs[i] = v;
+    xs64[i] = (double)v;
 }
 
 // One warp per tile: bounding box of its valid points (padding dims stay 0).
@@ -371,22 +375,35 @@ __device__ __forceinline__ double canon_d2(const float* a, const float* b, int m
     return acc;
 }
 
-// The same sum for a query held in registers (q[0..MP)) and a 16-byte aligned
-// candidate row: the row is read with 16-byte loads, the arithmetic is canon_d2's.
-template <int MP>
-__device__ __forceinline__ double canon_d2_q(const float* q, const float* __restrict__ c, int m)
+// canon_d2 on FP64 copies of the FP32 coordinates: the same arithmetic (the FP32 to
+// FP64 conversion is exact), without the conversions, which occupy the narrow FP64 pipe.
+__device__ __forceinline__ double canon_d2_64(const double* a, const double* __restrict__ b, int m)
 {
-    float cv[MP];
+    double acc = 0.0;
+    for (int r = 0; r < m; ++r) {
+        const double dl = __dsub_rn(a[r], b[r]);
+        const double s = __dmul_rn(dl, dl);
+        acc = r == 0 ? s : __dadd_rn(acc, s);
+    }
+    return acc;
+}
+
+// The same for a query held in registers (q[0..MP)) and a 16-byte aligned candidate row.
+template <int MP>
+__device__ __forceinline__ double canon_d2_q64(const double* q, const double* __restrict__ c, int m)
+{
+    double cv[MP];
 #pragma unroll
-    for (int r4 = 0; r4 < MP / 4; ++r4) {
-        const float4 v = *(const float4*)(c + 4 * r4);
-        cv[4 * r4] = v.x; cv[4 * r4 + 1] = v.y; cv[4 * r4 + 2] = v.z; cv[4 * r4 + 3] = v.w;
+    for (int r2 = 0; r2 < MP / 2; ++r2) {
+        const double2 v = *(const double2*)(c + 2 * r2);
+        cv[2 * r2] = v.x;
+        cv[2 * r2 + 1] = v.y;
     }
     double acc = 0.0;
 #pragma unroll
     for (int r = 0; r < MP; ++r) {
         if (r < m) {
-            const double dl = __dsub_rn((double)q[r], (double)cv[r]);
+            const double dl = __dsub_rn(q[r], cv[r]);
             const double sq = __dmul_rn(dl, dl);
             acc = r == 0 ? sq : __dadd_rn(acc, sq);
         }
@@ -396,6 +413,7 @@ __device__ __forceinline__ double canon_d2_q(const float* q, const float* __rest
 
 struct TileArgs {
     const float* xs;
+    const double* xs64;   // FP64 copies of xs (exact), for the FP64 rescoring
     const float* tlo;
     const float* thi;
     const uint32_t* perm;
@@ -500,9 +518,9 @@ __device__ bool finalize_row(const TileArgs& a, uint64_t* arr, int t, int size, 
     }
     const uint64_t Hkey = arr[(size - 1) * COLS + t];
     const uint32_t oq = a.perm[pq];
-    const float* qc = a.xs + pq * MP;
+    const double* qc = a.xs64 + pq * MP;
     constexpr bool QR = MP <= 16;
-    float qv[QR ? MP : 1];
+    double qv[QR ? MP : 1];
     if constexpr (QR) {
 #pragma unroll
         for (int r = 0; r < MP; ++r) qv[r] = qc[r];
@@ -543,8 +561,8 @@ __device__ bool finalize_row(const TileArgs& a, uint64_t* arr, int t, int size, 
             if (cpb[u] != 0xffffffffu) {
                 ojb[u] = a.perm[cpb[u]];
                 double d;
-                if constexpr (QR) d = canon_d2_q<MP>(qv, a.xs + (int64_t)cpb[u] * MP, a.m);
-                else d = canon_d2(qc, a.xs + (int64_t)cpb[u] * MP, a.m);
+                if constexpr (QR) d = canon_d2_q64<MP>(qv, a.xs64 + (int64_t)cpb[u] * MP, a.m);
+                else d = canon_d2_64(qc, a.xs64 + (int64_t)cpb[u] * MP, a.m);
                 djb[u] = (uint64_t)__double_as_longlong(d);
             }
         }
@@ -633,12 +651,12 @@ __device__ bool finalize_row_band(const TileArgs& a, uint64_t* arr, int t, int s
     }
     const uint64_t Hkey = arr[(size - 1) * COLS + t];
     const uint32_t oq = a.perm[pq];
-    const float* qc = a.xs + pq * MP;
+    const double* qc = a.xs64 + pq * MP;
     int32_t* on = a.nbr + (int64_t)oq * a.k;
     double* od = a.nbr_d2 + (int64_t)oq * a.k;
     const int k = a.k;
     constexpr bool QR = MP <= 16;
-    float qv[QR ? MP : 1];
+    double qv[QR ? MP : 1];
     if constexpr (QR) {
 #pragma unroll
         for (int r = 0; r < MP; ++r) qv[r] = qc[r];
@@ -660,8 +678,8 @@ __device__ bool finalize_row_band(const TileArgs& a, uint64_t* arr, int t, int s
             djb[u] = 0.0;
             if (cpb[u] != 0xffffffffu) {
                 ojb[u] = (int32_t)a.perm[cpb[u]];
-                if constexpr (QR) djb[u] = canon_d2_q<MP>(qv, a.xs + (int64_t)cpb[u] * MP, a.m);
-                else djb[u] = canon_d2(qc, a.xs + (int64_t)cpb[u] * MP, a.m);
+                if constexpr (QR) djb[u] = canon_d2_q64<MP>(qv, a.xs64 + (int64_t)cpb[u] * MP, a.m);
+                else djb[u] = canon_d2_64(qc, a.xs64 + (int64_t)cpb[u] * MP, a.m);
             }
         }
 #pragma unroll
@@ -2023,14 +2041,14 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
         }
     }
     const uint32_t* perm = w.val[cur];
-    gather_kernel<<<(unsigned)((npad * mp + 255) / 256), 256, 0, s>>>(x, perm, n, npad, m, mp, w.xs);
+    gather_kernel<<<(unsigned)((npad * mp + 255) / 256), 256, 0, s>>>(x, perm, n, npad, m, mp, w.xs, w.xs64);
     tile_box_kernel<<<(unsigned)((ntiles * 32 + 255) / 256), 256, 0, s>>>(w.xs, n, ntiles, m, mp, w.tlo, w.thi);
     vb_status st = last_launch();
     if (st != VB_OK) return st;
     mark(ctx, VB_STAGE_KNN_ORDER, 1);
 
     TileArgs a = {};
-    a.xs = w.xs; a.tlo = w.tlo; a.thi = w.thi; a.perm = perm; a.n = n; a.ntiles = ntiles;
+    a.xs = w.xs; a.xs64 = w.xs64; a.tlo = w.tlo; a.thi = w.thi; a.perm = perm; a.n = n; a.ntiles = ntiles;
     a.m = m; a.k = p->k; a.L = p->k + p->margin; a.prune = p->prune != VB_PRUNE_NONE;
     // enough neighbouring tiles to fill every heap, unless the caller (the autotuner) chose
     a.nseed = p->seed_tiles > 0 ? 1 + 2 * p->seed_tiles : 1 + 2 * (int)((a.L + TILE) / TILE);
@@ -2069,7 +2087,9 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
         if (tensor) {
             a.cap = a.L;
             st = VB_ERR_UNSUPPORTED;
-            if (p->tc_variant != VB_TC_STAGED && w.blk) {
+            // automatic choice: pipelined for FP16; BF16's 8-bit significand needs the staged kernel's
+            // operands recentred on every query tile (its error band at the cloud's centre is too wide)
+            if ((p->tc_variant == VB_TC_PIPELINED || (p->tc_variant == VB_TC_AUTO && f16)) && w.blk) {
                 // tile blocks of the pipelined search: centre, 16-bit images and norms
                 a.kp = pad_k16(m);
                 a.blk = w.blk;
