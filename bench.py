@@ -193,6 +193,26 @@ def run_reference(a, spec: Spec):
     print(json.dumps(line), flush=True)
 
 
+def _traffic(stage: str, form: str, workload: str):
+    """DRAM bytes (read + write) per launch of the dominant kernel, from the ncu capture
+    recorded in profiles/traffic.json, or None when there is none for this kernel, form and
+    workload or when the kernel's source file changed since the capture (SHA-1 mismatch)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path)).get(f"{stage}/{form}/{workload}")
+    except Exception:
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    if not os.path.exists(src) or hashlib.sha1(open(src, "rb").read()).hexdigest() != rec["source_sha1"]:
+        return None
+    return rec["dram_bytes_per_launch"]
+
+
 def _fp16_distance_error(spec: Spec, nbr: np.ndarray, rows: int = 2000) -> dict:
     """Relative error of the FP16 tile distance against FP64 on sampled neighbour pairs:
     both points recentred on a shared centre (the query's) and rounded to FP16, the
@@ -373,7 +393,7 @@ def main():
     cand = rep["knn_candidates"] / steps_prof
     off = nnz - spec.n
     G = 57
-    KP = max(16, 1 << max(2, (spec.m - 1).bit_length()))
+    KP = (spec.m + 15) // 16 * 16
     tensor_tflops = peaks.get("bf16_tflops", 1900.0)     # FP16 and BF16 run at the same dense rate
 
     def roof(stage):
@@ -387,11 +407,11 @@ def main():
                     "what": f"{G} kernel values per off-diagonal entry, {EX2_PER_ENTRY} ex2 on the SFU "
                             f"({N_SM} SM x {SFU_PER_SM_CLK}/clk x {f_mhz:.0f} MHz / {EX2_PER_ENTRY})"}
         if stage == "knn_tile" and best.endswith("fp16_tc"):
-            ach = cand * 2 * KP / s / 1e12
+            ach = cand * 2 * spec.m / s / 1e12
             return {"bound": "tensor", "unit": "TFLOP/s", "achieved": ach, "peak": tensor_tflops,
                     "frac": ach / tensor_tflops,
-                    "what": f"{int(cand)} candidate pairs x 2 K (K = {KP}) FLOP of FP16 tcgen05.mma; "
-                            f"peak = measured dense bf16 {src} (FP16 rate equal)"}
+                    "what": f"{int(cand)} candidate pairs x 2 m (m = {spec.m}; the MMA runs K = {KP}) FLOP of "
+                            f"FP16 tcgen05.mma; peak = dense bf16 {src} (FP16 rate equal)"}
         if stage == "knn_tile":
             ach = cand * (3 * spec.m + 2) / s / 1e9
             peak = N_SM * FP32_PER_SM_CLK * f_mhz * 1e6 / 1e9
@@ -414,7 +434,7 @@ def main():
     droof = roof(dom) or {"bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": None}
     droof = {kk: droof[kk] for kk in ("bound", "achieved", "peak", "unit", "frac", "what") if kk in droof}
     droof["kernel"] = dom
-    droof["traffic"] = None
+    droof["traffic"] = _traffic(dom, best, spec.name)
 
     cfg = dict(spec.config)
     cfg.update({"form": best, "nnz": nnz, "l2": "flushed between steps (256 MiB write)",

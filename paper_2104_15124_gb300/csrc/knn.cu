@@ -45,6 +45,7 @@ struct KnnWs {
     uint32_t* hsum;       // block sums of the histogram scan
     float* xs;            // npad * MP sorted coordinates
     double* xs64;         // the same in FP64 (exact copies), read by the FP64 rescoring
+    uint64_t* hdump;      // 16-bit search: npad x (k + max(margin, 32)) heap keys handed to the row finish
     float* tlo;           // ntiles * MP
     float* thi;
     int* fb_list;         // n
@@ -90,6 +91,11 @@ size_t knn_plan(Carve& c, int64_t n, int32_t m, const vb_knn_params* p, KnnWs* w
     t.hsum = c.take<uint32_t>((256 * nblk + USCAN_CHUNK - 1) / USCAN_CHUNK + 1);
     t.xs = c.take<float>(npad * mp);
     t.xs64 = c.take<double>(npad * mp);
+    t.hdump = nullptr;
+    if (p && p->precision != VB_PREC_FP32) {   // L <= k + max(margin, 32), the autotuner's range
+        const int64_t lmax = std::min(256, p->k + std::max(p->margin, 32));
+        t.hdump = c.take<uint64_t>((size_t)npad * lmax);
+    }
     t.tlo = c.take<float>(ntiles * mp);
     t.thi = c.take<float>(ntiles * mp);
     t.fb_list = c.take<int>(n);
@@ -445,6 +451,7 @@ struct TileArgs {
     int stages;                 // ring slots of staged tile blocks
     uint32_t* lbw;              // per CTA scratch: ntiles box bounds
     uint64_t* tlist;            // per CTA scratch: ntiles (bound, tile) keys in bound order
+    uint64_t* hdump;            // pipelined search: heaps handed to its row finish ([L][128] per query tile)
 };
 
 constexpr int IB = 8;         // candidates per insertion batch
@@ -1460,7 +1467,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) knn_tcp_kernel(TileArgs a)
     __shared__ volatile uint32_t sred[4];
     __shared__ uint64_t pkeys[32];
     __shared__ volatile int s_stop;
-    __shared__ int s_tile, s_cnt, s_fail;
+    __shared__ int s_tile, s_cnt;
     __shared__ int64_t s_ct[2];
     __shared__ float sqlo[MP], sqhi[MP];
     __shared__ uint32_t tmem_base;
@@ -1468,10 +1475,6 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) knn_tcp_kernel(TileArgs a)
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t nt = a.ntiles;
     const int64_t nst = (nt + 1) / 2;
-    Band bd;
-    bd.u = HT::unit;
-    bd.dabs = HT::dabs;
-    bd.rho_k = 2.f * (float)(KP + 4) * 5.9604645e-8f;
     unsigned long long evaluated = 0;
     unsigned levels = 0, staged = 0;
     uint32_t pseq = 0, mseq = 0, eseq = 0, qcount = 0;   // role-local sequence numbers
@@ -1498,10 +1501,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) knn_tcp_kernel(TileArgs a)
     uint64_t* tl = a.tlist + (int64_t)blockIdx.x * nt;
 
     for (;;) {
-        if (t == 0) {
-            s_tile = atomicAdd(a.work, 1);
-            s_fail = 0;
-        }
+        if (t == 0) s_tile = atomicAdd(a.work, 1);
         __syncthreads();
         const int64_t qs = s_tile;
         if (qs >= nst || s_stop) break;
@@ -1536,7 +1536,6 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) knn_tcp_kernel(TileArgs a)
         // query norm (from the tile block) and the heap's starting key
         float sqa = 0.f;
         if (valid) sqa = ((const float*)(a.blk + (p / TILE) * (size_t)BLK + IMG))[p % TILE];
-        const float qn = sqrtf(sqa);
         const float R2 = a.r2 && valid ? __fmul_ru(a.r2[p], a.r2_scale) : INFINITY;
         const uint64_t sentinel = a.r2 ? (((uint64_t)__float_as_uint(R2) << 32) | 0xffffffffu) : ~0ull;
         if (epi) {
@@ -1720,26 +1719,14 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) knn_tcp_kernel(TileArgs a)
                 const uint32_t wmax = __reduce_max_sync(0xffffffffu, valid ? (uint32_t)(heapmax >> 32) : 0u);
                 if (lane == 0) sred[warp] = wmax;
             }
-            bool ok = true;
-            if (valid) {
-                ok = !s_stop && !(F16 && qn > 0.25f * kHalfClamp);
-                if (ok) ok = finalize_row_band<MP, T2>(a, heap, t, L, p, qhi - qlo, levels, bd, qn);
-                if (!ok) s_fail = 1;
-            }
+            // the rows are finished by tcp_finish_kernel, which keeps the FP64 rescoring off
+            // this kernel's tensor pipeline: hand the heaps over in the same [L][128] layout
+            uint64_t* hd = a.hdump + (size_t)qs * L * T2;
+            for (int sl = 0; sl < L; ++sl) hd[(size_t)sl * T2 + t] = heap[sl * T2 + t];
         }
         ++qcount;
         __syncthreads();
         if (s_stop) break;
-        if (t == 0 && s_fail) {
-            for (int h = 0; h < 2; ++h) {
-                const int64_t qt = 2 * qs + h;
-                if (qt < nt && atomicExch(&a.fail_flag[qt], 1) == 0) {
-                    a.fail_list[atomicAdd(a.fail_count, 1)] = (int)qt;
-                    atomicAdd(&a.rep->knn_retry_tiles, 1ull);
-                }
-            }
-        }
-        __syncthreads();
     }
     // every MMA of this CTA has completed, and no bulk copy is still landing, before exit
     if (warp == 5 && lane == 0) {
@@ -1766,6 +1753,55 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) knn_tcp_kernel(TileArgs a)
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 5) tc::tmem_dealloc(tb, TCP_BUF * TILE);
+}
+
+// Row finish of the pipelined search, one CTA of 128 threads per query tile, on the heaps
+// the search left in a.hdump ([L][128] per query tile, max-heaps): heap sort, FP64
+// rescoring against the 16-bit error band and the certificate (finalize_row_band); a
+// query tile with a row that is not certified goes to the FP32 search.  Run as its own
+// kernel so that the narrow FP64 pipe works at full occupancy instead of stalling the
+// tensor-core pipeline of one CTA per SM.
+template <int MP, bool F16>
+__global__ void __launch_bounds__(T2) tcp_finish_kernel(TileArgs a)
+{
+    using HT = Half16<F16>;
+    const int64_t qs = blockIdx.x;
+    const int t = threadIdx.x;
+    const int L = a.cap;
+    const int64_t p = qs * T2 + t;
+    const bool valid = p < a.n;
+    Band bd;
+    bd.u = HT::unit;
+    bd.dabs = HT::dabs;
+    bd.rho_k = 2.f * (float)(a.kp + 4) * 5.9604645e-8f;
+    unsigned levels = 0;
+    bool ok = true;
+    if (valid) {
+        int64_t qlo = 0, qhi = a.n;
+        if (a.cl.B > 1) {
+            const int b = cloud_id(a.cl, p);
+            qlo = a.cl.ptr[b];
+            qhi = a.cl.ptr[b + 1];
+        }
+        const size_t BLK = tcp_blk_bytes(a.kp);
+        const float sqa = ((const float*)(a.blk + (p / TILE) * BLK + tcp_img_bytes(a.kp)))[p % TILE];
+        const float qn = sqrtf(sqa);
+        ok = !(F16 && qn > 0.25f * kHalfClamp);
+        if (ok) ok = finalize_row_band<MP, T2>(a, a.hdump + (size_t)qs * L * T2, t, L, p, qhi - qlo, levels, bd, qn);
+    }
+    if (__syncthreads_or(!ok) && t == 0) {
+        for (int h = 0; h < 2; ++h) {
+            const int64_t qt = 2 * qs + h;
+            if (qt < a.ntiles && atomicExch(&a.fail_flag[qt], 1) == 0) {
+                a.fail_list[atomicAdd(a.fail_count, 1)] = (int)qt;
+                atomicAdd(&a.rep->knn_retry_tiles, 1ull);
+            }
+        }
+    }
+    unsigned long long lv = levels;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lv += __shfl_xor_sync(0xffffffffu, lv, o);
+    if ((t & 31) == 0 && lv) atomicAdd(&a.rep->knn_heap_levels, lv);
 }
 
 // R2[pos] = (inflate * radius[perm[pos]])^2 for the sorted points (caller-provided radii).
@@ -1958,6 +1994,7 @@ static vb_status launch_tcp(TileArgs a, cudaStream_t s)
     const int64_t nst = (a.ntiles + 1) / 2;
     const int64_t grid = std::min<int64_t>({nst, (int64_t)per_sm * sms[dv], (int64_t)TCP_MAX_CTAS});
     knn_tcp_kernel<MP, F16><<<(unsigned)grid, TCP_THREADS, sm, s>>>(a);
+    tcp_finish_kernel<MP, F16><<<(unsigned)nst, T2, 0, s>>>(a);
     return last_launch();
 }
 
@@ -2048,7 +2085,7 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
     mark(ctx, VB_STAGE_KNN_ORDER, 1);
 
     TileArgs a = {};
-    a.xs = w.xs; a.xs64 = w.xs64; a.tlo = w.tlo; a.thi = w.thi; a.perm = perm; a.n = n; a.ntiles = ntiles;
+    a.xs = w.xs; a.xs64 = w.xs64; a.hdump = w.hdump; a.tlo = w.tlo; a.thi = w.thi; a.perm = perm; a.n = n; a.ntiles = ntiles;
     a.m = m; a.k = p->k; a.L = p->k + p->margin; a.prune = p->prune != VB_PRUNE_NONE;
     // enough neighbouring tiles to fill every heap, unless the caller (the autotuner) chose
     a.nseed = p->seed_tiles > 0 ? 1 + 2 * p->seed_tiles : 1 + 2 * (int)((a.L + TILE) / TILE);
@@ -2103,7 +2140,7 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
                 else
                     tcp_block_kernel<false><<<(unsigned)((npad + 255) / 256), 256, 0, s>>>(w.xs, n, npad, m, mp,
                                                                                           a.kp, w.crange, w.blk);
-                launches += 3;
+                launches += 3;   // range init, range, tile blocks
                 switch (mp) {
                     case 4: st = f16 ? launch_tcp<4, true>(a, s) : launch_tcp<4, false>(a, s); break;
                     case 8: st = f16 ? launch_tcp<8, true>(a, s) : launch_tcp<8, false>(a, s); break;
@@ -2113,16 +2150,21 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
                     default: st = f16 ? launch_tcp<128, true>(a, s) : launch_tcp<128, false>(a, s); break;
                 }
                 if (st == VB_ERR_UNSUPPORTED && p->tc_variant == VB_TC_PIPELINED) return st;
+                if (st == VB_OK) launches += 2;   // search, row finish
             }
-            if (st == VB_ERR_UNSUPPORTED) switch (mp) {
-                case 4: st = f16 ? launch_tc<4, true>(a, s) : launch_tc<4, false>(a, s); break;
-                case 8: st = f16 ? launch_tc<8, true>(a, s) : launch_tc<8, false>(a, s); break;
-                case 16: st = f16 ? launch_tc<16, true>(a, s) : launch_tc<16, false>(a, s); break;
-                case 32: st = f16 ? launch_tc<32, true>(a, s) : launch_tc<32, false>(a, s); break;
-                case 64: st = f16 ? launch_tc<64, true>(a, s) : launch_tc<64, false>(a, s); break;
-                default: st = f16 ? launch_tc<128, true>(a, s) : launch_tc<128, false>(a, s); break;
+            if (st == VB_ERR_UNSUPPORTED) {
+                launches += 1;   // staged search (its rows are finished inside)
+                switch (mp) {
+                    case 4: st = f16 ? launch_tc<4, true>(a, s) : launch_tc<4, false>(a, s); break;
+                    case 8: st = f16 ? launch_tc<8, true>(a, s) : launch_tc<8, false>(a, s); break;
+                    case 16: st = f16 ? launch_tc<16, true>(a, s) : launch_tc<16, false>(a, s); break;
+                    case 32: st = f16 ? launch_tc<32, true>(a, s) : launch_tc<32, false>(a, s); break;
+                    case 64: st = f16 ? launch_tc<64, true>(a, s) : launch_tc<64, false>(a, s); break;
+                    default: st = f16 ? launch_tc<128, true>(a, s) : launch_tc<128, false>(a, s); break;
+                }
             }
         } else {
+            launches += 1;   // search
             switch (mp) {
                 case 4: st = launch_tile<4>(a, s); break;
                 case 8: st = launch_tile<8>(a, s); break;
@@ -2138,7 +2180,6 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
         a.work = w.fb_count + 2;
         a.tile_list = w.fail_list;
         a.tile_count = w.fb_count + 3;
-        launches += 2;
     } else {
         mark(ctx, VB_STAGE_KNN_TILE, 0);
     }
