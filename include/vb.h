@@ -166,8 +166,8 @@ typedef struct {
 } vb_knn_params;
 
 /* Launch-shape autotuner (a16).  Times vb_knn on the caller's input for every
- * candidate shape -- heap depth k + margin with margin in {4, 8, 16, 32} and
- * seed_tiles in {1, 2, 3} for the FP32 search, the margin and the kernel
+ * candidate shape -- heap depth k + margin with margin in {2, 4, 8, 16, 32} and
+ * seed_tiles in {1, 2, 3} for the FP32 search, margin in {4, 8, 16, 32} and the kernel
  * (tc_variant staged or pipelined) for 16-bit tiles --
  * with CUDA events on the context's stream (synchronising), and writes the
  * fastest into *best (a copy of *p with margin, seed_tiles and tc_variant set) and its time

@@ -254,11 +254,11 @@ class Graph:
 # ----------------------------------------------------------------------------- the calls
 def knn(x: torch.Tensor, k: int, margin: int = 16, prune: bool = True, radius: torch.Tensor | None = None,
         inflate: float = 0.0, mlp=None, log_shift: float = 0.0, tensor_cores: str | None = None,
-        tc_variant: str = "auto"):
+        tc_variant: str = "auto", seed_tiles: int = 0):
     """Exact kNN (vb_knn): returns (nbr int32 [n, k], nbr_d2 fp64 [n, k]).  With `radius` (per-point
     guess of the k-th neighbour distance) or a learned `mlp`, the radius-first search runs;
     tensor_cores = "fp16" or "bf16" computes its distance tiles on the tensor cores, with the
-    kernel tc_variant = "auto", "staged" or "pipelined" (VB_TC_*)."""
+    kernel tc_variant = "auto", "staged" or "pipelined" (VB_TC_*); seed_tiles as in vb_knn_params."""
     n, m = x.shape
     dev = x.device
     mode = VB_PRUNE_LEARNED if (radius is not None or mlp is not None) else (VB_PRUNE_EXACT if prune else VB_PRUNE_NONE)
@@ -266,6 +266,7 @@ def knn(x: torch.Tensor, k: int, margin: int = 16, prune: bool = True, radius: t
     p = KnnParams(k, margin, prec, mode, _p(radius),
                   c_p(0) if mlp is None else c_p(mlp.handle()), inflate, log_shift)
     p.tc_variant = {"auto": VB_TC_AUTO, "staged": VB_TC_STAGED, "pipelined": VB_TC_PIPELINED}[tc_variant]
+    p.seed_tiles = seed_tiles
     nbr = torch.empty((n, k), dtype=torch.int32, device=dev)
     d2 = torch.empty((n, k), dtype=torch.float64, device=dev)
     ws = _ws(lib().vb_knn_workspace(n, m, ctypes.byref(p)), dev)

@@ -64,7 +64,8 @@ extern "C" vb_status vb_knn_autotune(vb_ctx* ctx, const float* x, int64_t n, int
         }
     }
     const bool fp32 = p->precision == VB_PREC_FP32;
-    const int margins[] = {4, 8, 16, 32};
+    // margin 2 only for the FP32 search (its certificate band is ~1e-6 relative; 16-bit bands need more)
+    const int margins[] = {2, 4, 8, 16, 32};
     const int seeds_fp32[] = {1, 2, 3};
     const int seeds_tc[] = {0};
     // 16-bit tiles: both kernels; the FP32 search has one
@@ -79,7 +80,7 @@ extern "C" vb_status vb_knn_autotune(vb_ctx* ctx, const float* x, int64_t n, int
     const bool prof = c->prof;
     c->prof = false;
     for (int mg : margins) {
-        if (p->k + mg > 256) continue;
+        if (p->k + mg > 256 || (mg < 4 && !fp32)) continue;
         const int* seeds = fp32 && p->prune != VB_PRUNE_LEARNED ? seeds_fp32 : seeds_tc;
         const int ns = fp32 && p->prune != VB_PRUNE_LEARNED ? 3 : 1;
         for (int vs = 0; vs < nv * ns; ++vs) {
