@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(USCAN_T) uscan_apply_kernel(uint32_t* a, int64
         v[i] = base + i < len ? a[base + i] : 0u;
         s += v[i];
     }
-    uint32_t run = bsum[blockIdx.x] + block_excl_scan_u32(s, sh, nullptr);
+    uint32_t run = (bsum ? bsum[blockIdx.x] : 0u) + block_excl_scan_u32(s, sh, nullptr);
 #pragma unroll
     for (int i = 0; i < USCAN_ITEMS; ++i) {
         if (base + i < len) a[base + i] = run;
@@ -285,12 +285,18 @@ __global__ void __launch_bounds__(USCAN_T) uscan_apply_kernel(uint32_t* a, int64
     }
 }
 
-static void scan_u32(cudaStream_t s, uint32_t* a, int64_t len, uint32_t* bsum)
+// Returns the number of kernels launched (one when len fits a single chunk).
+static int scan_u32(cudaStream_t s, uint32_t* a, int64_t len, uint32_t* bsum)
 {
     const int nb = (int)((len + USCAN_CHUNK - 1) / USCAN_CHUNK);
+    if (nb == 1) {
+        uscan_apply_kernel<<<1, USCAN_T, 0, s>>>(a, len, nullptr);
+        return 1;
+    }
     uscan_reduce_kernel<<<nb, USCAN_T, 0, s>>>(a, len, bsum);
     uscan_top_kernel<<<1, USCAN_T, 0, s>>>(bsum, nb);
     uscan_apply_kernel<<<nb, USCAN_T, 0, s>>>(a, len, bsum);
+    return 3;
 }
 
 // Stable scatter: inside a block, rounds of 256 consecutive keys; inside a
@@ -2058,7 +2064,7 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
     int cur = 0;
     for (int shift = 0; shift < 32; shift += 8) {
         radix_hist_kernel<<<nblk, RADIX_T, 0, s>>>(w.key[cur], n, shift, w.hist, nblk);
-        scan_u32(s, w.hist, (int64_t)256 * nblk, w.hsum);
+        ctx->launches += 2 + scan_u32(s, w.hist, (int64_t)256 * nblk, w.hsum);
         radix_scatter_kernel<<<nblk, RADIX_T, 0, s>>>(w.key[cur], w.val[cur], w.key[cur ^ 1], w.val[cur ^ 1], n,
                                                       shift, w.hist, nblk);
         cur ^= 1;
@@ -2070,11 +2076,10 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
         ctx->launches += 1;
         for (int shift = 0; (int64_t)(cl.B - 1) >> shift; shift += 8) {
             radix_hist_kernel<<<nblk, RADIX_T, 0, s>>>(w.key[cur], n, shift, w.hist, nblk);
-            scan_u32(s, w.hist, (int64_t)256 * nblk, w.hsum);
+            ctx->launches += 2 + scan_u32(s, w.hist, (int64_t)256 * nblk, w.hsum);
             radix_scatter_kernel<<<nblk, RADIX_T, 0, s>>>(w.key[cur], w.val[cur], w.key[cur ^ 1], w.val[cur ^ 1], n,
                                                           shift, w.hist, nblk);
             cur ^= 1;
-            ctx->launches += 5;
         }
     }
     const uint32_t* perm = w.val[cur];
@@ -2197,7 +2202,7 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
     ctx->launches += launches;
     knn_fallback_kernel<<<152, FB_THREADS, 0, s>>>(x, n, m, p->k, w.fb_list, w.fb_count, cl, nbr, nbr_d2);
     mark(ctx, VB_STAGE_KNN_FALLBACK, 1);
-    ctx->launches += 27;   // order: 3 + 4 radix passes x 5 + gather + boxes; search; fallback
+    ctx->launches += 7;   // order: bbox init, bbox, Morton keys, gather, boxes (radix passes counted above); search; fallback
     return last_launch();
 }
 

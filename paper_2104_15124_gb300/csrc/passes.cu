@@ -63,6 +63,23 @@ struct RowGroup {
     }
 };
 
+// A lane's next UNR entries of a row (stride LPR): their column and squared distance
+// loaded together (column -1 past the row's end), so the gathers that follow are all in
+// flight at once; the lane still adds its entries in increasing order, as a plain loop would.
+constexpr int UNR = 4;
+template <int LPR>
+__device__ __forceinline__ void load_entries(const int32_t* __restrict__ col, const float* __restrict__ ed2,
+                                             int64_t e0, int64_t re, int32_t* jj, float* xx)
+{
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+        const int64_t e = e0 + (int64_t)u * LPR;
+        const bool in = e < re;
+        jj[u] = in ? col[e] : -1;
+        xx[u] = in ? ed2[e] : 0.f;
+    }
+}
+
 __global__ void recip_f32_kernel(const double* __restrict__ v, int64_t n, float scale, float* out)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -94,16 +111,20 @@ __device__ void seg_totals(const double* __restrict__ partial, int G, const Clou
     const int64_t lo = cloud_lo(cl, b), hi = cloud_hi(cl, b, n);
     const int64_t bl0 = lo / per, bl1 = (hi - 1) / per;
     const int g = threadIdx.x % SEG_COLS, part = threadIdx.x / SEG_COLS;
-    double s0 = 0.0, s1 = 0.0;
+    // eight independent accumulators keep eight loads in flight per thread; the order of the
+    // additions is fixed, so the totals are deterministic
+    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (g < G) {
         int64_t bl = bl0 + part;
-        for (; bl + SEG_PARTS <= bl1; bl += 2 * SEG_PARTS) {
-            s0 += partial[(bl + b) * G + g];
-            s1 += partial[(bl + SEG_PARTS + b) * G + g];
+        for (; bl + 7 * SEG_PARTS <= bl1; bl += 8 * SEG_PARTS) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] += partial[(bl + u * SEG_PARTS + b) * G + g];
         }
-        if (bl <= bl1) s0 += partial[(bl + b) * G + g];
+#pragma unroll
+        for (int u = 0; u < 7; ++u)
+            if (bl + u * SEG_PARTS <= bl1) acc[u] += partial[(bl + u * SEG_PARTS + b) * G + g];
     }
-    sh[part * SEG_COLS + g] = s0 + s1;
+    sh[part * SEG_COLS + g] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
     __syncthreads();
     if (threadIdx.x < G) {
         double t = 0.0;
@@ -221,8 +242,20 @@ __global__ void __launch_bounds__(kRowThreads, 3) sweep57_kernel(const int64_t* 
         int64_t inext = row_ptr[min(a0 + 1, n)];
         float ri = a0 < n ? irho[a0] : 0.f;
         int since = 0;
+        // two-deep software pipeline: the column and squared distance of the entry two chunks
+        // ahead and the bandwidth gather of the next chunk's entry are in flight while this
+        // chunk's 57 kernel values are formed (column -1: past the warp's range)
+        int32_t j0 = -1, j1 = -1;
+        float x0 = 0.f, x1 = 0.f;
+        if (e0 + lane < e1) { j0 = col[e0 + lane]; x0 = ed2[e0 + lane]; }
+        if (e0 + 32 + lane < e1) { j1 = col[e0 + 32 + lane]; x1 = ed2[e0 + 32 + lane]; }
+        float rj0 = j0 >= 0 ? irho[j0] : 0.f;
         for (int64_t eb = e0; eb < e1; eb += 32) {
             const int64_t e = eb + lane;
+            int32_t j2 = -1;
+            float x2 = 0.f;
+            if (e + 64 < e1) { j2 = col[e + 64]; x2 = ed2[e + 64]; }
+            const float rj1 = j1 >= 0 ? irho[j1] : 0.f;
             float u = INFINITY;
             if (e < e1) {
                 while (inext <= e) {
@@ -230,9 +263,10 @@ __global__ void __launch_bounds__(kRowThreads, 3) sweep57_kernel(const int64_t* 
                     inext = row_ptr[i + 1];
                     ri = irho[i];
                 }
-                const int32_t j = col[e];
-                if (j != i) u = ed2[e] * (ri * irho[j]) * c0;
+                if (j0 != i) u = x0 * (ri * rj0) * c0;
             }
+            j0 = j1; x0 = x1; rj0 = rj1;
+            j1 = j2; x1 = x2;
             float prev[4];
 #pragma unroll
             for (int g = G57 - 1; g >= 0; --g) {
@@ -371,7 +405,14 @@ __global__ void __launch_bounds__(kRowThreads) density_kernel(const int64_t* __r
         const int64_t rb = ok ? row_ptr[i] : 0, re = ok ? row_ptr[i + 1] : 0;
         const float bi = ok ? ib[i] : 0.f;
         float s = 0.f;
-        for (int64_t e = rb + it.sub; e < re; e += LPR) s += ex2_approx(-(ed2[e] * (bi * ib[col[e]])) * c);
+        for (int64_t e0 = rb + it.sub; e0 < re; e0 += UNR * LPR) {
+            int32_t jj[UNR];
+            float xx[UNR];
+            load_entries<LPR>(col, ed2, e0, re, jj, xx);
+#pragma unroll
+            for (int u = 0; u < UNR; ++u)
+                if (jj[u] >= 0) s += ex2_approx(-(xx[u] * (bi * ib[jj[u]])) * c);
+        }
         const float tot = RowGroup<LPR>::sum(s);
         if (ok && it.sub == 0) psi[i] = (double)tot;
     }
@@ -448,12 +489,17 @@ __global__ void __launch_bounds__(kRowThreads) centre_kernel(const int64_t* __re
             const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
             const float pi_ = iP[i], bi = ib[i];
             float so = 0.f, sd = 0.f;
-            for (int64_t e = rb + lane; e < re; e += 32) {
-                const int32_t j = col[e];
-                if (j == i) continue;
-                const float x = ed2[e];
-                so += x * (pi_ * iP[j]);
-                sd += x * (bi * ib[j]);
+            for (int64_t e0 = rb + lane; e0 < re; e0 += UNR * 32) {
+                int32_t jj[UNR];
+                float xx[UNR];
+                load_entries<32>(col, ed2, e0, re, jj, xx);
+#pragma unroll
+                for (int u = 0; u < UNR; ++u) {
+                    const int32_t j = jj[u];
+                    if (j < 0 || j == i) continue;
+                    so += xx[u] * (pi_ * iP[j]);
+                    sd += xx[u] * (bi * ib[j]);
+                }
             }
             so = warp_sum_f32(so);   // FP32 tree over the lanes; the FP64 pipe is narrow
             sd = warp_sum_f32(sd);
@@ -582,9 +628,13 @@ __global__ void __launch_bounds__(kRowThreads) q_kernel(const int64_t* __restric
         const int64_t rb = ok ? row_ptr[i] : 0, re = ok ? row_ptr[i + 1] : 0;
         const float ph = ok ? iPh[i] : 0.f, pl = ok ? iPl[i] : 0.f;
         float s = 0.f;
-        for (int64_t e = rb + it.sub; e < re; e += LPR) {
-            const int32_t j = col[e];
-            s += k_op(ed2[e], ph, pl, iPh[j], iPl[j], c1.h, c1.l);
+        for (int64_t e0 = rb + it.sub; e0 < re; e0 += UNR * LPR) {
+            int32_t jj[UNR];
+            float xx[UNR];
+            load_entries<LPR>(col, ed2, e0, re, jj, xx);
+#pragma unroll
+            for (int u = 0; u < UNR; ++u)
+                if (jj[u] >= 0) s += k_op(xx[u], ph, pl, iPh[jj[u]], iPl[jj[u]], c1.h, c1.l);
         }
         const double tot = (double)RowGroup<LPR>::sum(s);
         if (ok && it.sub == 0) {
@@ -611,9 +661,16 @@ __global__ void __launch_bounds__(kRowThreads) d_kernel(const int64_t* __restric
         const int64_t rb = ok ? row_ptr[i] : 0, re = ok ? row_ptr[i + 1] : 0;
         const float ph = ok ? iPh[i] : 0.f, pl = ok ? iPl[i] : 0.f, qi = ok ? qa[i] : 0.f;
         float s = 0.f;
-        for (int64_t e = rb + it.sub; e < re; e += LPR) {
-            const int32_t j = col[e];
-            s += k_op(ed2[e], ph, pl, iPh[j], iPl[j], c1.h, c1.l) * (qi * qa[j]);
+        for (int64_t e0 = rb + it.sub; e0 < re; e0 += UNR * LPR) {
+            int32_t jj[UNR];
+            float xx[UNR];
+            load_entries<LPR>(col, ed2, e0, re, jj, xx);
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                if (jj[u] < 0) continue;
+                const int32_t j = jj[u];
+                s += k_op(xx[u], ph, pl, iPh[j], iPl[j], c1.h, c1.l) * (qi * qa[j]);
+            }
         }
         const double tot = (double)RowGroup<LPR>::sum(s);
         if (ok && it.sub == 0) {
@@ -645,12 +702,20 @@ __global__ void __launch_bounds__(kRowThreads) lhat_kernel(const int64_t* __rest
         const float ph = ok ? iPh[i] : 0.f, pl = ok ? iPl[i] : 0.f, qi = ok ? qa[i] : 0.f, si = ok ? iS[i] : 0.f;
         float off = 0.f;
         int64_t diag = -1;
-        for (int64_t e = rb + it.sub; e < re; e += LPR) {
-            const int32_t j = col[e];
-            if (j == i) { diag = e; continue; }
-            const float kt = k_op(ed2[e], ph, pl, iPh[j], iPl[j], c1.h, c1.l) * (qi * qa[j]);
-            off += kt;
-            val[e] = kt * (si * iS[j]) * ie;
+        for (int64_t e0 = rb + it.sub; e0 < re; e0 += UNR * LPR) {
+            int32_t jj[UNR];
+            float xx[UNR];
+            load_entries<LPR>(col, ed2, e0, re, jj, xx);
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const int64_t e = e0 + u * LPR;
+                const int32_t j = jj[u];
+                if (j < 0) continue;
+                if (j == i) { diag = e; continue; }
+                const float kt = k_op(xx[u], ph, pl, iPh[j], iPl[j], c1.h, c1.l) * (qi * qa[j]);
+                off += kt;
+                val[e] = kt * (si * iS[j]) * ie;
+            }
         }
         const double tot = (double)RowGroup<LPR>::sum(off);
         if (diag >= 0) {

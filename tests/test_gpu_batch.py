@@ -131,7 +131,7 @@ def test_autotune_picks_a_shape_and_keeps_results(vb, batch):
     torch.cuda.synchronize()
     before = (out.nbr.clone(), out.val.clone(), out.eps2_op.clone())
     shape = builder.autotune(x)
-    assert shape["margin"] in (4, 8, 16, 32) and shape["seed_tiles"] in (1, 2, 3)
+    assert shape["margin"] in (2, 4, 8, 16, 32) and shape["seed_tiles"] in (1, 2, 3)
     assert shape["knn_ms"] > 0
     again = builder.autotune(x)                      # cached: no timing the second time
     assert again["knn_ms"] == 0 and again["margin"] == shape["margin"]
