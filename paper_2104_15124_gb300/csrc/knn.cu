@@ -4,8 +4,9 @@
 // nearest other samples of every point, ordered by the canonical FP64 squared
 // distance and then by index.  The search itself runs in FP32 and is made
 // exact by an FP64 certificate:
-//   a1  Morton order: bounding box, 32-bit Morton keys of the first min(m,4)
-//       coordinates (first 3 when m > 4), stable LSD radix sort, gather of the
+//   a1  Morton order: bounding box, 32-bit Morton keys of the m coordinates when
+//       m <= 4, else of the projections on the cloud's 5 leading principal axes
+//       (sampled covariance, subspace iteration), stable LSD radix sort, gather of the
 //       coordinates into 64-point tiles (zero-padded to MP = 4, 8, ..., 128).
 //   a2  pruning: every tile carries its bounding box; a candidate tile is
 //       skipped when the box-to-box (and, per query, point-to-box) distance,
@@ -38,7 +39,10 @@ constexpr int USCAN_T = 1024, USCAN_ITEMS = 8, USCAN_CHUNK = USCAN_T * USCAN_ITE
 constexpr int FB_THREADS = 256;
 
 struct KnnWs {
-    int* bbox;            // 8 ordered ints: min[4], max[4]
+    int* bbox;            // 16 ordered ints: min[8], max[8]
+    double* pcs;          // m > 4: sampled moments (1 + m + m * m), then the principal axes
+    float* pcc;           // m > 4: the covariance (m x m)
+    float* proj;          // m > 4: n x 5 projections on the leading principal axes
     uint32_t* key[2];
     uint32_t* val[2];     // val[0] after the sort = perm (sorted position -> original index)
     uint32_t* hist;       // 256 * nblk
@@ -58,6 +62,7 @@ struct KnnWs {
     uint32_t* lbw;        // TCP_MAX_CTAS * ntiles: box bounds of the candidate tiles (per CTA)
     uint64_t* tlist;      // TCP_MAX_CTAS * ntiles: candidate tiles ordered by bound (per CTA)
     int* crange;          // 256 ordered ints: per-coordinate min and max of the cloud
+    float* trad;          // ntiles: radius of each tile's ball about its box centre
 };
 
 constexpr int TCP_MAX_CTAS = 304;   // persistent grid of the pipelined search (2 per SM on 152 SMs)
@@ -72,8 +77,9 @@ static int pad_dim(int m)
     while (mp < m) mp *= 2;
     return mp;
 }
-static int morton_dims(int m) { return m <= 4 ? m : 3; }
-static int morton_bits(int md) { return md == 1 ? 30 : md == 2 ? 15 : md == 3 ? 10 : 8; }
+constexpr int PCA_D = 5;           // principal axes of the Morton key when m > 4
+static int morton_dims(int m) { return m <= 4 ? m : PCA_D; }
+static int morton_bits(int md) { return md == 1 ? 30 : md == 2 ? 15 : md == 3 ? 10 : md == 4 ? 8 : md == 5 ? 6 : 5; }
 
 size_t knn_plan(Carve& c, int64_t n, int32_t m, const vb_knn_params* p, KnnWs* w)
 {
@@ -82,7 +88,15 @@ size_t knn_plan(Carve& c, int64_t n, int32_t m, const vb_knn_params* p, KnnWs* w
     const int64_t npad = (ntiles + (ntiles & 1)) * TILE;   // even tile count: the tensor-core search pairs tiles
     const int64_t nblk = (n + RADIX_ITEMS - 1) / RADIX_ITEMS;
     KnnWs t;
-    t.bbox = c.take<int>(8);
+    t.bbox = c.take<int>(16);
+    t.pcs = nullptr;
+    t.pcc = nullptr;
+    t.proj = nullptr;
+    if (m > 4) {
+        t.pcc = c.take<float>((size_t)m * m);
+        t.pcs = c.take<double>(1 + m + (size_t)m * m + (size_t)m * PCA_D);
+        t.proj = c.take<float>((size_t)n * PCA_D);
+    }
     t.key[0] = c.take<uint32_t>(n);
     t.key[1] = c.take<uint32_t>(n);
     t.val[0] = c.take<uint32_t>(n);
@@ -107,11 +121,13 @@ size_t knn_plan(Carve& c, int64_t n, int32_t m, const vb_knn_params* p, KnnWs* w
     t.lbw = nullptr;
     t.tlist = nullptr;
     t.crange = nullptr;
+    t.trad = nullptr;
     if (p && p->precision != VB_PREC_FP32) {
         t.blk = c.take<unsigned char>((size_t)(npad / TILE) * tcp_blk_bytes(pad_k16(m)));
         t.lbw = c.take<uint32_t>((size_t)TCP_MAX_CTAS * ntiles);
         t.tlist = c.take<uint64_t>((size_t)TCP_MAX_CTAS * ntiles);
         t.crange = c.take<int>(256);
+        t.trad = c.take<float>(ntiles);
     }
     if (w) *w = t;
     return c.off;
@@ -128,37 +144,40 @@ __device__ __forceinline__ float ord2f(int i) { return __int_as_float(i >= 0 ? i
 __global__ void bbox_init_kernel(int* bbox, int* fb_count)
 {
     int t = threadIdx.x;
-    if (t < 4) bbox[t] = 0x7fffffff;
-    else if (t < 8) bbox[t] = (int)0x80000000;
+    if (t < 8) bbox[t] = 0x7fffffff;
+    else if (t < 16) bbox[t] = (int)0x80000000;
     if (t < 8) fb_count[t] = 0;
 }
 
 // Bounding box of the Morton coordinates; also rejects non-finite input.
 __global__ void bbox_kernel(const float* __restrict__ x, int64_t n, int m, int md, int* bbox, DevReport* rep)
 {
-    int lo[4], hi[4];
+    int lo[8], hi[8];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) { lo[r] = 0x7fffffff; hi[r] = (int)0x80000000; }
+    for (int r = 0; r < 8; ++r) { lo[r] = 0x7fffffff; hi[r] = (int)0x80000000; }
     bool bad = false;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         for (int r = 0; r < m; ++r) {
             float v = x[i * m + r];
             if (!isfinite(v)) bad = true;
-            if (r < md) {
-                int o = f2ord(v);
-                lo[r] = min(lo[r], o);
-                hi[r] = max(hi[r], o);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (q == r && r < md) {
+                    int o = f2ord(v);
+                    lo[q] = min(lo[q], o);
+                    hi[q] = max(hi[q], o);
+                }
             }
         }
     }
     if (bad) report_error(rep, VB_ERR_DEGENERATE);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < 8; ++r) {
         int a = __reduce_min_sync(0xffffffffu, lo[r]);
         int b = __reduce_max_sync(0xffffffffu, hi[r]);
         if ((threadIdx.x & 31) == 0 && r < md) {
             atomicMin(&bbox[r], a);
-            atomicMax(&bbox[4 + r], b);
+            atomicMax(&bbox[8 + r], b);
         }
     }
 }
@@ -169,9 +188,9 @@ __global__ void morton_kernel(const float* __restrict__ x, int64_t n, int m, int
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float qmax = (float)((1u << bits) - 1u);
-    uint32_t q[4] = {0, 0, 0, 0};
+    uint32_t q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int r = 0; r < md; ++r) {
-        float lo = ord2f(bbox[r]), hi = ord2f(bbox[4 + r]);
+        float lo = ord2f(bbox[r]), hi = ord2f(bbox[8 + r]);
         float ext = hi - lo;
         float s = ext > 0.f ? qmax / ext : 0.f;
         float v = fminf(fmaxf((x[i * m + r] - lo) * s, 0.f), qmax);
@@ -182,6 +201,137 @@ __global__ void morton_kernel(const float* __restrict__ x, int64_t n, int m, int
         for (int r = 0; r < md; ++r) k = (k << 1) | ((q[r] >> b) & 1u);
     key[i] = k;
     val[i] = (uint32_t)i;
+}
+
+// ---- m > 4: the Morton key is built on the projections onto the cloud's PCA_D leading
+// principal axes, so that 64-point tiles are compact in the directions the points spread
+// along (the first coordinates of a wide input need not be those).  The axes only decide
+// the order of the search; the neighbour lists are exact whatever they are.
+constexpr int PCA_SAMPLE = 16384;   // rows sampled for the second moments
+constexpr int PCA_ROWS = 64;        // sampled rows staged per step
+constexpr int PCA_BLOCKS = 16;      // blocks of the moment pass (few, so few atomics)
+constexpr int PCA_EPT = 65;         // moments per thread: (128 * 128 + 128) / 256 rounded up
+constexpr int PCA_ITERS = 40;       // subspace iterations
+
+__global__ void pca_zero_kernel(double* mom, int64_t len)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        mom[i] = 0.0;
+}
+
+// Sampled first and second moments: mom[0] = rows, mom[1 + r] = sum x_r, mom[1 + m + r m + c] = sum x_r x_c.
+// Each of PCA_BLOCKS blocks sums its share of the sampled rows in FP32 registers, then adds
+// them to the FP64 totals once.
+__global__ void __launch_bounds__(256) pca_moments_kernel(const float* __restrict__ x, int64_t n, int m, int64_t stride,
+                                                        int64_t rows, double* mom)
+{
+    __shared__ float xs[PCA_ROWS][128];
+    const int t = threadIdx.x;
+    const int ne = m * m + m;
+    float acc[PCA_EPT];
+#pragma unroll
+    for (int j = 0; j < PCA_EPT; ++j) acc[j] = 0.f;
+    int64_t taken = 0;
+    for (int64_t r0 = (int64_t)blockIdx.x * PCA_ROWS; r0 < rows; r0 += (int64_t)gridDim.x * PCA_ROWS) {
+        const int nr = (int)min((int64_t)PCA_ROWS, rows - r0);
+        __syncthreads();
+        for (int i = t; i < nr * m; i += blockDim.x) {
+            const int rr = i / m, c = i - rr * m;
+            xs[rr][c] = x[(r0 + rr) * stride * m + c];
+        }
+        __syncthreads();
+        taken += nr;
+#pragma unroll
+        for (int j = 0; j < PCA_EPT; ++j) {
+            const int e = t + j * 256;
+            if (e < m * m) {
+                const int a = e / m, b = e - a * m;
+                for (int rr = 0; rr < nr; ++rr) acc[j] = fmaf(xs[rr][a], xs[rr][b], acc[j]);
+            } else if (e < ne) {
+                const int a = e - m * m;
+                for (int rr = 0; rr < nr; ++rr) acc[j] += xs[rr][a];
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < PCA_EPT; ++j) {
+        const int e = t + j * 256;
+        if (e < m * m) atomicAdd(&mom[1 + m + e], (double)acc[j]);
+        else if (e < ne) atomicAdd(&mom[1 + (e - m * m)], (double)acc[j]);
+    }
+    if (t == 0) atomicAdd(&mom[0], (double)taken);
+}
+
+// One block: covariance from the moments, then PCA_ITERS steps of subspace iteration
+// V <- orth(C V) for PCA_D columns (modified Gram-Schmidt); writes V (m x PCA_D).
+__global__ void __launch_bounds__(256) pca_axes_kernel(double* mom, int m, float* C)
+{
+    __shared__ float V[128][PCA_D], Wm[128][PCA_D];
+    __shared__ float red[8];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const double N = fmax(mom[0], 1.0);
+    const double* mu = mom + 1;
+    const double* S = mom + 1 + m;
+    for (int i = t; i < m * m; i += blockDim.x) {   // covariance, FP32 from here on
+        const int r = i / m, c = i - r * m;
+        C[i] = (float)(S[i] / N - (mu[r] / N) * (mu[c] / N));
+    }
+    for (int i = t; i < m * PCA_D; i += blockDim.x) {   // a fixed, well-spread start
+        const int r = i / PCA_D, d = i - r * PCA_D;
+        const uint32_t h = (uint32_t)(r * 2654435761u) ^ (uint32_t)(d * 40503u + 0x9e3779b9u);
+        V[r][d] = (float)((h >> 8) & 0xffff) / 65536.f - 0.5f + (r % PCA_D == d ? 1.f : 0.f);
+    }
+    __syncthreads();
+    for (int it = 0; it < PCA_ITERS; ++it) {
+        for (int i = t; i < m * PCA_D; i += blockDim.x) {   // W = C V, C = S / N - mu mu^T
+            const int r = i / PCA_D, d = i - r * PCA_D;
+            float acc = 0.f;
+            for (int c = 0; c < m; ++c) acc = fmaf(C[r * m + c], V[c][d], acc);
+            Wm[r][d] = acc;
+        }
+        __syncthreads();
+        for (int d = 0; d < PCA_D; ++d) {   // Gram-Schmidt on column d against the earlier ones
+            for (int e = 0; e <= d; ++e) {
+                float part = 0.f;
+                for (int r = t; r < m; r += blockDim.x) part += (e < d ? V[r][e] : Wm[r][d]) * Wm[r][d];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                if (lane == 0) red[w] = part;
+                __syncthreads();
+                float dot = 0.f;
+                for (int q = 0; q < 8; ++q) dot += red[q];
+                __syncthreads();
+                if (e < d) {
+                    for (int r = t; r < m; r += blockDim.x) Wm[r][d] -= dot * V[r][e];
+                } else {
+                    const float inv = dot > 0.f ? rsqrtf(dot) : 0.f;
+                    for (int r = t; r < m; r += blockDim.x) V[r][d] = Wm[r][d] * inv;
+                }
+                __syncthreads();
+            }
+        }
+    }
+    double* out = mom + 1 + m + (size_t)m * m;
+    for (int i = t; i < m * PCA_D; i += blockDim.x) out[i] = (double)V[i / PCA_D][i % PCA_D];
+}
+
+// Projections of every point on the axes: proj[i][d] = sum_r x_ir V_rd.
+__global__ void pca_project_kernel(const float* __restrict__ x, int64_t n, int m, const double* __restrict__ axes,
+                                   float* proj)
+{
+    __shared__ float V[128 * PCA_D];
+    for (int i = threadIdx.x; i < m * PCA_D; i += blockDim.x) V[i] = (float)axes[i];
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float acc[PCA_D] = {};
+    for (int r = 0; r < m; ++r) {
+        const float v = x[i * m + r];
+#pragma unroll
+        for (int d = 0; d < PCA_D; ++d) acc[d] = fmaf(v, V[r * PCA_D + d], acc[d]);
+    }
+#pragma unroll
+    for (int d = 0; d < PCA_D; ++d) proj[i * PCA_D + d] = acc[d];
 }
 
 // Key of the cloud passes: the cloud of each point, in the current (Morton) order.
@@ -351,6 +501,27 @@ __global__ void gather_kernel(const float* __restrict__ x, const uint32_t* __res
     xs64[i] = (double)v;
 }
 
+// One warp per tile: radius of the ball about the tile's box centre that holds its valid
+// points, rounded up past the FP32 error of the sum (relative (m + 2) 2^-24 on the square).
+__global__ void tile_ball_kernel(const float* __restrict__ xs, int64_t n, int64_t ntiles, int m, int mp,
+                                 const float* __restrict__ tlo, const float* __restrict__ thi, float* trad)
+{
+    const int64_t tile = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (tile >= ntiles) return;
+    const int64_t p0 = tile * TILE + lane, p1 = p0 + 32;
+    float s0 = 0.f, s1 = 0.f;
+    for (int r = 0; r < m; ++r) {
+        const float c = 0.5f * (tlo[tile * mp + r] + thi[tile * mp + r]);
+        if (p0 < n) { const float d = xs[p0 * mp + r] - c; s0 = fmaf(d, d, s0); }
+        if (p1 < n) { const float d = xs[p1 * mp + r] - c; s1 = fmaf(d, d, s1); }
+    }
+    float sm = fmaxf(s0, s1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sm = fmaxf(sm, __shfl_xor_sync(0xffffffffu, sm, o));
+    if (lane == 0) trad[tile] = __fmul_ru(sqrtf(sm), 1.00002f);
+}
+
 // One warp per tile: bounding box of its valid points (padding dims stay 0).
 __global__ void tile_box_kernel(const float* __restrict__ xs, int64_t n, int64_t ntiles, int m, int mp,
                                 float* tlo, float* thi)
@@ -457,6 +628,7 @@ struct TileArgs {
     int stages;                 // ring slots of staged tile blocks
     uint32_t* lbw;              // per CTA scratch: ntiles box bounds
     uint64_t* tlist;            // per CTA scratch: ntiles (bound, tile) keys in bound order
+    const float* trad;          // per tile: radius of its ball about the box centre (pipelined search)
     uint64_t* hdump;            // pipelined search: heaps handed to its row finish ([L][128] per query tile)
 };
 
@@ -1363,7 +1535,8 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
 constexpr int TCP_BUF = 4;         // tensor-memory accumulator buffers of 64 columns
 constexpr int TCP_META = 16;       // tile ids in flight (>= slots + buffers + 1)
 constexpr int TCP_THREADS = 192;   // warps 0-3 epilogue, 4 producer, 5 MMA
-constexpr int TCP_BINS = 1024;     // counting-sort bins: FP32 bits of the bound >> 21
+constexpr int TCP_BINS = 4096;     // counting-sort bins: FP32 bits of the bound >> 19 (6 % wide)
+constexpr int TCP_SHIFT = 19;
 
 __global__ void tcp_range_init_kernel(int* crange)
 {
@@ -1476,6 +1649,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) knn_tcp_kernel(TileArgs a)
     __shared__ int s_tile, s_cnt;
     __shared__ int64_t s_ct[2];
     __shared__ float sqlo[MP], sqhi[MP];
+    __shared__ float s_rq;
     __shared__ uint32_t tmem_base;
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -1538,6 +1712,29 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) knn_tcp_kernel(TileArgs a)
             sqlo[r] = lo;
             sqhi[r] = hi;
         }
+        if (warp == 5) {
+            // ball of the query tile about its box centre: the two tiles' balls moved to that centre
+            // (triangle inequality), FP32 sums rounded up
+            float rq = 0.f;
+            for (int h = 0; h < 2; ++h) {
+                const int64_t tq = 2 * qs + h;
+                if (tq >= nt) break;
+                float s2 = 0.f;
+                for (int r = lane; r < a.m; r += 32) {
+                    float lo = a.tlo[(2 * qs) * MP + r], hi = a.thi[(2 * qs) * MP + r];
+                    if (2 * qs + 1 < nt) {
+                        lo = fminf(lo, a.tlo[(2 * qs + 1) * MP + r]);
+                        hi = fmaxf(hi, a.thi[(2 * qs + 1) * MP + r]);
+                    }
+                    const float d = 0.5f * (a.tlo[tq * MP + r] + a.thi[tq * MP + r]) - 0.5f * (lo + hi);
+                    s2 = fmaf(d, d, s2);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                rq = fmaxf(rq, __fadd_ru(__fmul_ru(sqrtf(s2), 1.00002f), a.trad[tq]));
+            }
+            if (lane == 0) s_rq = __fmul_ru(rq, 1.00002f);
+        }
         for (int i = t; i < 2 * TCP_BINS; i += TCP_THREADS) hist[i] = 0;
         // query norm (from the tile block) and the heap's starting key
         float sqa = 0.f;
@@ -1551,15 +1748,24 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) knn_tcp_kernel(TileArgs a)
         __syncthreads();
         const int64_t ct_lo = s_ct[0], ct_hi = s_ct[1];
         // candidate tiles by box lower bound: bounds, bin counts, scan, scatter
+        const float rq = s_rq;
         for (int64_t ct = ct_lo + t; ct < ct_hi; ct += TCP_THREADS) {
-            float acc = 0.f;
+            // two lower bounds on the distance of any candidate in tile ct to any query of this
+            // tile: box to box, and ball to ball (centres apart minus both radii), which is the
+            // tighter one for wide inputs on a low-dimensional set
+            float acc = 0.f, cd = 0.f;
             for (int r = 0; r < a.m; ++r) {
-                const float g = fmaxf(fmaxf(a.tlo[ct * MP + r] - sqhi[r], sqlo[r] - a.thi[ct * MP + r]), 0.f);
+                const float lo = a.tlo[ct * MP + r], hi = a.thi[ct * MP + r];
+                const float g = fmaxf(fmaxf(lo - sqhi[r], sqlo[r] - hi), 0.f);
                 acc = fmaf(g, g, acc);
+                const float dc = 0.5f * (lo + hi) - 0.5f * (sqlo[r] + sqhi[r]);
+                cd = fmaf(dc, dc, cd);
             }
+            const float gap = __fsub_rd(__fmul_rd(sqrtf(cd), 0.99998f), __fadd_ru(rq, a.trad[ct]));
+            if (gap > 0.f) acc = fmaxf(acc, __fmul_rd(__fmul_rd(gap, gap), 0.99998f));
             const uint32_t lbb = __float_as_uint(__fmul_rd(acc, a.lb_factor));
             lbw[ct - ct_lo] = lbb;
-            atomicAdd(&hist[min(lbb >> 21, (uint32_t)TCP_BINS - 1)], 1u);
+            atomicAdd(&hist[min(lbb >> TCP_SHIFT, (uint32_t)TCP_BINS - 1)], 1u);
         }
         __syncthreads();
         if (warp == 0) {
@@ -1583,7 +1789,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) knn_tcp_kernel(TileArgs a)
         __syncthreads();
         for (int64_t ct = ct_lo + t; ct < ct_hi; ct += TCP_THREADS) {
             const uint32_t lbb = lbw[ct - ct_lo];
-            const uint32_t pos = atomicAdd(&hist[TCP_BINS + min(lbb >> 21, (uint32_t)TCP_BINS - 1)], 1u);
+            const uint32_t pos = atomicAdd(&hist[TCP_BINS + min(lbb >> TCP_SHIFT, (uint32_t)TCP_BINS - 1)], 1u);
             tl[pos] = ((uint64_t)lbb << 32) | (uint32_t)ct;
         }
         __syncthreads();   // the list is complete and the bins are free for the heaps
@@ -1608,7 +1814,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) knn_tcp_kernel(TileArgs a)
                         if (key != ~0ull) {
                             const uint32_t lbb = (uint32_t)(key >> 32);
                             const uint32_t thr = max(max(sred[0], sred[1]), max(sred[2], sred[3]));
-                            if (lbb > thr && (lbb >> 21) <= (thr >> 21)) continue;   // skip this tile only
+                            if (lbb > thr && (lbb >> TCP_SHIFT) <= (thr >> TCP_SHIFT)) continue;   // skip this tile only
                             if (lbb <= thr) ct = (int)(uint32_t)key;                 // else: this bin and beyond
                         }
                         const int sl = (int)(pseq % (uint32_t)S);
@@ -1681,8 +1887,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) knn_tcp_kernel(TileArgs a)
                 tc::fence_after_sync();
                 float v[TILE];
                 if (ct >= 0) {
-                    tc::tmem_ld32(lane_addr + (uint32_t)(b * TILE), v);
-                    tc::tmem_ld32(lane_addr + (uint32_t)(b * TILE + 32), v + 32);
+                    tc::tmem_ld64(lane_addr + (uint32_t)(b * TILE), v);
                     const float4* x4 = (const float4*)txn[b];
 #pragma unroll
                     for (int i4 = 0; i4 < TILE / 4; ++i4) {
@@ -1702,9 +1907,11 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) knn_tcp_kernel(TileArgs a)
                     evaluated += TILE;
 #pragma unroll
                     for (int ch = 0; ch < TILE / 32; ++ch) {
-                        uint32_t msk = 0;
+                        // mask of the columns under the bound: four independent 8-bit chains
+                        uint32_t mq[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) msk |= (v[ch * 32 + i] <= hmf ? 1u : 0u) << i;
+                        for (int i = 0; i < 32; ++i) mq[i & 3] |= (v[ch * 32 + i] <= hmf ? 1u : 0u) << i;
+                        uint32_t msk = (mq[0] | mq[1]) | (mq[2] | mq[3]);
                         while (msk) {   // the full key test and the heap update
                             const int i = __ffs(msk) - 1;
                             msk &= msk - 1u;
@@ -2059,8 +2266,24 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
 
     mark(ctx, VB_STAGE_KNN_ORDER, 0);
     bbox_init_kernel<<<1, 32, 0, s>>>(w.bbox, w.fb_count);
-    bbox_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 4), 256, 0, s>>>(x, n, m, md, w.bbox, ctx->rep);
-    morton_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n, m, md, bits, w.bbox, w.key[0], w.val[0]);
+    const unsigned bbox_grid = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 4);
+    if (m <= 4) {
+        bbox_kernel<<<bbox_grid, 256, 0, s>>>(x, n, m, md, w.bbox, ctx->rep);
+        morton_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n, m, md, bits, w.bbox, w.key[0], w.val[0]);
+    } else {
+        // finite check of the input, then the key on the leading principal axes
+        bbox_kernel<<<bbox_grid, 256, 0, s>>>(x, n, m, 0, w.bbox, ctx->rep);
+        const int64_t stride = std::max<int64_t>(1, n / PCA_SAMPLE), rows = (n + stride - 1) / stride;
+        const int64_t mlen = 1 + m + (int64_t)m * m;
+        pca_zero_kernel<<<(unsigned)((mlen + 255) / 256), 256, 0, s>>>(w.pcs, mlen);
+        pca_moments_kernel<<<PCA_BLOCKS, 256, 0, s>>>(x, n, m, stride, rows, w.pcs);
+        pca_axes_kernel<<<1, 256, 0, s>>>(w.pcs, m, w.pcc);
+        pca_project_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n, m, w.pcs + mlen, w.proj);
+        bbox_kernel<<<bbox_grid, 256, 0, s>>>(w.proj, n, PCA_D, PCA_D, w.bbox, ctx->rep);
+        morton_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.proj, n, PCA_D, PCA_D, bits, w.bbox, w.key[0],
+                                                                  w.val[0]);
+        ctx->launches += 5;   // moments zeroed, moments, axes, projection, box of the projections
+    }
     int cur = 0;
     for (int shift = 0; shift < 32; shift += 8) {
         radix_hist_kernel<<<nblk, RADIX_T, 0, s>>>(w.key[cur], n, shift, w.hist, nblk);
@@ -2137,6 +2360,9 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
                 a.blk = w.blk;
                 a.lbw = w.lbw;
                 a.tlist = w.tlist;
+                a.trad = w.trad;
+                tile_ball_kernel<<<(unsigned)((ntiles * 32 + 255) / 256), 256, 0, s>>>(w.xs, n, ntiles, m, mp, w.tlo,
+                                                                                      w.thi, w.trad);
                 tcp_range_init_kernel<<<1, 128, 0, s>>>(w.crange);
                 tcp_range_kernel<<<(unsigned)((n + 63) / 64), 128, 0, s>>>(w.xs, n, m, mp, w.crange);
                 if (f16)
@@ -2145,7 +2371,7 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
                 else
                     tcp_block_kernel<false><<<(unsigned)((npad + 255) / 256), 256, 0, s>>>(w.xs, n, npad, m, mp,
                                                                                           a.kp, w.crange, w.blk);
-                launches += 3;   // range init, range, tile blocks
+                launches += 4;   // tile balls, range init, range, tile blocks
                 switch (mp) {
                     case 4: st = f16 ? launch_tcp<4, true>(a, s) : launch_tcp<4, false>(a, s); break;
                     case 8: st = f16 ? launch_tcp<8, true>(a, s) : launch_tcp<8, false>(a, s); break;
