@@ -61,6 +61,7 @@ struct KnnWs {
     unsigned char* blk;   // npad / 64 tile blocks: 16-bit operand image + 64 FP32 norms
     uint32_t* lbw;        // TCP_MAX_CTAS * ntiles: box bounds of the candidate tiles (per CTA)
     uint64_t* tlist;      // TCP_MAX_CTAS * ntiles: candidate tiles ordered by bound (per CTA)
+    uint4* lbs;           // TCP_MAX_CTAS * ntiles: their bounds for each group of 32 queries (per CTA)
     int* crange;          // 256 ordered ints: per-coordinate min and max of the cloud
     float* trad;          // ntiles: radius of each tile's ball about its box centre
 };
@@ -120,12 +121,14 @@ size_t knn_plan(Carve& c, int64_t n, int32_t m, const vb_knn_params* p, KnnWs* w
     t.blk = nullptr;
     t.lbw = nullptr;
     t.tlist = nullptr;
+    t.lbs = nullptr;
     t.crange = nullptr;
     t.trad = nullptr;
     if (p && p->precision != VB_PREC_FP32) {
         t.blk = c.take<unsigned char>((size_t)(npad / TILE) * tcp_blk_bytes(pad_k16(m)));
         t.lbw = c.take<uint32_t>((size_t)TCP_MAX_CTAS * ntiles);
         t.tlist = c.take<uint64_t>((size_t)TCP_MAX_CTAS * ntiles);
+        t.lbs = c.take<uint4>((size_t)TCP_MAX_CTAS * ntiles);
         t.crange = c.take<int>(256);
         t.trad = c.take<float>(ntiles);
     }
@@ -628,6 +631,7 @@ struct TileArgs {
     int stages;                 // ring slots of staged tile blocks
     uint32_t* lbw;              // per CTA scratch: ntiles box bounds
     uint64_t* tlist;            // per CTA scratch: ntiles (bound, tile) keys in bound order
+    uint4* lbs;                 // per CTA scratch: ntiles bounds of the four 32-query groups
     const float* trad;          // per tile: radius of its ball about the box centre (pipelined search)
     uint64_t* hdump;            // pipelined search: heaps handed to its row finish ([L][128] per query tile)
 };
@@ -1650,6 +1654,8 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) knn_tcp_kernel(TileArgs a)
     __shared__ int64_t s_ct[2];
     __shared__ float sqlo[MP], sqhi[MP];
     __shared__ float s_rq;
+    __shared__ float sblo[4][MP], sbhi[4][MP], sbr[4];   // the four 32-query groups: boxes, ball radii
+    __shared__ uint4 psub[32];
     __shared__ uint32_t tmem_base;
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -1744,6 +1750,25 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) knn_tcp_kernel(TileArgs a)
         if (epi) {
             const uint32_t wr = __reduce_max_sync(0xffffffffu, valid ? (uint32_t)(sentinel >> 32) : 0u);
             if (lane == 0) sred[warp] = wr;
+            // this warp's 32 queries: their box, and the ball about its centre (FP32 sums rounded up)
+            const bool any = __any_sync(0xffffffffu, valid);
+            float s2 = 0.f;
+            for (int r = 0; r < MP; ++r) {
+                const float v = valid && r < a.m ? a.xs[p * MP + r] : 0.f;
+                float l = valid ? v : INFINITY, h = valid ? v : -INFINITY;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    l = fminf(l, __shfl_xor_sync(0xffffffffu, l, o));
+                    h = fmaxf(h, __shfl_xor_sync(0xffffffffu, h, o));
+                }
+                if (!any) { l = 0.f; h = 0.f; }
+                if (lane == 0) { sblo[warp][r] = l; sbhi[warp][r] = h; }
+                const float d = valid ? v - 0.5f * (l + h) : 0.f;
+                s2 = fmaf(d, d, s2);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s2 = fmaxf(s2, __shfl_xor_sync(0xffffffffu, s2, o));
+            if (lane == 0) sbr[warp] = any ? __fmul_ru(sqrtf(s2), 1.00002f) : -1.f;   // -1: no query here
         }
         __syncthreads();
         const int64_t ct_lo = s_ct[0], ct_hi = s_ct[1];
@@ -1752,19 +1777,41 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) knn_tcp_kernel(TileArgs a)
         for (int64_t ct = ct_lo + t; ct < ct_hi; ct += TCP_THREADS) {
             // two lower bounds on the distance of any candidate in tile ct to any query of this
             // tile: box to box, and ball to ball (centres apart minus both radii), which is the
-            // tighter one for wide inputs on a low-dimensional set
-            float acc = 0.f, cd = 0.f;
+            // tighter one for wide inputs on a low-dimensional set; the same two for each group of
+            // 32 queries (one per selection warp), which the producer tests against that warp's
+            // own largest heap bound.  One pass over the coordinates serves all five.
+            float acc = 0.f, cd = 0.f, ab[4] = {0.f, 0.f, 0.f, 0.f}, cb[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
             for (int r = 0; r < a.m; ++r) {
                 const float lo = a.tlo[ct * MP + r], hi = a.thi[ct * MP + r];
+                const float cc = 0.5f * (lo + hi);
                 const float g = fmaxf(fmaxf(lo - sqhi[r], sqlo[r] - hi), 0.f);
                 acc = fmaf(g, g, acc);
-                const float dc = 0.5f * (lo + hi) - 0.5f * (sqlo[r] + sqhi[r]);
+                const float dc = cc - 0.5f * (sqlo[r] + sqhi[r]);
                 cd = fmaf(dc, dc, cd);
+#pragma unroll
+                for (int w4 = 0; w4 < 4; ++w4) {
+                    const float bl = sblo[w4][r], bh = sbhi[w4][r];
+                    const float gw = fmaxf(fmaxf(lo - bh, bl - hi), 0.f);
+                    ab[w4] = fmaf(gw, gw, ab[w4]);
+                    const float dw = cc - 0.5f * (bl + bh);
+                    cb[w4] = fmaf(dw, dw, cb[w4]);
+                }
             }
-            const float gap = __fsub_rd(__fmul_rd(sqrtf(cd), 0.99998f), __fadd_ru(rq, a.trad[ct]));
+            const float rct = a.trad[ct];
+            const float gap = __fsub_rd(__fmul_rd(sqrtf(cd), 0.99998f), __fadd_ru(rq, rct));
             if (gap > 0.f) acc = fmaxf(acc, __fmul_rd(__fmul_rd(gap, gap), 0.99998f));
             const uint32_t lbb = __float_as_uint(__fmul_rd(acc, a.lb_factor));
             lbw[ct - ct_lo] = lbb;
+            uint32_t sub[4];
+#pragma unroll
+            for (int w4 = 0; w4 < 4; ++w4) {
+                float abw = ab[w4];
+                const float gw = __fsub_rd(__fmul_rd(sqrtf(cb[w4]), 0.99998f), __fadd_ru(sbr[w4], rct));
+                if (gw > 0.f) abw = fmaxf(abw, __fmul_rd(__fmul_rd(gw, gw), 0.99998f));
+                sub[w4] = sbr[w4] < 0.f ? 0x7f800000u : __float_as_uint(__fmul_rd(abw, a.lb_factor));   // empty group
+            }
+            a.lbs[(int64_t)blockIdx.x * nt + (ct - ct_lo)] = make_uint4(sub[0], sub[1], sub[2], sub[3]);
             atomicAdd(&hist[min(lbb >> TCP_SHIFT, (uint32_t)TCP_BINS - 1)], 1u);
         }
         __syncthreads();
@@ -1805,7 +1852,9 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) knn_tcp_kernel(TileArgs a)
             const int cnt = s_cnt;
             int go = 1;
             for (int base = 0; go; base += 32) {
-                pkeys[lane] = base + lane < cnt ? tl[base + lane] : ~0ull;
+                const uint64_t kl = base + lane < cnt ? tl[base + lane] : ~0ull;
+                pkeys[lane] = kl;
+                if (kl != ~0ull) psub[lane] = a.lbs[(int64_t)blockIdx.x * nt + ((int64_t)(uint32_t)kl - ct_lo)];
                 __syncwarp();
                 if (lane == 0) {
                     for (int j = 0; j < 32 && go; ++j) {
@@ -1815,7 +1864,11 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) knn_tcp_kernel(TileArgs a)
                             const uint32_t lbb = (uint32_t)(key >> 32);
                             const uint32_t thr = max(max(sred[0], sred[1]), max(sred[2], sred[3]));
                             if (lbb > thr && (lbb >> TCP_SHIFT) <= (thr >> TCP_SHIFT)) continue;   // skip this tile only
-                            if (lbb <= thr) ct = (int)(uint32_t)key;                 // else: this bin and beyond
+                            if (lbb <= thr) {                                        // else: this bin and beyond
+                                const uint4 sb = psub[j];   // skip unless some group of 32 queries may gain
+                                if (sb.x > sred[0] && sb.y > sred[1] && sb.z > sred[2] && sb.w > sred[3]) continue;
+                                ct = (int)(uint32_t)key;
+                            }
                         }
                         const int sl = (int)(pseq % (uint32_t)S);
                         if (!tcp_wait(&empty[sl], ((pseq / (uint32_t)S) & 1u) ^ 1u, &s_stop, a.rep)) {
@@ -2360,6 +2413,7 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
                 a.blk = w.blk;
                 a.lbw = w.lbw;
                 a.tlist = w.tlist;
+                a.lbs = w.lbs;
                 a.trad = w.trad;
                 tile_ball_kernel<<<(unsigned)((ntiles * 32 + 255) / 256), 256, 0, s>>>(w.xs, n, ntiles, m, mp, w.tlo,
                                                                                       w.thi, w.trad);
