@@ -13,6 +13,7 @@ paper's order and notation:
              S = P D^(1/2), P = psi^beta, c = 2 - 2 alpha + d beta + 2 beta
   chi, chi'  bandwidth sweep, eps_xi^2 = 2^xi, Eq. (bandwidth sensitivity), Sec. 2.3
   solve      f~ = Lambda^-1 g~, g~ = Q^T S^2 g / n, f = Q f~, Eqs. (LS minimiser, f_LS), Sec. 3.1
+  gradient   grad u . grad v from the eigenpairs and C-hat_ljk = <phi_l, phi_j * phi_k>_S, Sec. 3.2
 
 Readings where the paper is silent or ambiguous (each also listed in the design doc):
   R1 sparsity: the matrix lives on E = diagonal U kNN U kNN^T (no delta_tol drop).
@@ -323,6 +324,34 @@ def spectral_solve(e: Eigen, S: np.ndarray, g: np.ndarray) -> np.ndarray:
     Q = e.phi[:, 1:]
     gt = Q.T @ (S * S * g) / n
     return Q @ (gt / e.evals[1:])
+
+
+def triple_products(e: Eigen, S: np.ndarray) -> np.ndarray:
+    """Sec. 3.2: C-hat_ljk = <phi_l, phi_j * phi_k>_S over the computed eigenvectors
+    (l, j, k = 0..ell), the discrete counterpart of Eq. (C_ijk)."""
+    n = S.shape[0]
+    return np.einsum("il,ij,ik,i->ljk", e.phi, e.phi, e.phi, S * S / n, optimize=True)
+
+
+def gradient_dot(e: Eigen, S: np.ndarray, u: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """Sec. 3.2, Eq. (gradient in the eigenbasis) truncated after the computed
+    eigenpairs:  grad u . grad v = sum_{l,j,k} u_j v_k (C_ljk / 2)(lambda_l - lambda_j
+    - lambda_k) phi_l, with u_j = <u, phi_j>_S and v_k = <v, phi_k>_S.  With v the
+    coordinate x_s this is the derivative du/dx_s (Eq. gradient of u)."""
+    n = S.shape[0]
+    w = S * S / n
+    uh = e.phi.T @ (w * u)
+    vh = e.phi.T @ (w * v)
+    lam = e.evals
+    C = triple_products(e, S)
+    fac = 0.5 * (lam[:, None, None] - lam[None, :, None] - lam[None, None, :])
+    coef = np.einsum("ljk,j,k->l", C * fac, uh, vh)
+    return e.phi @ coef
+
+
+def carre_du_champ(L: np.ndarray, u: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """Lemma (Carre du Champ identity) for a matrix L: (L(uv) - u L v - v L u) / 2."""
+    return 0.5 * (L @ (u * v) - u * (L @ v) - v * (L @ u))
 
 
 def s_inner(S: np.ndarray, f: np.ndarray, g: np.ndarray) -> float:
