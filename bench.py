@@ -196,6 +196,32 @@ def run_reference(a, spec: Spec):
     print(json.dumps(line), flush=True)
 
 
+def _gradient_timing(vb, out, xt, peaks, src, ell: int = 16, reps: int = 10) -> dict:
+    """vb_gradient (Sec. 3.2) on the built operator: the derivatives along every coordinate
+    of u = sum of the coordinates, from ell + 1 eigenpairs (vb_solve, not timed), timed with
+    CUDA events over `reps` calls.  Memory-bound on the eigenvectors: the algorithmic bytes
+    are four passes over phi ((ell + 1) n FP32 each) plus u, x, S in and grad out."""
+    import torch
+    e = vb.solve(out.graph, out.val, out.S, ell)
+    u = xt.sum(dim=1).contiguous()
+    for _ in range(2):
+        vb.gradient(e.evals, e.phi, out.S, u, xt)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(reps):
+        vb.gradient(e.evals, e.phi, out.S, u, xt)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / reps
+    n, m = xt.shape
+    nbytes = 4 * (ell + 1) * n * 4 + n * (4 + 4 * m + 8) + 4 * m * n
+    ach = nbytes / (ms / 1e3) / 1e9
+    return {"ell": ell, "ms": ms, "bound": "hbm", "unit": "GB/s", "achieved": ach, "peak": peaks["hbm_gbs"],
+            "frac": ach / peaks["hbm_gbs"], "converged": bool(e.converged),
+            "what": f"4 passes over the (ell + 1) x n FP32 eigenvectors + u, x, S, grad; peak hbm_gbs {src}"}
+
+
 def _traffic(stage: str, form: str, workload: str):
     """DRAM bytes (read + write) per launch of the dominant kernel, from the ncu capture
     recorded in profiles/traffic.json, or None when there is none for this kernel, form and
@@ -464,6 +490,8 @@ def main():
             "clocks": clocks, "wall_s": r0["wall"]}
     if net is not None:
         line["learned_radius"] = train_note
+    if rank == 0 and not batched and spec.m <= 16:
+        line["gradient"] = _gradient_timing(vb, ref, xt, peaks, src)
     if "fp16_tc" in forms:
         line["fp16_distance_error"] = _fp16_distance_error(spec, ref.nbr.cpu().numpy())
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:

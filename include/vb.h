@@ -380,6 +380,25 @@ vb_status vb_solve(vb_ctx* ctx, const vb_graph* g, int64_t cap, const float* val
                    const vb_solve_params* p, double* evals, float* phi, const float* g_rhs, float* f,
                    int32_t* iters, void* ws, size_t ws_bytes);
 
+/* ------------------------------------------- gradients in the eigenbasis
+ * Sec. 3.2 (Lemma Carre du Champ identity, Eqs. C_ijk and gradient of u): the
+ * derivatives of a function u along every coordinate, from ell + 1 eigenpairs
+ * of L (as written by vb_solve),
+ *     du/dx_s = sum_{l,j,k=0..ell} u_j v_k (C_ljk / 2)(lambda_l - lambda_j - lambda_k) phi_l,
+ * C_ljk = <phi_l, phi_j * phi_k>_S, u_j = <u, phi_j>_S, v_k = <x_s, phi_k>_S and
+ * <f, g>_S = f^T S^2 g / n.  Computed without forming C: the sums over j and k
+ * reduce exactly to projections of the products (sum_j u_j phi_j)(sum_k v_k phi_k)
+ * and their lambda-weighted companions, O(ell n) per coordinate; FP32 products,
+ * FP64 sums across 1024-sample chunks, reproducible run to run.
+ * evals: ell + 1 FP64 (device); phi: (ell + 1) x n FP32 (device, eigenvector j
+ * contiguous, phi_j = S^-1 phi-hat_j); S: n FP64 (device, from vb_kernel_csr);
+ * u: n FP32 (device); x: n x m FP32 row-major (device, the samples, so that
+ * v = x_s); grad: n x m FP32 row-major (device): grad[i m + s] = du/dx_s at x_i.
+ * 1 <= m <= 128, 0 <= ell <= 1023; workspace from vb_gradient_workspace(). */
+size_t vb_gradient_workspace(int64_t n, int32_t ell, int32_t m);
+vb_status vb_gradient(vb_ctx* ctx, int64_t n, int32_t ell, const double* evals, const float* phi, const double* S,
+                      const float* u, const float* x, int32_t m, float* grad, void* ws, size_t ws_bytes);
+
 /* Diagnostic: one tensor-core tile (tcgen05.mma, kind::f16), d [128][N] = a [128][K] b [N][K]^T
  * with a and b rounded to BF16 and FP32 accumulation in tensor memory; K a multiple of 16 up
  * to 128, N a multiple of 32 up to 128; FP32 row-major device arrays.  The BF16 distance tiles

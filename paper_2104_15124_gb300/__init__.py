@@ -116,6 +116,8 @@ _SIGS = {
     "vb_spmv": (c_i32, [c_p, ctypes.POINTER(GraphC), c_p, c_p, c_i32, c_f32, c_p, c_f32, c_p, c_p, c_sz]),
     "vb_spmv_laplacian_noalloc": (c_i32, [c_p, ctypes.POINTER(GraphC), c_p, c_p, c_f32, c_p, c_f32, c_p]),
     "vb_solve_workspace": (c_sz, [c_i64, c_i64, ctypes.POINTER(SolveParams)]),
+    "vb_gradient_workspace": (c_sz, [c_i64, c_i32, c_i32]),
+    "vb_gradient": (c_i32, [c_p, c_i64, c_i32, c_p, c_p, c_p, c_p, c_p, c_i32, c_p, c_p, c_sz]),
     "vb_solve": (c_i32, [c_p, ctypes.POINTER(GraphC), c_i64, c_p, c_p, ctypes.POINTER(SolveParams), c_p, c_p, c_p,
                          c_p, ctypes.POINTER(c_i32), c_p, c_sz]),
     "vb_mlp_param_count": (c_i64, [c_i32]),
@@ -465,6 +467,18 @@ def solve(g: Graph, val: torch.Tensor, S: torch.Tensor, ell: int, rhs: torch.Ten
     if rc not in (0, -6):
         _check(rc, "vb_solve")
     return Eigen(evals, phi, f, int(it.value), rc == 0)
+
+
+def gradient(evals: torch.Tensor, phi: torch.Tensor, S: torch.Tensor, u: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
+    """Derivatives of u along every coordinate from the eigenpairs of L (vb_gradient):
+    returns grad [n, m] FP32 with grad[i, s] = du/dx_s at sample i."""
+    n, m = x.shape
+    ell = phi.shape[0] - 1
+    grad = torch.empty((n, m), dtype=torch.float32, device=x.device)
+    ws = _ws(lib().vb_gradient_workspace(n, ell, m), x.device)
+    _check(lib().vb_gradient(c_p(_ctx(x.device)), n, ell, _p(evals), _p(phi), _p(S), _p(u), _p(x), m, _p(grad),
+                             _p(ws), ws.numel()), "vb_gradient")
+    return grad
 
 
 @dataclasses.dataclass

@@ -305,6 +305,17 @@ vb_status vb_spmv(vb_ctx* ctx, const vb_graph* gr, const float* val, const doubl
     return spmv_run(C(ctx), gr, val, S, mode, alpha, x, beta, y, ws, ws_bytes);
 }
 
+size_t vb_gradient_workspace(int64_t n, int32_t ell, int32_t m) { return gradient_ws_bytes(n, ell, m); }
+
+vb_status vb_gradient(vb_ctx* ctx, int64_t n, int32_t ell, const double* evals, const float* phi, const double* S,
+                      const float* u, const float* x, int32_t m, float* grad, void* ws, size_t ws_bytes)
+{
+    if (!ctx) return VB_ERR_ARG;
+    DeviceGuard g(C(ctx)->device);
+    if (!g.ok) return VB_ERR_CUDA;
+    return gradient_run(C(ctx), n, ell, evals, phi, S, u, x, m, grad, ws, ws_bytes);
+}
+
 size_t vb_solve_workspace(int64_t n, int64_t cap, const vb_solve_params* p) { return solve_ws_bytes(n, cap, p); }
 
 vb_status vb_solve(vb_ctx* ctx, const vb_graph* gr, int64_t cap, const float* val, const double* S,

@@ -131,6 +131,9 @@ constexpr int kRowThreads = 256;
 
 // ------------------------------------------------------------------ launch wrappers (defined per .cu)
 // kNN (knn.cu)
+size_t gradient_ws_bytes(int64_t n, int32_t ell, int32_t m);
+vb_status gradient_run(Ctx* ctx, int64_t n, int32_t ell, const double* evals, const float* phi, const double* S,
+                       const float* u, const float* x, int32_t m, float* grad, void* ws, size_t ws_bytes);
 size_t knn_plan(Carve& c, int64_t n, int32_t m, const vb_knn_params* p, struct KnnWs* w);
 vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_params* p, int32_t* nbr,
                   double* nbr_d2, void* ws, size_t ws_bytes, Clouds cl = Clouds());
