@@ -115,8 +115,11 @@ vb_status vb_profile_read(vb_ctx* ctx, float* ms, int64_t* launches);
  * canonical FP64 squared distances
  *     d2 = ((s_0 + s_1) + s_2) + ...,  s_r = (x_ir - x_jr)^2  (RN, no FMA),
  * and neighbours are ordered by (d2, j): distance first, then smaller index.
- * The search stages the points in a Morton order, prunes 64-point tiles by
- * bounding boxes and keeps the k + margin nearest FP32 candidates per row;
+ * The search stages the points in a Morton order (of the coordinates when
+ * m <= 4, of the projections on the cloud's 5 leading principal axes when
+ * m > 4), prunes 64-point tiles by bounding boxes (and, in the pipelined
+ * 16-bit search, by balls about the box centres) and keeps the k + margin
+ * nearest FP32 (or 16-bit) candidates per row;
  * an FP64 rescoring with a proven FP32 error bound certifies every row, and
  * rows that fail it are recomputed by an exact FP64 radix selection.  The
  * output is therefore exact, identical to a brute-force FP64 search. */
