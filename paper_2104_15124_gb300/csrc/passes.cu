@@ -98,6 +98,9 @@ struct SweepConst {
 // cloud's total is summed in a fixed order.
 __host__ __device__ inline int64_t rows_per_block(int64_t n, int nblk) { return (n + nblk - 1) / nblk; }
 inline size_t seg_slots(int B) { return (size_t)kRowBlocks + (size_t)B; }
+// The sweeps run one resident wave (three 256-thread blocks per SM, their launch bound): each
+// warp then owns a longer range of entries, which amortises its 57 end-of-range reductions.
+constexpr int kSweepBlocks = 152 * 3;
 
 // Column totals over cloud b's slots (slots of G values) by a block of SEG_T threads:
 // thread t sums column t % 64 over the slots bl = t / 64, t / 64 + SEG_PARTS, ... (reads of
@@ -370,13 +373,13 @@ vb_status sweep_run(Ctx* ctx, const vb_graph* g, const double* rho, double scale
     recip_f32_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(rho, g->n, 1.f, irho);
     mark(ctx, stage, 0);
     if (G == G57 && dxi == 0.25)
-        sweep57_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, g->n, irho, xi_c_dev, scale, sc,
+        sweep57_kernel<<<kSweepBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, g->n, irho, xi_c_dev, scale, sc,
                                                           cl, partial);
     else
-        sweep_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, g->n, irho, xi_c_dev, scale, G, sc,
+        sweep_kernel<<<kSweepBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, g->n, irho, xi_c_dev, scale, G, sc,
                                                         cl, partial);
     mark(ctx, stage, 1);
-    sweep_finish_kernel<<<(unsigned)cl.B, 1024, 0, s>>>(partial, kRowBlocks, G, g->n, cl, xi_lo, dxi, xi_c_dev,
+    sweep_finish_kernel<<<(unsigned)cl.B, 1024, 0, s>>>(partial, kSweepBlocks, G, g->n, cl, xi_lo, dxi, xi_c_dev,
                                                         warn_bit, eps2, chi, dim, ctx->rep);
     ctx->launches += 3;
     return last_launch();
