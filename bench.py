@@ -116,6 +116,22 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(v: float, ws: int, device) -> float:
+    """The largest of every rank's v (the job's time is its slowest rank's); v itself on one rank."""
+    if ws <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, steps: int, ws: int, max_seconds: float) -> float:
+    """Whole-job units per second: every rank's units over the slowest rank's time."""
+    return units_per_rank * steps * ws / max_seconds
+
+
 def _dist():
     return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
 
@@ -343,11 +359,7 @@ def main():
         wall = time.perf_counter() - t_wall
         clocks = clk.stop()
         rep = vb.raise_on_device_error(dev)
-        total_s = sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3
-        if ws > 1:
-            t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_s = float(t.item())
+        total_s = max_over_ranks(sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3, ws, dev)
         return dict(total_s=total_s, clocks=clocks, wall=wall, graph=g)
 
     def profile_form(builder, steps):
@@ -379,7 +391,7 @@ def main():
     r0 = res[best]
     builder = builders[best]
     total_s = r0["total_s"]
-    value = spec.n * a.steps * ws / total_s
+    value = job_throughput(spec.n, a.steps, ws, total_s)
 
     # ---------------- end to end through the public API: host input -> build -> host CSR
     x_pin = torch.from_numpy(spec.x).pin_memory()
@@ -406,11 +418,7 @@ def main():
         e2e_ms.append(e0.elapsed_time(e1))
         d2h = 8 + z * 8 + (spec.n + 1) * 8
     barrier()
-    e2e_s = sum(e2e_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(sum(e2e_ms) / 1e3, ws, dev)
 
     # ---------------- roofline of every stage of the chosen form, and of the dominant one
     peaks, src = _peaks()
@@ -472,14 +480,14 @@ def main():
             "ms_per_step": 1e3 * total_s / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
             "forms": {f: {"ms_per_step": 1e3 * res[f]["total_s"] / a.steps,
-                          "points_per_s": spec.n * a.steps * ws / res[f]["total_s"],
+                          "points_per_s": job_throughput(spec.n, a.steps, ws, res[f]["total_s"]),
                           "knn_ms": round(res[f]["stage_ms"].get("knn_tile", 0.0), 4),
                           "knn_candidate_pairs": res[f]["rep"]["knn_candidates"] // steps_prof,
                           "knn_retry_tiles": res[f]["rep"]["knn_retry_tiles"] // steps_prof,
                           "knn_fallback_rows": res[f]["rep"]["knn_fallback_rows"] // steps_prof,
                           "autotuned": {kk: v for kk, v in shapes[f].items() if kk != "knn_ms"}} for f in forms},
             "vs_plain_fp32": res["plain_fp32"]["total_s"] / total_s,
-            "e2e": {"value": spec.n * a.steps * ws / e2e_s, "unit": "points/s", "h2d_bytes_per_step": int(spec.x.nbytes),
+            "e2e": {"value": job_throughput(spec.n, a.steps, ws, e2e_s), "unit": "points/s", "h2d_bytes_per_step": int(spec.x.nbytes),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s / a.steps},
             "gpu_launches": int(r0["launches"] * a.steps), "roofline": droof, "kernels": kernels,
             "knn": {"candidate_pairs_per_step": int(cand),
