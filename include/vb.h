@@ -140,6 +140,8 @@ vb_status vb_profile_read(vb_ctx* ctx, float* ms, int64_t* launches);
  * converted once into its MMA operand image; a producer warp stages the images by
  * bulk copies (TMA) into a shared-memory ring, an MMA warp feeds four tensor-memory
  * accumulator buffers, and four warps select, all overlapped. */
+#define VB_KEYS_COMPACT 0
+#define VB_KEYS_FULL    1
 #define VB_TC_AUTO      0
 #define VB_TC_STAGED    1
 #define VB_TC_PIPELINED 2
@@ -166,6 +168,10 @@ typedef struct {
                                 kernel centres its operands on the whole cloud, not on each query tile,
                                 so its 16-bit error band is wider: exact either way, but with BF16 many
                                 rows go back to the FP32 search */
+    int32_t heap_keys;       /* FP32 search (not radius-first): VB_KEYS_COMPACT (default: 32-bit heap
+                                keys, half the shared memory, first pass; tiles that need more than 255
+                                candidate-tile visits or fail the certificate are redone with full keys)
+                                or VB_KEYS_FULL (64-bit keys only) */
 } vb_knn_params;
 
 /* Launch-shape autotuner (a16).  Times vb_knn on the caller's input for every

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libvb.so")
 VB_PREC_FP32, VB_PREC_BF16, VB_PREC_FP16 = 0, 1, 2
 VB_PRUNE_NONE, VB_PRUNE_EXACT, VB_PRUNE_LEARNED = 0, 1, 2
 VB_TC_AUTO, VB_TC_STAGED, VB_TC_PIPELINED = 0, 1, 2
+VB_KEYS_COMPACT, VB_KEYS_FULL = 0, 1
 VB_SPMV_PLAIN, VB_SPMV_LAPLACIAN = 0, 1
 XI_LO, XI_HI, DXI = -10.0, 4.0, 0.25
 VB_NOALLOC_MAX_N = 1 << 20   # rows vb_spmv_laplacian_noalloc accepts (its static scratch size)
@@ -46,7 +47,7 @@ c_i32, c_i64, c_f32, c_f64, c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_floa
 class KnnParams(ctypes.Structure):
     _fields_ = [("k", c_i32), ("margin", c_i32), ("precision", c_i32), ("prune", c_i32), ("radius", c_p),
                 ("mlp", c_p), ("radius_inflate", c_f32), ("radius_log_shift", c_f32), ("cloud_log_shift", c_p),
-                ("seed_tiles", c_i32), ("tc_variant", c_i32)]
+                ("seed_tiles", c_i32), ("tc_variant", c_i32), ("heap_keys", c_i32)]
 
 
 class GraphC(ctypes.Structure):
@@ -256,11 +257,12 @@ class Graph:
 # ----------------------------------------------------------------------------- the calls
 def knn(x: torch.Tensor, k: int, margin: int = 16, prune: bool = True, radius: torch.Tensor | None = None,
         inflate: float = 0.0, mlp=None, log_shift: float = 0.0, tensor_cores: str | None = None,
-        tc_variant: str = "auto", seed_tiles: int = 0):
+        tc_variant: str = "auto", seed_tiles: int = 0, heap_keys: str = "compact"):
     """Exact kNN (vb_knn): returns (nbr int32 [n, k], nbr_d2 fp64 [n, k]).  With `radius` (per-point
     guess of the k-th neighbour distance) or a learned `mlp`, the radius-first search runs;
     tensor_cores = "fp16" or "bf16" computes its distance tiles on the tensor cores, with the
-    kernel tc_variant = "auto", "staged" or "pipelined" (VB_TC_*); seed_tiles as in vb_knn_params."""
+    kernel tc_variant = "auto", "staged" or "pipelined" (VB_TC_*); seed_tiles and heap_keys
+    ("compact" or "full") as in vb_knn_params."""
     n, m = x.shape
     dev = x.device
     mode = VB_PRUNE_LEARNED if (radius is not None or mlp is not None) else (VB_PRUNE_EXACT if prune else VB_PRUNE_NONE)
@@ -269,6 +271,7 @@ def knn(x: torch.Tensor, k: int, margin: int = 16, prune: bool = True, radius: t
                   c_p(0) if mlp is None else c_p(mlp.handle()), inflate, log_shift)
     p.tc_variant = {"auto": VB_TC_AUTO, "staged": VB_TC_STAGED, "pipelined": VB_TC_PIPELINED}[tc_variant]
     p.seed_tiles = seed_tiles
+    p.heap_keys = {"compact": VB_KEYS_COMPACT, "full": VB_KEYS_FULL}[heap_keys]
     nbr = torch.empty((n, k), dtype=torch.int32, device=dev)
     d2 = torch.empty((n, k), dtype=torch.float64, device=dev)
     ws = _ws(lib().vb_knn_workspace(n, m, ctypes.byref(p)), dev)

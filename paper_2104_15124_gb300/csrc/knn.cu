@@ -642,17 +642,17 @@ constexpr int RUN = 8;        // longest run of FP32-indistinguishable neighbour
 constexpr int FB = 8;         // keys rescored per batch in the row finish
 
 // Sift key down from node i of the max-heap heap[0..size) (column t of a [.][COLS] array).
-template <int COLS = TILE>
-__device__ __forceinline__ void sift_down(uint64_t* heap, int t, int i, int size, uint64_t key, unsigned& levels)
+template <int COLS = TILE, class K>
+__device__ __forceinline__ void sift_down(K* heap, int t, int i, int size, K key, unsigned& levels)
 {
     for (;;) {
         int l = 2 * i + 1;
         if (l >= size) break;
         ++levels;
-        uint64_t ck = heap[l * COLS + t];
+        K ck = heap[l * COLS + t];
         int ch = l;
         if (l + 1 < size) {
-            uint64_t rk = heap[(l + 1) * COLS + t];
+            K rk = heap[(l + 1) * COLS + t];
             if (rk > ck) { ck = rk; ch = l + 1; }
         }
         if (ck <= key) break;
@@ -663,11 +663,38 @@ __device__ __forceinline__ void sift_down(uint64_t* heap, int t, int i, int size
 }
 
 // Floyd's bottom-up construction of a max-heap over heap[0..size).
-template <int COLS = TILE>
-__device__ __forceinline__ void heapify(uint64_t* heap, int t, int size, unsigned& levels)
+template <int COLS = TILE, class K>
+__device__ __forceinline__ void heapify(K* heap, int t, int size, unsigned& levels)
 {
     for (int i = size / 2 - 1; i >= 0; --i) sift_down<COLS>(heap, t, i, size, heap[i * COLS + t], levels);
 }
+
+// Heap keys of the FP32 search.  Full: FP32 distance bits << 32 | sorted position.
+// Compact (32-bit, half the shared memory, so twice the CTAs per SM): the distance bits
+// truncated to 18 (sign dropped, 8 exponent and 10 mantissa bits: the key is a lower edge of
+// a bucket 2^-10 wide) << 14 | slot, slot = visit number << 6 | lane of the candidate tile;
+// the CTA keeps the tile of every visit number.  Both order by distance first.
+template <bool K32> struct KeyOps;
+template <> struct KeyOps<false> {
+    using T = uint64_t;
+    static constexpr T EMPTY = ~0ull;
+    // FP32 bits no smaller than the distance of any key <= k
+    static __device__ __forceinline__ uint32_t dist_hi(T k) { return (uint32_t)(k >> 32); }
+    static __device__ __forceinline__ T make(uint32_t dbits, int, int, int64_t cp)
+    {
+        return ((uint64_t)dbits << 32) | (uint32_t)cp;
+    }
+};
+constexpr int VMAX = 255;      // visits a compact-key query tile may make (slot 0x3fff stays unused)
+template <> struct KeyOps<true> {
+    using T = uint32_t;
+    static constexpr T EMPTY = ~0u;
+    static __device__ __forceinline__ uint32_t dist_hi(T k) { return k == ~0u ? ~0u : (((k >> 14) << 13) | 0x1fffu); }
+    static __device__ __forceinline__ T make(uint32_t dbits, int vis, int c, int64_t)
+    {
+        return ((dbits >> 13) << 14) | ((uint32_t)vis << 6) | (uint32_t)c;
+    }
+};
 
 template <int MP>
 __device__ __forceinline__ float point_box_lb(const float* q, const float* lo, const float* hi)
@@ -694,18 +721,23 @@ __device__ __forceinline__ float point_box_lb(const float* q, const float* lo, c
 // e_lin, e_const: an absolute error bound E(d) = e_lin sqrt(d) + e_const of the
 // distances in the keys on top of the relative FP32 band (0 for FP32 distances;
 // the BF16 tensor-core distances need them).
-template <int MP, int COLS = TILE>
-__device__ bool finalize_row(const TileArgs& a, uint64_t* arr, int t, int size, bool is_heap, int64_t pq,
-                             int64_t ncl, int bound_mode, float bound, unsigned& levels, float e_lin = 0.f, float e_const = 0.f)
+// Compact keys (K = uint32_t) decode through vtab, the tile of every visit number, and carry
+// a distance bucket [lo, hi] instead of a value: runs and the certificate use its edges.
+template <int MP, int COLS = TILE, class K = uint64_t>
+__device__ bool finalize_row(const TileArgs& a, K* arr, int t, int size, bool is_heap, int64_t pq,
+                             int64_t ncl, int bound_mode, float bound, unsigned& levels, float e_lin = 0.f, float e_const = 0.f,
+                             const int* vtab = nullptr)
 {
+    constexpr bool K32 = sizeof(K) == 4;
+    constexpr K EMPTY = (K)~(K)0;
     if (!is_heap) heapify<COLS>(arr, t, size, levels);
     for (int e = size - 1; e > 0; --e) {
-        const uint64_t top = arr[t];
-        const uint64_t key = arr[e * COLS + t];
+        const K top = arr[t];
+        const K key = arr[e * COLS + t];
         arr[e * COLS + t] = top;
         sift_down<COLS>(arr, t, 0, e, key, levels);
     }
-    const uint64_t Hkey = arr[(size - 1) * COLS + t];
+    const K Hkey = arr[(size - 1) * COLS + t];
     const uint32_t oq = a.perm[pq];
     const double* qc = a.xs64 + pq * MP;
     constexpr bool QR = MP <= 16;
@@ -736,12 +768,19 @@ __device__ bool finalize_row(const TileArgs& a, uint64_t* arr, int t, int size, 
     for (int r0 = 0; r0 < size && !done; r0 += FB) {
         uint32_t cpb[FB], ojb[FB];
         uint64_t djb[FB];
-        float dfb[FB];
+        float dfb[FB], dfh[FB];
 #pragma unroll
         for (int u = 0; u < FB; ++u) {
-            const uint64_t key = r0 + u < size ? arr[(r0 + u) * COLS + t] : ~0ull;
-            cpb[u] = (uint32_t)key;
-            dfb[u] = __uint_as_float((uint32_t)(key >> 32));
+            const K key = r0 + u < size ? arr[(r0 + u) * COLS + t] : EMPTY;
+            if constexpr (K32) {
+                const uint32_t slot = key & 0x3fffu, q = (key >> 14) << 13;
+                cpb[u] = key == EMPTY ? 0xffffffffu : (uint32_t)vtab[slot >> 6] * TILE + (slot & 63u);
+                dfb[u] = __uint_as_float(q);
+                dfh[u] = __uint_as_float(q | 0x1fffu);
+            } else {
+                cpb[u] = (uint32_t)key;
+                dfb[u] = dfh[u] = __uint_as_float((uint32_t)(key >> 32));
+            }
         }
 #pragma unroll
         for (int u = 0; u < FB; ++u) {
@@ -783,7 +822,7 @@ __device__ bool finalize_row(const TileArgs& a, uint64_t* arr, int t, int size, 
                 }
             }
             ++rlen;
-            run_last = df;
+            run_last = dfh[u];
         }
     }
     if (ok && out < a.k) emit();
@@ -791,8 +830,9 @@ __device__ bool finalize_row(const TileArgs& a, uint64_t* arr, int t, int size, 
     if (out < a.k) { atomicAdd(&a.rep->knn_rows_short, 1ull); return false; }
     float B = bound;
     if (bound_mode == 1) {
-        if (ncl - 1 <= (int64_t)size || Hkey == ~0ull) return true;   // every candidate was kept
-        B = __uint_as_float((uint32_t)(Hkey >> 32));
+        if (ncl - 1 <= (int64_t)size || Hkey == EMPTY) return true;   // every candidate was kept
+        if constexpr (K32) B = __uint_as_float((Hkey >> 14) << 13);   // lower edge of its bucket
+        else B = __uint_as_float((uint32_t)(Hkey >> 32));
     }
     const double Eb = 1.01 * ((double)e_lin * sqrt((double)fmaxf(B, 0.f)) + (double)e_const);
     const bool cert = isfinite(B) && dk < ((double)B - Eb) * a.cert_factor - (double)a.m * 1.1754943508222875e-38;
@@ -904,25 +944,31 @@ __device__ bool finalize_row_band(const TileArgs& a, uint64_t* arr, int t, int s
 
 // Query tiles are taken from a global counter by a persistent grid of 64-thread
 // CTAs, one query per thread.  Shared memory:
-//   heap  [L][64]  u64  max-heap per query of keys (FP32 distance bits << 32 | sorted position)
-//   buf   [IB][64] u64  per-thread batch of keys that passed the heap threshold
+//   heap  [L][64]  key  max-heap per query of keys (KeyOps: 64-bit full or 32-bit compact)
+//   buf   [IB][64] key  per-thread batch of keys that passed the heap threshold
 //   cand  [64][MP] f32  staged candidate tile
 //   qs    [MP][64] f32  query coordinates (MP > 16 only)
 //   slist [SCAP]   u64  surviving candidate tiles keyed (box lower bound bits << 32 | tile)
+//   vtab  [VMAX]   i32  compact keys: the candidate tile of every visit number
 // MR <= MP is the number of coordinates the distance loop reads (the rest are zero padding).
-template <int MP, int MR = MP>
+// With compact keys a query tile that needs more than VMAX visits, or has a row that fails the
+// certificate, is listed for the plain search with full keys (a second pass).
+template <int MP, int MR = MP, bool K32 = false>
 __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
 {
+    using KO = KeyOps<K32>;
+    using KT = typename KO::T;
     extern __shared__ __align__(16) unsigned char smem[];
     const int L = a.L;
-    uint64_t* heap = (uint64_t*)smem;
-    uint64_t* buf = heap + (size_t)L * TILE;
-    uint64_t* slist = buf + IB * TILE;
+    KT* heap = (KT*)smem;
+    KT* buf = heap + (size_t)L * TILE;
+    uint64_t* slist = (uint64_t*)(buf + IB * TILE);
     float* cand = (float*)(slist + SCAP);
     float* qs = cand + TILE * MP;
+    int* vtab = (int*)(qs + (MP > 16 ? TILE * MP : 0));
     __shared__ float sqlo[MP], sqhi[MP];
     __shared__ uint32_t sred[2];
-    __shared__ int s_tile, s_cnt;
+    __shared__ int s_tile, s_cnt, s_nvis;
     __shared__ int64_t s_ct[2];
 
     constexpr bool QREG = MP <= 16;
@@ -963,16 +1009,18 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
         } else {
             for (int r = 0; r < MP; ++r) qs[r * TILE + t] = a.xs[p * MP + r];
         }
-        for (int sl = 0; sl < L; ++sl) heap[sl * TILE + t] = ~0ull;
+        for (int sl = 0; sl < L; ++sl) heap[sl * TILE + t] = KO::EMPTY;
+        if (t == 0) s_nvis = 0;
+        bool overflow = false;   // compact keys: more visits than vtab holds
         for (int r = t; r < MP; r += TILE) {
             sqlo[r] = a.tlo[qt * MP + r];
             sqhi[r] = a.thi[qt * MP + r];
         }
-        uint64_t maxkey = ~0ull;
+        KT maxkey = KO::EMPTY;
         int fill = 0;               // keys stored so far; the heap is ordered once it holds L
         uint32_t thr_blk = 0xffffffffu;
-        const bool rmode = a.r2 != nullptr;
-        if (rmode) {
+        const bool rmode = !K32 && a.r2 != nullptr;   // compact keys: plain search only
+        if constexpr (!K32) if (rmode) {
             // radius-first: every slot starts as a sentinel at the query's radius bound, so only
             // candidates inside the radius ever enter and tiles are pruned from the start
             const float R2 = valid ? __fmul_ru(a.r2[p], a.r2_scale) : 0.f;
@@ -990,6 +1038,7 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
 
         // Visit candidate tile ct for every query of this tile that may still gain from it.
         auto visit = [&](int64_t ct) {
+            if (K32 && overflow) return;   // the tile goes to the full-key search anyway
             const float* clo = a.tlo + ct * MP;
             const float* chi = a.thi + ct * MP;
             bool need = valid;
@@ -1006,9 +1055,17 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
                     }
                     lb = acc;
                 }
-                need = __float_as_uint(__fmul_rd(lb, a.lb_factor)) <= (uint32_t)(maxkey >> 32);
+                need = __float_as_uint(__fmul_rd(lb, a.lb_factor)) <= KO::dist_hi(maxkey);
             }
             if (!__syncthreads_or(need)) return;
+            int vis = 0;   // compact keys: this visit's number (read by all threads between barriers)
+            if constexpr (K32) {
+                vis = s_nvis;
+                if (vis >= VMAX) {
+                    overflow = true;
+                    return;
+                }
+            }
             staged += t == 0;
             {
                 const float4* src = (const float4*)(a.xs + ct * TILE * MP);
@@ -1016,6 +1073,12 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
                 for (int i = t; i < TILE * MP / 4; i += TILE) dst[i] = src[i];
             }
             __syncthreads();
+            if constexpr (K32) {
+                if (t == 0) {   // read again only after the barriers that end this visit
+                    vtab[vis] = (int)ct;
+                    s_nvis = vis + 1;
+                }
+            }
             if (need) {
                 evaluated += TILE;
                 const int64_t c0 = ct * TILE;
@@ -1024,8 +1087,8 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
                 for (int cb = 0; cb < TILE; cb += IB) {
                     // distances of one batch; keys under the current threshold go to buf
                     int cnt = 0;
-                    const uint64_t thr = maxkey;
-                    const uint32_t thr_hi = (uint32_t)(thr >> 32);
+                    const KT thr = maxkey;
+                    const uint32_t thr_hi = KO::dist_hi(thr);
 #pragma unroll 4
                     for (int c = cb; c < cb + IB; ++c) {
                         float acc = 0.f;
@@ -1049,7 +1112,7 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
                         }
                         if (__float_as_uint(acc) <= thr_hi) {   // rare once the heap is full
                             const int64_t cp = c0 + c;
-                            const uint64_t key = ((uint64_t)__float_as_uint(acc) << 32) | (uint32_t)cp;
+                            const KT key = KO::make(__float_as_uint(acc), vis, c, cp);
                             if (key < thr && (whole || (cp != p && cp >= qlo && cp < qhi))) {
                                 buf[cnt * TILE + t] = key;
                                 ++cnt;
@@ -1058,7 +1121,7 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
                     }
                     rounds += cnt;
                     for (int b = 0; b < cnt; ++b) {
-                        const uint64_t key = buf[b * TILE + t];
+                        const KT key = buf[b * TILE + t];
                         if (fill < L) {   // first L keys: append, then order them in one pass
                             heap[fill * TILE + t] = key;
                             if (++fill == L) {
@@ -1074,7 +1137,7 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
                 }
             }
             // tile threshold = largest heap maximum among the tile's valid queries
-            uint32_t mine = valid ? (uint32_t)(maxkey >> 32) : 0u;
+            uint32_t mine = valid ? KO::dist_hi(maxkey) : 0u;
             uint32_t wmax = __reduce_max_sync(0xffffffffu, mine);
             if (lane == 0) sred[warp] = wmax;
             __syncthreads();
@@ -1142,8 +1205,11 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
         }
 
         // ---------------- a5: order the kept candidates, rescore in FP64, certify
-        const bool row_ok = !valid || finalize_row<MP>(a, heap, t, L, fill == L, p, qhi - qlo, 1, 0.f, levels);
-        if (rmode) {
+        bool row_ok = true;
+        if (valid && !(K32 && overflow))
+            row_ok = finalize_row<MP, TILE, KT>(a, heap, t, L, fill == L, p, qhi - qlo, 1, 0.f, levels, 0.f, 0.f, vtab);
+        if (K32 && overflow) row_ok = false;
+        if (rmode || K32) {
             // a row with fewer than k points inside its radius, or uncertified: redo the tile exactly
             if (__syncthreads_or(!row_ok) && t == 0 && atomicExch(&a.fail_flag[qt], 1) == 0) {
                 a.fail_list[atomicAdd(a.fail_count, 1)] = (int)qt;
@@ -2174,10 +2240,12 @@ __global__ void __launch_bounds__(FB_THREADS) knn_fallback_kernel(const float* _
 }
 
 // ------------------------------------------------------------------ host orchestration
-template <int MP>
+template <int MP, bool K32 = false>
 static size_t tile_smem(int L)
 {
-    return (size_t)L * TILE * 8 + IB * TILE * 8 + SCAP * 8 + TILE * MP * 4 + (MP > 16 ? TILE * MP * 4 : 0);
+    const size_t kb = K32 ? 4 : 8;
+    return (size_t)L * TILE * kb + IB * TILE * kb + SCAP * 8 + TILE * MP * 4 + (MP > 16 ? TILE * MP * 4 : 0) +
+           (K32 ? VMAX * sizeof(int) : 0);
 }
 
 template <int MP>
@@ -2264,38 +2332,38 @@ static vb_status launch_tcp(TileArgs a, cudaStream_t s)
     return last_launch();
 }
 
-template <int MP, int MR = MP>
+template <int MP, int MR = MP, bool K32 = false>
 static vb_status launch_tile_m(const TileArgs& a, cudaStream_t s)
 {
-    size_t sm = tile_smem<MP>(a.L);
+    size_t sm = tile_smem<MP, K32>(a.L);
     static bool attr_set[16] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (!attr_set[dev & 15]) {
-        if (cudaFuncSetAttribute(knn_tile_kernel<MP, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tile_smem<MP>(256)) != cudaSuccess ||
-            cudaFuncSetAttribute(knn_tile_kernel<MP, MR>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        if (cudaFuncSetAttribute(knn_tile_kernel<MP, MR, K32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tile_smem<MP, K32>(256)) != cudaSuccess ||
+            cudaFuncSetAttribute(knn_tile_kernel<MP, MR, K32>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
             return VB_ERR_CUDA;
         attr_set[dev & 15] = true;
     }
-    knn_tile_kernel<MP, MR><<<(unsigned)a.ntiles, TILE, sm, s>>>(a);
+    knn_tile_kernel<MP, MR, K32><<<(unsigned)a.ntiles, TILE, sm, s>>>(a);
     return last_launch();
 }
 
 // m <= 4: the distance loop reads only the m real coordinates of the 4-wide rows.
-template <int MP>
+template <int MP, bool K32 = false>
 static vb_status launch_tile(const TileArgs& a, cudaStream_t s)
 {
     if constexpr (MP == 4) {
         switch (a.m) {
-            case 1: return launch_tile_m<4, 1>(a, s);
-            case 2: return launch_tile_m<4, 2>(a, s);
-            case 3: return launch_tile_m<4, 3>(a, s);
-            default: return launch_tile_m<4, 4>(a, s);
+            case 1: return launch_tile_m<4, 1, K32>(a, s);
+            case 2: return launch_tile_m<4, 2, K32>(a, s);
+            case 3: return launch_tile_m<4, 3, K32>(a, s);
+            default: return launch_tile_m<4, 4, K32>(a, s);
         }
     }
-    return launch_tile_m<MP>(a, s);
+    return launch_tile_m<MP, MP, K32>(a, s);
 }
 
 vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_params* p, int32_t* nbr,
@@ -2462,6 +2530,27 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
         if (st != VB_OK) return st;
         // tiles the first pass could not settle: the exact FP32 search (seeded, no radius) on that list only
         a.r2 = nullptr;
+        a.work = w.fb_count + 2;
+        a.tile_list = w.fail_list;
+        a.tile_count = w.fb_count + 3;
+    } else if (p->heap_keys != VB_KEYS_FULL) {
+        // compact 32-bit heap keys first; tiles that overflow the visit table or have a row that
+        // fails the certificate are redone below with full keys
+        if (cudaMemsetAsync(w.fail_flag, 0, sizeof(int) * 2 * ntiles, s) != cudaSuccess) return VB_ERR_CUDA;
+        mark(ctx, VB_STAGE_KNN_TILE, 0);
+        a.fail_flag = w.fail_flag;
+        a.fail_list = w.fail_list;
+        a.fail_count = w.fb_count + 3;
+        launches += 1;
+        switch (mp) {
+            case 4: st = launch_tile<4, true>(a, s); break;
+            case 8: st = launch_tile<8, true>(a, s); break;
+            case 16: st = launch_tile<16, true>(a, s); break;
+            case 32: st = launch_tile<32, true>(a, s); break;
+            case 64: st = launch_tile<64, true>(a, s); break;
+            default: st = launch_tile<128, true>(a, s); break;
+        }
+        if (st != VB_OK) return st;
         a.work = w.fb_count + 2;
         a.tile_list = w.fail_list;
         a.tile_count = w.fb_count + 3;
