@@ -168,10 +168,10 @@ typedef struct {
                                 kernel centres its operands on the whole cloud, not on each query tile,
                                 so its 16-bit error band is wider: exact either way, but with BF16 many
                                 rows go back to the FP32 search */
-    int32_t heap_keys;       /* FP32 search (not radius-first): VB_KEYS_COMPACT (default: 32-bit heap
-                                keys, half the shared memory, first pass; tiles that need more than 255
-                                candidate-tile visits or fail the certificate are redone with full keys)
-                                or VB_KEYS_FULL (64-bit keys only) */
+    int32_t heap_keys;       /* FP32 search (not radius-first), m <= 16: VB_KEYS_COMPACT (default: 32-bit
+                                heap keys, half the shared memory, first pass; tiles that need more than
+                                255 candidate-tile visits or fail the certificate are redone with full
+                                keys) or VB_KEYS_FULL (64-bit keys only; always when m > 16) */
 } vb_knn_params;
 
 /* Launch-shape autotuner (a16).  Times vb_knn on the caller's input for every

@@ -2533,9 +2533,10 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
         a.work = w.fb_count + 2;
         a.tile_list = w.fail_list;
         a.tile_count = w.fb_count + 3;
-    } else if (p->heap_keys != VB_KEYS_FULL) {
+    } else if (p->heap_keys != VB_KEYS_FULL && mp <= 16) {
         // compact 32-bit heap keys first; tiles that overflow the visit table or have a row that
-        // fails the certificate are redone below with full keys
+        // fails the certificate are redone below with full keys (wide inputs, where the box bounds
+        // prune little and a query tile visits hundreds of tiles, keep full keys)
         if (cudaMemsetAsync(w.fail_flag, 0, sizeof(int) * 2 * ntiles, s) != cudaSuccess) return VB_ERR_CUDA;
         mark(ctx, VB_STAGE_KNN_TILE, 0);
         a.fail_flag = w.fail_flag;
