@@ -636,10 +636,11 @@ struct TileArgs {
     uint64_t* hdump;            // pipelined search: heaps handed to its row finish ([L][128] per query tile)
 };
 
-constexpr int IB = 8;         // candidates per insertion batch
+constexpr int IB = 8;         // candidate distances computed per batch before any insertion
 constexpr int SCAP = 256;     // candidate tiles per sorted chunk
 constexpr int RUN = 8;        // longest run of FP32-indistinguishable neighbours ordered in registers
-constexpr int FB = 8;         // keys rescored per batch in the row finish
+constexpr int FB = 8;         // keys rescored per batch in the 16-bit row finish
+constexpr int FB_ROW = 4;     // the same in the FP32 row finish (fewer registers: more CTAs per SM)
 
 // Sift key down from node i of the max-heap heap[0..size) (column t of a [.][COLS] array).
 template <int COLS = TILE, class K>
@@ -714,19 +715,14 @@ __device__ __forceinline__ float point_box_lb(const float* q, const float* lo, c
 // sort the keys are walked in ascending order: FP64 canonical distances are
 // computed for the first k (plus the run straddling rank k), and keys whose FP32
 // distances lie within the error band of each other ("runs") are ordered exactly
-// by (d2, index) in registers.  Certificate: when `bound_mode` is 1 the largest
-// kept FP32 distance bounds every excluded candidate (heap search); when it is 2,
-// `bound` does (radius search).  The k-th FP64 distance must lie below the bound
-// minus the error band.  Returns false when the row needs the exact fallback.
-// e_lin, e_const: an absolute error bound E(d) = e_lin sqrt(d) + e_const of the
-// distances in the keys on top of the relative FP32 band (0 for FP32 distances;
-// the BF16 tensor-core distances need them).
+// by (d2, index) in registers.  Certificate: the largest kept FP32 distance bounds
+// every excluded candidate, and the k-th FP64 distance must lie below it minus the
+// relative FP32 error band.  Returns false when the row needs the exact fallback.
 // Compact keys (K = uint32_t) decode through vtab, the tile of every visit number, and carry
 // a distance bucket [lo, hi] instead of a value: runs and the certificate use its edges.
 template <int MP, int COLS = TILE, class K = uint64_t>
 __device__ bool finalize_row(const TileArgs& a, K* arr, int t, int size, bool is_heap, int64_t pq,
-                             int64_t ncl, int bound_mode, float bound, unsigned& levels, float e_lin = 0.f, float e_const = 0.f,
-                             const int* vtab = nullptr)
+                             int64_t ncl, unsigned& levels, const int* vtab = nullptr)
 {
     constexpr bool K32 = sizeof(K) == 4;
     constexpr K EMPTY = (K)~(K)0;
@@ -764,13 +760,13 @@ __device__ bool finalize_row(const TileArgs& a, K* arr, int t, int size, bool is
         }
         rlen = 0;
     };
-    // keys are taken FB at a time: their index and coordinate loads are issued together
-    for (int r0 = 0; r0 < size && !done; r0 += FB) {
-        uint32_t cpb[FB], ojb[FB];
-        uint64_t djb[FB];
-        float dfb[FB], dfh[FB];
+    // keys are taken FB_ROW at a time: their index and coordinate loads are issued together
+    for (int r0 = 0; r0 < size && !done; r0 += FB_ROW) {
+        uint32_t cpb[FB_ROW], ojb[FB_ROW];
+        uint64_t djb[FB_ROW];
+        float dfb[FB_ROW], dfh[FB_ROW];
 #pragma unroll
-        for (int u = 0; u < FB; ++u) {
+        for (int u = 0; u < FB_ROW; ++u) {
             const K key = r0 + u < size ? arr[(r0 + u) * COLS + t] : EMPTY;
             if constexpr (K32) {
                 const uint32_t slot = key & 0x3fffu, q = (key >> 14) << 13;
@@ -783,7 +779,7 @@ __device__ bool finalize_row(const TileArgs& a, K* arr, int t, int size, bool is
             }
         }
 #pragma unroll
-        for (int u = 0; u < FB; ++u) {
+        for (int u = 0; u < FB_ROW; ++u) {
             ojb[u] = 0;
             djb[u] = 0;
             if (cpb[u] != 0xffffffffu) {
@@ -795,14 +791,13 @@ __device__ bool finalize_row(const TileArgs& a, K* arr, int t, int size, bool is
             }
         }
 #pragma unroll
-        for (int u = 0; u < FB; ++u) {
+        for (int u = 0; u < FB_ROW; ++u) {
             if (done) break;
             if (cpb[u] == 0xffffffffu) { done = true; break; }   // empty slot or radius sentinel
             const float df = dfb[u];
-            // a new run starts once the distance clears the error band (tiny distances,
-            // where FP32 may have underflowed, all stay in one run)
-            const float gap = 2.02f * (e_lin * sqrtf(fmaxf(df, 0.f)) + e_const);
-            if (rlen > 0 && df > run_last * a.band + gap && df > 1e-30f) {
+            // a new run starts once the distance clears the error band (tiny distances, where
+            // FP32 may have underflowed, and overflowed ones all stay in one run)
+            if (rlen > 0 && df > run_last * a.band && df > 1e-30f && df <= 3.402823466e38f) {
                 emit();
                 if (out >= a.k) { done = true; break; }
             }
@@ -828,14 +823,11 @@ __device__ bool finalize_row(const TileArgs& a, K* arr, int t, int size, bool is
     if (ok && out < a.k) emit();
     if (!ok) { atomicAdd(&a.rep->knn_rows_long_run, 1ull); return false; }
     if (out < a.k) { atomicAdd(&a.rep->knn_rows_short, 1ull); return false; }
-    float B = bound;
-    if (bound_mode == 1) {
-        if (ncl - 1 <= (int64_t)size || Hkey == EMPTY) return true;   // every candidate was kept
-        if constexpr (K32) B = __uint_as_float((Hkey >> 14) << 13);   // lower edge of its bucket
-        else B = __uint_as_float((uint32_t)(Hkey >> 32));
-    }
-    const double Eb = 1.01 * ((double)e_lin * sqrt((double)fmaxf(B, 0.f)) + (double)e_const);
-    const bool cert = isfinite(B) && dk < ((double)B - Eb) * a.cert_factor - (double)a.m * 1.1754943508222875e-38;
+    if (ncl - 1 <= (int64_t)size || Hkey == EMPTY) return true;   // every candidate was kept
+    float B;
+    if constexpr (K32) B = __uint_as_float((Hkey >> 14) << 13);   // lower edge of its bucket
+    else B = __uint_as_float((uint32_t)(Hkey >> 32));
+    const bool cert = isfinite(B) && dk < (double)B * a.cert_factor - (double)a.m * 1.1754943508222875e-38;
     if (!cert) atomicAdd(&a.rep->knn_rows_uncertified, 1ull);
     return cert;
 }
@@ -945,7 +937,6 @@ __device__ bool finalize_row_band(const TileArgs& a, uint64_t* arr, int t, int s
 // Query tiles are taken from a global counter by a persistent grid of 64-thread
 // CTAs, one query per thread.  Shared memory:
 //   heap  [L][64]  key  max-heap per query of keys (KeyOps: 64-bit full or 32-bit compact)
-//   buf   [IB][64] key  per-thread batch of keys that passed the heap threshold
 //   cand  [64][MP] f32  staged candidate tile
 //   qs    [MP][64] f32  query coordinates (MP > 16 only)
 //   slist [SCAP]   u64  surviving candidate tiles keyed (box lower bound bits << 32 | tile)
@@ -961,8 +952,7 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
     extern __shared__ __align__(16) unsigned char smem[];
     const int L = a.L;
     KT* heap = (KT*)smem;
-    KT* buf = heap + (size_t)L * TILE;
-    uint64_t* slist = (uint64_t*)(buf + IB * TILE);
+    uint64_t* slist = (uint64_t*)(heap + (size_t)L * TILE);
     float* cand = (float*)(slist + SCAP);
     float* qs = cand + TILE * MP;
     int* vtab = (int*)(qs + (MP > 16 ? TILE * MP : 0));
@@ -1085,12 +1075,13 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
                 // the whole candidate tile lies in this query's cloud and is not its own tile
                 const bool whole = ct != qt && c0 >= qlo && c0 + TILE <= qhi;
                 for (int cb = 0; cb < TILE; cb += IB) {
-                    // distances of one batch; keys under the current threshold go to buf
-                    int cnt = 0;
-                    const KT thr = maxkey;
-                    const uint32_t thr_hi = KO::dist_hi(thr);
-#pragma unroll 4
-                    for (int c = cb; c < cb + IB; ++c) {
+                    // distances of one batch, all computed before any key is stored: the shared-memory
+                    // loads of the batch are then free to overlap (a store to the heap could alias them)
+                    const uint32_t thr_hi = KO::dist_hi(maxkey);
+                    float dist[IB];
+#pragma unroll
+                    for (int u = 0; u < IB; ++u) {
+                        const int c = cb + u;
                         float acc = 0.f;
                         if constexpr (QREG) {
                             const float4* cv = (const float4*)(cand + c * MP);
@@ -1110,18 +1101,25 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
                                 acc = fmaf(d, d, acc);
                             }
                         }
-                        if (__float_as_uint(acc) <= thr_hi) {   // rare once the heap is full
-                            const int64_t cp = c0 + c;
-                            const KT key = KO::make(__float_as_uint(acc), vis, c, cp);
-                            if (key < thr && (whole || (cp != p && cp >= qlo && cp < qhi))) {
-                                buf[cnt * TILE + t] = key;
-                                ++cnt;
-                            }
-                        }
+                        dist[u] = acc;
                     }
-                    rounds += cnt;
-                    for (int b = 0; b < cnt; ++b) {
-                        const KT key = buf[b * TILE + t];
+                    unsigned pass = 0;
+#pragma unroll
+                    for (int u = 0; u < IB; ++u) pass |= (unsigned)(__float_as_uint(dist[u]) <= thr_hi) << u;
+                    // keys under the heap maximum go in one by one (rare once the heap is full); a key
+                    // at or above the current maximum cannot be among the L smallest
+                    while (pass) {
+                        const int u = __ffs(pass) - 1;
+                        pass &= pass - 1;
+                        float du = dist[0];
+#pragma unroll
+                        for (int v = 1; v < IB; ++v)
+                            if (v == u) du = dist[v];
+                        const int c = cb + u;
+                        const int64_t cp = c0 + c;
+                        const KT key = KO::make(__float_as_uint(du), vis, c, cp);
+                        if (!(key < maxkey) || !(whole || (cp != p && cp >= qlo && cp < qhi))) continue;
+                        ++rounds;
                         if (fill < L) {   // first L keys: append, then order them in one pass
                             heap[fill * TILE + t] = key;
                             if (++fill == L) {
@@ -1130,7 +1128,6 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
                             }
                             continue;
                         }
-                        if (key >= maxkey) continue;
                         sift_down(heap, t, 0, L, key, levels);   // replace the root
                         maxkey = heap[t];
                     }
@@ -1207,7 +1204,7 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
         // ---------------- a5: order the kept candidates, rescore in FP64, certify
         bool row_ok = true;
         if (valid && !(K32 && overflow))
-            row_ok = finalize_row<MP, TILE, KT>(a, heap, t, L, fill == L, p, qhi - qlo, 1, 0.f, levels, 0.f, 0.f, vtab);
+            row_ok = finalize_row<MP, TILE, KT>(a, heap, t, L, fill == L, p, qhi - qlo, levels, vtab);
         if (K32 && overflow) row_ok = false;
         if (rmode || K32) {
             // a row with fewer than k points inside its radius, or uncertified: redo the tile exactly
@@ -2244,7 +2241,7 @@ template <int MP, bool K32 = false>
 static size_t tile_smem(int L)
 {
     const size_t kb = K32 ? 4 : 8;
-    return (size_t)L * TILE * kb + IB * TILE * kb + SCAP * 8 + TILE * MP * 4 + (MP > 16 ? TILE * MP * 4 : 0) +
+    return (size_t)L * TILE * kb + SCAP * 8 + TILE * MP * 4 + (MP > 16 ? TILE * MP * 4 : 0) +
            (K32 ? VMAX * sizeof(int) : 0);
 }
 
