@@ -52,6 +52,8 @@ struct KnnWs {
     uint64_t* hdump;      // 16-bit search: npad x (k + max(margin, 32)) heap keys handed to the row finish
     float* tlo;           // ntiles * MP
     float* thi;
+    float* slo;           // ceil(ntiles / 64) * MP: boxes of super-tiles (64 consecutive tiles)
+    float* shi;
     int* fb_list;         // n
     int* fb_count;        // [0] fallback rows, [1] next query tile, [2] next failed tile, [3] failed tiles
     float* r2;            // n (radius search: squared radius bound per sorted point)
@@ -113,6 +115,8 @@ size_t knn_plan(Carve& c, int64_t n, int32_t m, const vb_knn_params* p, KnnWs* w
     }
     t.tlo = c.take<float>(ntiles * mp);
     t.thi = c.take<float>(ntiles * mp);
+    t.slo = c.take<float>((ntiles + TILE - 1) / TILE * mp);
+    t.shi = c.take<float>((ntiles + TILE - 1) / TILE * mp);
     t.fb_list = c.take<int>(n);
     t.fb_count = c.take<int>(8);
     t.r2 = c.take<float>(npad);
@@ -549,6 +553,31 @@ __global__ void tile_box_kernel(const float* __restrict__ xs, int64_t n, int64_t
     }
 }
 
+// Box of every super-tile of 64 consecutive tiles (the union of their boxes), one warp each:
+// a query tile skips a whole super-tile whose box lies beyond its threshold.
+__global__ void super_box_kernel(const float* __restrict__ tlo, const float* __restrict__ thi, int64_t ntiles, int mp,
+                                 float* slo, float* shi)
+{
+    const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= (ntiles + TILE - 1) / TILE) return;
+    const int64_t t0 = g * TILE + lane, t1 = t0 + 32;
+    for (int r = 0; r < mp; ++r) {
+        float lo = INFINITY, hi = -INFINITY;
+        if (t0 < ntiles) { lo = tlo[t0 * mp + r]; hi = thi[t0 * mp + r]; }
+        if (t1 < ntiles) { lo = fminf(lo, tlo[t1 * mp + r]); hi = fmaxf(hi, thi[t1 * mp + r]); }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) {
+            slo[g * mp + r] = lo;
+            shi[g * mp + r] = hi;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ a2-a5: the tiled search
 __device__ __forceinline__ double canon_d2(const float* a, const float* b, int m)
 {
@@ -602,6 +631,8 @@ struct TileArgs {
     const double* xs64;   // FP64 copies of xs (exact), for the FP64 rescoring
     const float* tlo;
     const float* thi;
+    const float* slo;     // boxes of super-tiles (64 consecutive tiles; FP32 search)
+    const float* shi;
     const uint32_t* perm;
     int64_t n;
     int64_t ntiles;
@@ -638,6 +669,7 @@ struct TileArgs {
 
 constexpr int IB = 8;         // candidate distances computed per batch before any insertion
 constexpr int SCAP = 256;     // candidate tiles per sorted chunk
+constexpr int FLAT_SUPERS = 16;   // up to this many super-tiles (64 tiles each) in range: one-level scan
 constexpr int RUN = 8;        // longest run of FP32-indistinguishable neighbours ordered in registers
 constexpr int FB = 8;         // keys rescored per batch in the 16-bit row finish
 constexpr int FB_ROW = 4;     // the same in the FP32 row finish (fewer registers: more CTAs per SM)
@@ -942,10 +974,12 @@ __device__ bool finalize_row_band(const TileArgs& a, uint64_t* arr, int t, int s
 //   slist [SCAP]   u64  surviving candidate tiles keyed (box lower bound bits << 32 | tile)
 //   vtab  [VMAX]   i32  compact keys: the candidate tile of every visit number
 // MR <= MP is the number of coordinates the distance loop reads (the rest are zero padding).
+// Up to 10 CTAs per SM for MP <= 8 (at most 102 registers a thread, 21.5 KB of shared memory at
+// k + M = 68 with compact keys), 8 for wider inputs, whose query and candidate rows need more.
 // With compact keys a query tile that needs more than VMAX visits, or has a row that fails the
 // certificate, is listed for the plain search with full keys (a second pass).
 template <int MP, int MR = MP, bool K32 = false>
-__global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
+__global__ void __launch_bounds__(TILE, MP <= 8 ? 10 : 8) knn_tile_kernel(TileArgs a)
 {
     using KO = KeyOps<K32>;
     using KT = typename KO::T;
@@ -1148,38 +1182,16 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
             int64_t ct = (sidx & 1) ? qt + s2 : qt - s2;
             if (ct >= ct_lo && ct < ct_hi) visit(ct);
         }
-        // every other tile whose box lower bound does not exceed the threshold, nearest first
-        for (int64_t c0 = ct_lo; c0 < ct_hi;) {
-            if (t == 0) s_cnt = 0;
-            __syncthreads();
-            for (; c0 < ct_hi; c0 += TILE) {
-                const int64_t ct = c0 + t;
-                bool keep = ct < ct_hi;
-                if (keep && !rmode) {
-                    const int64_t dct = ct - qt;
-                    keep = (dct > (a.nseed >> 1) || dct < -((a.nseed - 1) >> 1));   // not a seed tile
-                }
-                float lb = 0.f;
-                if (keep) {
-                    float acc = 0.f;
-                    for (int r = 0; r < MP; ++r) {
-                        float g = fmaxf(fmaxf(a.tlo[ct * MP + r] - sqhi[r], sqlo[r] - a.thi[ct * MP + r]), 0.f);
-                        acc = fmaf(g, g, acc);
-                    }
-                    lb = __fmul_rd(acc, a.lb_factor);
-                    keep = !a.prune || __float_as_uint(lb) <= thr_blk;
-                }
-                unsigned bal = __ballot_sync(0xffffffffu, keep);
-                if (lane == 0 && bal) sred[warp] = atomicAdd(&s_cnt, __popc(bal));
-                __syncwarp();
-                if (keep) slist[sred[warp] + __popc(bal & ((1u << lane) - 1u))] = ((uint64_t)__float_as_uint(lb) << 32) | (uint32_t)ct;
-                __syncthreads();
-                if (s_cnt > SCAP - TILE) { c0 += TILE; break; }
-            }
-            const int cnt = s_cnt;
+        // Every other tile whose box lower bound does not exceed the threshold, nearest first.
+        // Two levels: super-tiles (64 consecutive tiles) first, nearest first; a super-tile whose
+        // box lies beyond the threshold is skipped whole (its box contains every tile box, and the
+        // bound is monotone in the box, rounding included), otherwise its 64 tiles are bounded,
+        // gathered, sorted and visited.  slist[SCAP/2 ..) holds super-tiles, slist[0 .. SCAP/2) tiles
+        // (all of slist when the super-tiles are too few to be worth bounding).
+        auto sort_keys = [&](uint64_t* lst, int cnt) {   // ascending bitonic sort of lst[0..cnt)
             int P = 1;
             while (P < cnt) P <<= 1;
-            for (int i = cnt + t; i < P; i += TILE) slist[i] = ~0ull;
+            for (int i = cnt + t; i < P; i += TILE) lst[i] = ~0ull;
             __syncthreads();
             for (int size = 2; size <= P; size <<= 1) {
                 for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -1187,18 +1199,102 @@ __global__ void __launch_bounds__(TILE) knn_tile_kernel(TileArgs a)
                         int lo = 2 * i - (i & (stride - 1));
                         int hi = lo + stride;
                         bool up = (lo & size) == 0;
-                        uint64_t x = slist[lo], y = slist[hi];
-                        if ((x > y) == up) { slist[lo] = y; slist[hi] = x; }
+                        uint64_t x = lst[lo], y = lst[hi];
+                        if ((x > y) == up) { lst[lo] = y; lst[hi] = x; }
                     }
                     __syncthreads();
                 }
             }
-            for (int si = 0; si < cnt; ++si) {
-                const uint64_t e = slist[si];
-                if (a.prune && (uint32_t)(e >> 32) > thr_blk) break;   // sorted: the rest lie farther
-                visit((int64_t)(uint32_t)e);
-            }
+        };
+        // appends (bound, index) of the threads that keep theirs to lst at s_cnt
+        auto append = [&](uint64_t* lst, bool keep, float lb, int64_t idx) {
+            unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0 && bal) sred[warp] = atomicAdd(&s_cnt, __popc(bal));
+            __syncwarp();
+            if (keep) lst[sred[warp] + __popc(bal & ((1u << lane) - 1u))] = ((uint64_t)__float_as_uint(lb) << 32) | (uint32_t)idx;
             __syncthreads();
+        };
+        uint64_t* sup = slist + SCAP / 2;
+        const int64_t g_lo = ct_lo / TILE, g_hi = (ct_hi + TILE - 1) / TILE;
+        // few super-tiles (a small cloud): their tiles are scanned directly, in index order
+        const bool flat = g_hi - g_lo <= FLAT_SUPERS;
+        const int tcap = flat ? SCAP - TILE : SCAP / 2 - TILE;   // tiles gathered before a sort
+        for (int64_t g0 = g_lo; g0 < g_hi;) {
+            if (t == 0) s_cnt = 0;
+            __syncthreads();
+            int ng;
+            if (flat) {
+                ng = (int)(g_hi - g_lo);
+                g0 = g_hi;
+            } else {
+                for (; g0 < g_hi; g0 += TILE) {
+                    const int64_t g = g0 + t;
+                    bool keep = g < g_hi;
+                    float lb = 0.f;
+                    if (keep) {
+                        float acc = 0.f;
+                        for (int r = 0; r < MP; ++r) {
+                            float gp = fmaxf(fmaxf(a.slo[g * MP + r] - sqhi[r], sqlo[r] - a.shi[g * MP + r]), 0.f);
+                            acc = fmaf(gp, gp, acc);
+                        }
+                        lb = __fmul_rd(acc, a.lb_factor);
+                        keep = !a.prune || __float_as_uint(lb) <= thr_blk;
+                    }
+                    append(sup, keep, lb, g);
+                    if (s_cnt > SCAP / 2 - TILE) { g0 += TILE; break; }
+                }
+                ng = s_cnt;
+                sort_keys(sup, ng);
+                if (t == 0) s_cnt = 0;   // every thread has read it before the sort's barriers
+                __syncthreads();
+            }
+            // tiles of the kept super-tiles, nearest super-tile first, gathered until the list holds
+            // more than tcap, then sorted and visited nearest first
+            int gi = 0;
+            while (gi < ng) {
+                for (; gi < ng; ++gi) {
+                    int64_t g = g_lo + gi;
+                    if (!flat) {
+                        const uint64_t eg = sup[gi];
+                        if (a.prune && (uint32_t)(eg >> 32) > thr_blk) {   // sorted: the rest lie farther
+                            gi = ng;
+                            break;
+                        }
+                        g = (int64_t)(uint32_t)eg;
+                    }
+                    const int64_t ct = g * TILE + t;
+                    bool keep = ct >= ct_lo && ct < ct_hi;
+                    if (keep && !rmode) {
+                        const int64_t dct = ct - qt;
+                        keep = (dct > (a.nseed >> 1) || dct < -((a.nseed - 1) >> 1));   // not a seed tile
+                    }
+                    float lb = 0.f;
+                    if (keep) {
+                        float acc = 0.f;
+                        for (int r = 0; r < MP; ++r) {
+                            float gp = fmaxf(fmaxf(a.tlo[ct * MP + r] - sqhi[r], sqlo[r] - a.thi[ct * MP + r]), 0.f);
+                            acc = fmaf(gp, gp, acc);
+                        }
+                        lb = __fmul_rd(acc, a.lb_factor);
+                        keep = !a.prune || __float_as_uint(lb) <= thr_blk;
+                    }
+                    append(slist, keep, lb, ct);
+                    if (s_cnt > tcap) {
+                        ++gi;
+                        break;
+                    }
+                }
+                const int cnt = s_cnt;
+                sort_keys(slist, cnt);
+                for (int si = 0; si < cnt; ++si) {
+                    const uint64_t e = slist[si];
+                    if (a.prune && (uint32_t)(e >> 32) > thr_blk) break;
+                    visit((int64_t)(uint32_t)e);
+                }
+                __syncthreads();
+                if (t == 0) s_cnt = 0;
+                __syncthreads();
+            }
         }
 
         // ---------------- a5: order the kept candidates, rescore in FP64, certify
@@ -2426,12 +2522,14 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
     const uint32_t* perm = w.val[cur];
     gather_kernel<<<(unsigned)((npad * mp + 255) / 256), 256, 0, s>>>(x, perm, n, npad, m, mp, w.xs, w.xs64);
     tile_box_kernel<<<(unsigned)((ntiles * 32 + 255) / 256), 256, 0, s>>>(w.xs, n, ntiles, m, mp, w.tlo, w.thi);
+    super_box_kernel<<<(unsigned)(((ntiles + TILE - 1) / TILE * 32 + 255) / 256), 256, 0, s>>>(w.tlo, w.thi, ntiles, mp,
+                                                                                              w.slo, w.shi);
     vb_status st = last_launch();
     if (st != VB_OK) return st;
     mark(ctx, VB_STAGE_KNN_ORDER, 1);
 
     TileArgs a = {};
-    a.xs = w.xs; a.xs64 = w.xs64; a.hdump = w.hdump; a.tlo = w.tlo; a.thi = w.thi; a.perm = perm; a.n = n; a.ntiles = ntiles;
+    a.xs = w.xs; a.xs64 = w.xs64; a.hdump = w.hdump; a.tlo = w.tlo; a.thi = w.thi; a.slo = w.slo; a.shi = w.shi; a.perm = perm; a.n = n; a.ntiles = ntiles;
     a.m = m; a.k = p->k; a.L = p->k + p->margin; a.prune = p->prune != VB_PRUNE_NONE;
     // enough neighbouring tiles to fill every heap, unless the caller (the autotuner) chose
     a.nseed = p->seed_tiles > 0 ? 1 + 2 * p->seed_tiles : 1 + 2 * (int)((a.L + TILE) / TILE);
@@ -2569,7 +2667,7 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
     ctx->launches += launches;
     knn_fallback_kernel<<<152, FB_THREADS, 0, s>>>(x, n, m, p->k, w.fb_list, w.fb_count, cl, nbr, nbr_d2);
     mark(ctx, VB_STAGE_KNN_FALLBACK, 1);
-    ctx->launches += 7;   // order: bbox init, bbox, Morton keys, gather, boxes (radix passes counted above); search; fallback
+    ctx->launches += 8;   // order: bbox init, bbox, Morton keys, gather, boxes, super-tile boxes (radix passes counted above); search; fallback
     return last_launch();
 }
 

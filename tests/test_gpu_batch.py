@@ -124,6 +124,23 @@ def test_invalid_cloud_ptr_is_rejected(vb):
         b(x)
 
 
+def test_batch_with_a_large_cloud_starting_mid_tile(vb):
+    # the second cloud starts inside tile 46 and spans 1,094 tiles: its queries run the two-level
+    # (super-tile) scan over a tile range that is not aligned to super-tiles
+    from oracle import knn as OK
+    rng = np.random.default_rng(46)
+    x = np.concatenate([rng.standard_normal((3000, 3)), 3.0 + rng.uniform(-1.0, 1.0, (70000, 3))]).astype(np.float32)
+    ptr = [0, 3000, 73000]
+    out = vb.Builder(73000, 3, K, D, C, BETA, cloud_ptr=ptr)(_t(x))
+    torch.cuda.synchronize()
+    vb.raise_on_device_error()
+    nbr = out.nbr.cpu().numpy()
+    for b in range(2):
+        lo, hi = ptr[b], ptr[b + 1]
+        ref_nbr, _ = OK.knn(x[lo:hi], K)
+        assert np.array_equal(nbr[lo:hi] - lo, ref_nbr), f"cloud {b}: neighbour lists"
+
+
 def test_autotune_picks_a_shape_and_keeps_results(vb, batch):
     bt, builder, out = batch
     x = _t(bt.x)

@@ -79,6 +79,14 @@ def test_knn_circle_2k_and_vmf_50k(vb):
     _knn_case(vb, W.VMF_50K.sample(), 64)
 
 
+@pytest.mark.parametrize("prune", [True, False])
+def test_knn_two_level_scan_70k(vb, prune):
+    # 70,000 points are 1,094 tiles, 18 super-tiles of 64 tiles: more than the one-level scan
+    # takes, so query tiles bound super-tiles first (pruned) or gather them all (unpruned)
+    x = np.random.default_rng(70).uniform(-1.0, 1.0, (70000, 3)).astype(np.float32)
+    _knn_case(vb, x, 24, prune)
+
+
 def test_knn_torus_1m_sampled_rows(vb):
     x = W.TORUS_1M.sample()
     nbr, d2 = vb.knn(_t(x), 64)
