@@ -969,7 +969,7 @@ __device__ bool finalize_row_band(const TileArgs& a, uint64_t* arr, int t, int s
 // Query tiles are taken from a global counter by a persistent grid of 64-thread
 // CTAs, one query per thread.  Shared memory:
 //   heap  [L][64]  key  max-heap per query of keys (KeyOps: 64-bit full or 32-bit compact)
-//   cand  [64][MP] f32  staged candidate tile
+//   cand  [MP][64] f32  staged candidate tile, coordinate-major (MP <= 16; [64][MP] for wider inputs)
 //   qs    [MP][64] f32  query coordinates (MP > 16 only)
 //   slist [SCAP]   u64  surviving candidate tiles keyed (box lower bound bits << 32 | tile)
 //   vtab  [VMAX]   i32  compact keys: the candidate tile of every visit number
@@ -1092,9 +1092,21 @@ __global__ void __launch_bounds__(TILE, MP <= 8 ? 10 : 8) knn_tile_kernel(TileAr
             }
             staged += t == 0;
             {
-                const float4* src = (const float4*)(a.xs + ct * TILE * MP);
-                float4* dst = (float4*)cand;
-                for (int i = t; i < TILE * MP / 4; i += TILE) dst[i] = src[i];
+                if constexpr (QREG) {   // transposed: the distance loop reads one coordinate of four candidates
+                    const float4* src = (const float4*)(a.xs + (ct * TILE + t) * MP);
+#pragma unroll
+                    for (int r4 = 0; r4 < MP / 4; ++r4) {
+                        const float4 v = src[r4];
+                        cand[(4 * r4 + 0) * TILE + t] = v.x;
+                        cand[(4 * r4 + 1) * TILE + t] = v.y;
+                        cand[(4 * r4 + 2) * TILE + t] = v.z;
+                        cand[(4 * r4 + 3) * TILE + t] = v.w;
+                    }
+                } else {
+                    const float4* src = (const float4*)(a.xs + ct * TILE * MP);
+                    float4* dst = (float4*)cand;
+                    for (int i = t; i < TILE * MP / 4; i += TILE) dst[i] = src[i];
+                }
             }
             __syncthreads();
             if constexpr (K32) {
@@ -1113,29 +1125,39 @@ __global__ void __launch_bounds__(TILE, MP <= 8 ? 10 : 8) knn_tile_kernel(TileAr
                     // loads of the batch are then free to overlap (a store to the heap could alias them)
                     const uint32_t thr_hi = KO::dist_hi(maxkey);
                     float dist[IB];
+                    if constexpr (QREG) {
+                        // two candidates per packed FP32 instruction: d = x - q (the same square as
+                        // q - x under round-to-nearest), then d0^2 + d1^2 + ... with the rounding
+                        // sequence of the scalar form, so the distances are the same bits
+                        float2 acc[IB / 2];
 #pragma unroll
-                    for (int u = 0; u < IB; ++u) {
-                        const int c = cb + u;
-                        float acc = 0.f;
-                        if constexpr (QREG) {
-                            const float4* cv = (const float4*)(cand + c * MP);
+                        for (int r = 0; r < MR; ++r) {
+                            const float2 nq = make_float2(-qr[r], -qr[r]);
 #pragma unroll
-                            for (int r4 = 0; r4 < MP / 4; ++r4) {
-                                const float4 v = cv[r4];
-                                const float d0 = qr[4 * r4 + 0] - v.x, d1 = qr[4 * r4 + 1] - v.y;
-                                const float d2 = qr[4 * r4 + 2] - v.z, d3 = qr[4 * r4 + 3] - v.w;
-                                if (4 * r4 + 0 < MR) acc = fmaf(d0, d0, acc);
-                                if (4 * r4 + 1 < MR) acc = fmaf(d1, d1, acc);
-                                if (4 * r4 + 2 < MR) acc = fmaf(d2, d2, acc);
-                                if (4 * r4 + 3 < MR) acc = fmaf(d3, d3, acc);
+                            for (int h = 0; h < IB / 4; ++h) {
+                                const float4 v = *(const float4*)(cand + r * TILE + cb + 4 * h);
+                                const float2 d0 = __fadd2_rn(make_float2(v.x, v.y), nq);
+                                const float2 d1 = __fadd2_rn(make_float2(v.z, v.w), nq);
+                                acc[2 * h] = r == 0 ? __fmul2_rn(d0, d0) : __ffma2_rn(d0, d0, acc[2 * h]);
+                                acc[2 * h + 1] = r == 0 ? __fmul2_rn(d1, d1) : __ffma2_rn(d1, d1, acc[2 * h + 1]);
                             }
-                        } else {
+                        }
+#pragma unroll
+                        for (int j = 0; j < IB / 2; ++j) {
+                            dist[2 * j] = acc[j].x;
+                            dist[2 * j + 1] = acc[j].y;
+                        }
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < IB; ++u) {
+                            const int c = cb + u;
+                            float acc = 0.f;
                             for (int r = 0; r < MP; ++r) {
                                 float d = qs[r * TILE + t] - cand[c * MP + r];
                                 acc = fmaf(d, d, acc);
                             }
+                            dist[u] = acc;
                         }
-                        dist[u] = acc;
                     }
                     unsigned pass = 0;
 #pragma unroll
