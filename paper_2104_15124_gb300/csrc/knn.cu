@@ -966,6 +966,32 @@ __device__ bool finalize_row_band(const TileArgs& a, uint64_t* arr, int t, int s
     return cert;
 }
 
+// Appends key, for the threads whose keep is set, to lst at positions cnt, cnt + 1, ... in
+// thread order, and advances cnt (a register, the same in every thread) by the number kept in
+// the block.  One barrier.  The per-warp counts go to wc[par], and par alternates between calls:
+// a warp that runs ahead to the next call writes the other half while the others still read
+// this one, and cannot come back to this half before all of them pass the next barrier.  The
+// count is never read from shared memory after the barrier, so no warp can see a count that
+// another warp has already advanced (every warp takes the same branch on cnt).
+template <int NW>
+__device__ __forceinline__ void block_append(uint64_t* lst, int& cnt, bool keep, uint64_t key, int (*wc)[NW], int& par)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) wc[par][warp] = __popc(bal);
+    __syncthreads();
+    int off = cnt, tot = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const int c = wc[par][w];
+        if (w < warp) off += c;
+        tot += c;
+    }
+    if (keep) lst[off + __popc(bal & ((1u << lane) - 1u))] = key;
+    cnt += tot;
+    par ^= 1;
+}
+
 // Query tiles are taken from a global counter by a persistent grid of 64-thread
 // CTAs, one query per thread.  Shared memory:
 //   heap  [L][64]  key  max-heap per query of keys (KeyOps: 64-bit full or 32-bit compact)
@@ -992,7 +1018,9 @@ __global__ void __launch_bounds__(TILE, MP <= 8 ? 10 : 8) knn_tile_kernel(TileAr
     int* vtab = (int*)(qs + (MP > 16 ? TILE * MP : 0));
     __shared__ float sqlo[MP], sqhi[MP];
     __shared__ uint32_t sred[2];
-    __shared__ int s_tile, s_cnt, s_nvis;
+    __shared__ int s_tile, s_nvis;
+    __shared__ int s_wc[2][TILE / 32];   // block_append scratch
+    int apar = 0;
     __shared__ int64_t s_ct[2];
 
     constexpr bool QREG = MP <= 16;
@@ -1228,13 +1256,9 @@ __global__ void __launch_bounds__(TILE, MP <= 8 ? 10 : 8) knn_tile_kernel(TileAr
                 }
             }
         };
-        // appends (bound, index) of the threads that keep theirs to lst at s_cnt
-        auto append = [&](uint64_t* lst, bool keep, float lb, int64_t idx) {
-            unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (lane == 0 && bal) sred[warp] = atomicAdd(&s_cnt, __popc(bal));
-            __syncwarp();
-            if (keep) lst[sred[warp] + __popc(bal & ((1u << lane) - 1u))] = ((uint64_t)__float_as_uint(lb) << 32) | (uint32_t)idx;
-            __syncthreads();
+        // appends (bound, index) of the threads that keep theirs to lst at cnt
+        auto append = [&](uint64_t* lst, int& cnt, bool keep, float lb, int64_t idx) {
+            block_append<TILE / 32>(lst, cnt, keep, ((uint64_t)__float_as_uint(lb) << 32) | (uint32_t)idx, s_wc, apar);
         };
         uint64_t* sup = slist + SCAP / 2;
         const int64_t g_lo = ct_lo / TILE, g_hi = (ct_hi + TILE - 1) / TILE;
@@ -1242,9 +1266,7 @@ __global__ void __launch_bounds__(TILE, MP <= 8 ? 10 : 8) knn_tile_kernel(TileAr
         const bool flat = g_hi - g_lo <= FLAT_SUPERS;
         const int tcap = flat ? SCAP - TILE : SCAP / 2 - TILE;   // tiles gathered before a sort
         for (int64_t g0 = g_lo; g0 < g_hi;) {
-            if (t == 0) s_cnt = 0;
-            __syncthreads();
-            int ng;
+            int ng = 0;
             if (flat) {
                 ng = (int)(g_hi - g_lo);
                 g0 = g_hi;
@@ -1262,18 +1284,16 @@ __global__ void __launch_bounds__(TILE, MP <= 8 ? 10 : 8) knn_tile_kernel(TileAr
                         lb = __fmul_rd(acc, a.lb_factor);
                         keep = !a.prune || __float_as_uint(lb) <= thr_blk;
                     }
-                    append(sup, keep, lb, g);
-                    if (s_cnt > SCAP / 2 - TILE) { g0 += TILE; break; }
+                    append(sup, ng, keep, lb, g);
+                    if (ng > SCAP / 2 - TILE) { g0 += TILE; break; }
                 }
-                ng = s_cnt;
                 sort_keys(sup, ng);
-                if (t == 0) s_cnt = 0;   // every thread has read it before the sort's barriers
-                __syncthreads();
             }
             // tiles of the kept super-tiles, nearest super-tile first, gathered until the list holds
             // more than tcap, then sorted and visited nearest first
             int gi = 0;
             while (gi < ng) {
+                int cnt = 0;
                 for (; gi < ng; ++gi) {
                     int64_t g = g_lo + gi;
                     if (!flat) {
@@ -1300,21 +1320,18 @@ __global__ void __launch_bounds__(TILE, MP <= 8 ? 10 : 8) knn_tile_kernel(TileAr
                         lb = __fmul_rd(acc, a.lb_factor);
                         keep = !a.prune || __float_as_uint(lb) <= thr_blk;
                     }
-                    append(slist, keep, lb, ct);
-                    if (s_cnt > tcap) {
+                    append(slist, cnt, keep, lb, ct);
+                    if (cnt > tcap) {
                         ++gi;
                         break;
                     }
                 }
-                const int cnt = s_cnt;
                 sort_keys(slist, cnt);
                 for (int si = 0; si < cnt; ++si) {
                     const uint64_t e = slist[si];
                     if (a.prune && (uint32_t)(e >> 32) > thr_blk) break;
                     visit((int64_t)(uint32_t)e);
                 }
-                __syncthreads();
-                if (t == 0) s_cnt = 0;
                 __syncthreads();
             }
         }
@@ -1405,8 +1422,10 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
     uint64_t* slist = (uint64_t*)(sqb + TILE);                 // [SCAP]
     uint64_t* buf = slist + SCAP;                              // [C][T2] max-heaps
     __shared__ float sqlo[MP], sqhi[MP], scen[MP];
-    __shared__ uint32_t sred[4], soff[4];
-    __shared__ int s_tile, s_cnt, s_fail, s_abort;
+    __shared__ uint32_t sred[4];
+    __shared__ int s_tile, s_fail, s_abort;
+    __shared__ int s_wc[2][T2 / 32];   // block_append scratch
+    int apar = 0;
     __shared__ int64_t s_ct[2];
     __shared__ float s_amax[4];
     __shared__ __align__(8) uint64_t bar;
@@ -1614,8 +1633,7 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
             if (!visit(ct)) break;
         // every other tile whose box lower bound does not exceed the tile bound, nearest first
         for (int64_t c0 = ct_lo; c0 < ct_hi && !far && !s_abort;) {
-            if (t == 0) s_cnt = 0;
-            __syncthreads();
+            int cnt = 0;
             for (; c0 < ct_hi; c0 += T2) {
                 const int64_t ct = c0 + t;
                 bool keep = ct < ct_hi && (ct < s_lo || ct >= s_hi);
@@ -1629,16 +1647,9 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
                     lb = __fmul_rd(acc, a.lb_factor);
                     keep = __float_as_uint(lb) <= thr_blk;
                 }
-                const unsigned bal = __ballot_sync(0xffffffffu, keep);
-                if (lane == 0 && bal) soff[warp] = atomicAdd(&s_cnt, __popc(bal));
-                __syncwarp();
-                if (keep)
-                    slist[soff[warp] + __popc(bal & ((1u << lane) - 1u))] =
-                        ((uint64_t)__float_as_uint(lb) << 32) | (uint32_t)ct;
-                __syncthreads();
-                if (s_cnt > SCAP - T2) { c0 += T2; break; }
+                block_append<T2 / 32>(slist, cnt, keep, ((uint64_t)__float_as_uint(lb) << 32) | (uint32_t)ct, s_wc, apar);
+                if (cnt > SCAP - T2) { c0 += T2; break; }
             }
-            const int cnt = s_cnt;
             int P = 1;
             while (P < cnt) P <<= 1;
             for (int i = cnt + t; i < P; i += T2) slist[i] = ~0ull;
