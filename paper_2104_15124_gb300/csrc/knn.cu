@@ -1576,6 +1576,7 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
             tc::fence_after_sync();
             if (__syncthreads_or(!done)) {   // a bounded wait ran out: record it and stop
                 if (t == 0) { report_error(a.rep, VB_ERR_TIMEOUT); s_abort = 1; }
+                __syncthreads();   // every thread sees the flag before the loops test it
                 return false;
             }
             if (need) evaluated += TILE;
