@@ -14,7 +14,10 @@ Contents
              density, operator normalisations, symmetric operator L-hat),
              the dense all-pairs form of Algorithm 1 used as a pin, and the
              spectral solve of Sec. 3.1
-  analytic.py closed-form spectra and densities the oracle is pinned to
+  mlp.py     the learned radius network's forward and backward passes in FP64, for
+             the training-kernel pins
+  radius.py  the paper's delta_tol pattern (Algorithm 1, Sec. 4) and its per-grid-point
+             sweep, the next row after the kNN pattern
 
 Every function cites the passage (section, equation, algorithm) it follows.
 """
