@@ -91,7 +91,7 @@ vb_status vb_report_reset(vb_ctx* ctx);
 /* Measurement hooks (not part of the paper's method).  When enabled, every
  * stage below is bracketed by CUDA events on the context's stream, and the
  * host counts the kernel launches it enqueues. */
-#define VB_STAGE_KNN_ORDER       0   /* bounding box, Morton keys, radix sort, gather, tile boxes */
+#define VB_STAGE_KNN_ORDER       0   /* bounding box, Morton keys, radix sort, gather, tile and super-tile boxes */
 #define VB_STAGE_KNN_TILE        1   /* tiled FP32 search, FP64 rescoring and certificate */
 #define VB_STAGE_KNN_FALLBACK    2   /* exact FP64 selection of uncertified rows */
 #define VB_STAGE_GRAPH           3   /* symmetric union CSR */
@@ -117,8 +117,9 @@ vb_status vb_profile_read(vb_ctx* ctx, float* ms, int64_t* launches);
  * and neighbours are ordered by (d2, j): distance first, then smaller index.
  * The search stages the points in a Morton order (of the coordinates when
  * m <= 4, of the projections on the cloud's 5 leading principal axes when
- * m > 4), prunes 64-point tiles by bounding boxes (and, in the pipelined
- * 16-bit search, by balls about the box centres) and keeps the k + margin
+ * m > 4), prunes 64-point tiles by bounding boxes (in the FP32 search of a cloud
+ * of more than 1,024 tiles, boxes of 64-tile super-tiles first; in the pipelined
+ * 16-bit search, also balls about the box centres) and keeps the k + margin
  * nearest FP32 (or 16-bit) candidates per row;
  * an FP64 rescoring with a proven FP32 error bound certifies every row, and
  * rows that fail it are recomputed by an exact FP64 radix selection.  The
