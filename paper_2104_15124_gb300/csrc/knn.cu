@@ -855,7 +855,9 @@ __device__ bool finalize_row(const TileArgs& a, K* arr, int t, int size, bool is
     if (ok && out < a.k) emit();
     if (!ok) { atomicAdd(&a.rep->knn_rows_long_run, 1ull); return false; }
     if (out < a.k) { atomicAdd(&a.rep->knn_rows_short, 1ull); return false; }
-    if (ncl - 1 <= (int64_t)size || Hkey == EMPTY) return true;   // every candidate was kept
+    // every candidate was kept (a small cloud without a radius, or an unfilled heap); a radius
+    // excludes the candidates beyond it even in a small cloud, so the certificate decides there
+    if ((ncl - 1 <= (int64_t)size && !a.r2) || Hkey == EMPTY) return true;
     float B;
     if constexpr (K32) B = __uint_as_float((Hkey >> 14) << 13);   // lower edge of its bucket
     else B = __uint_as_float((uint32_t)(Hkey >> 32));
@@ -958,7 +960,9 @@ __device__ bool finalize_row_band(const TileArgs& a, uint64_t* arr, int t, int s
         }
     }
     if (out < k) { atomicAdd(&a.rep->knn_rows_short, 1ull); return false; }
-    if (ncl - 1 <= (int64_t)size || Hkey == ~0ull) return true;   // every candidate was kept
+    // every candidate was kept (a small cloud without a radius, or an unfilled heap); with a
+    // radius the candidates beyond it were never kept, so the certificate decides
+    if ((ncl - 1 <= (int64_t)size && !a.r2) || Hkey == ~0ull) return true;
     const double B = (double)__uint_as_float((uint32_t)(Hkey >> 32));
     const bool cert = isfinite(B) && dk < 4e8 &&
                       dk < (B - bd.E(qn, dk, B)) * a.cert_factor - (double)a.m * 1.1754943508222875e-38;

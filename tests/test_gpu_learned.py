@@ -91,6 +91,22 @@ def test_radius_search_exact_for_any_radius(vb, mode):
         assert rep["knn_retry_tiles"] == 0        # a loose radius only loosens the initial pruning
 
 
+@pytest.mark.parametrize("scale", [0.5, 1.0, 1.5])
+def test_radius_search_exact_in_a_cloud_smaller_than_the_heap(vb, scale):
+    # 20 points, k + margin = 24 slots: every candidate would fit in the heap, but the radius
+    # still excludes those beyond it, so a row is settled by its certificate against the radius
+    # (or redone by the exact search), never by counting the cloud
+    x = np.random.default_rng(11).standard_normal((20, 3)).astype(np.float32)
+    k = 8
+    ref_nbr, ref_d2 = OK.knn(x, k)
+    radius = (scale * np.sqrt(ref_d2[:, k - 1])).astype(np.float32)
+    nbr, d2 = vb.knn(_t(x), k, radius=_t(radius), inflate=1.0)
+    torch.cuda.synchronize()
+    vb.raise_on_device_error()
+    assert np.array_equal(nbr.cpu().numpy(), ref_nbr)
+    assert np.array_equal(d2.cpu().numpy(), ref_d2)
+
+
 def test_learned_radius_search_exact_and_prunes(vb):
     k = 64
     xt_train = _t(W.torus4(100000, 0.01, 103))
