@@ -18,6 +18,8 @@ Contents
              the training-kernel pins
   radius.py  the paper's delta_tol pattern (Algorithm 1, Sec. 4) and its per-grid-point
              sweep, the next row after the kNN pattern
+  evolve.py  one explicit step of the particle evolution of a time-dependent density
+             (Sec. 6): solve L_{1,psi} f = g, grad f by Sec. 3.2, move the samples
 
 Every function cites the passage (section, equation, algorithm) it follows.
 """
