@@ -7,17 +7,20 @@ synthetic workload whose coordinates are already resident in HBM, replayed
 from a CUDA graph recorded once per form.  Every form computes the same
 matrix (neighbour lists and L-hat bit for bit, asserted); the forms differ in
 how the kNN search gets there:
-  plain_fp32   exact heap search with FP32 ALU distance tiles
-  fp16_tc      FP16 distance tiles on the tensor cores (tcgen05.mma), FP64 rescoring
-  learned_fp32 / learned_fp16_tc  the same with each query's heap started at a
-               radius predicted by the learned network (trained beforehand, not timed)
-The JSON line's value is the fastest form; every form's time is listed, and
-plain_fp32 is the comparison the metric names.  Each form's kNN launch shape
-comes from the autotuner (run before timing).
+  plain_fp32        exact heap search with FP32 ALU distance tiles (the comparison the metric names)
+  fp16_tc, bf16_tc  16-bit distance tiles on the tensor cores (tcgen05.mma), FP64 rescoring
+  learned_*         the same with each query's heap started at a radius predicted by the
+                    learned network (trained beforehand on a separate draw, not timed)
+  const_radius_fp32 ablation of the learned part: one global radius for every point
+The JSON line's value is the workload's target form, the one its configuration
+names (learned radius + BF16 tiles on the 1M torus and the ellipsoid batch, BF16
+tiles on the sphere, FP16 tiles in R^100), and vs_plain_fp32 says how it compares
+with plain_fp32, whichever way it falls; every form's time is listed.  Each
+form's kNN launch shape comes from the autotuner (run before timing).
 
-Workloads (--workload): vmf_s2_50k (default: 50,000 points on S^2, vMF kappa 2,
-k = 64), torus_r4_1m (1,000,000 points on the flat torus in R^4, sigma 0.01,
-k = 64), gauss100_200k (200,000 points of a 5-dim Gaussian in R^100, k = 128),
+Workloads (--workload): torus_r4_1m (default: 1,000,000 points on the flat torus in
+R^4, sigma 0.01, k = 64), vmf_s2_50k (50,000 points on S^2, vMF kappa 2, k = 64),
+gauss100_200k (200,000 points of a 5-dim Gaussian in R^100, k = 128),
 ellipsoids_256 (256 clouds, n_b ~ U[2000, 40000], k = 32, one batched build).
 Between timed steps a 256 MiB buffer is written to flush the 129 MB L2.
 
@@ -51,6 +54,9 @@ N_SM = 152
 EX2_PER_ENTRY = 15       # the 57-point sweep: 15 ex2 per entry (squaring chains for the rest)
 
 BATCHED = {"ellipsoids_256": dict(n_clouds=256, n_lo=2000, n_hi=40000, seed=5, m=3, k=32, d=2, c=1.0, beta=-0.25)}
+# the form each workload's configuration names (mixed precision, plus the learned radius where named)
+TARGET = {"torus_r4_1m": "learned_bf16_tc", "vmf_s2_50k": "bf16_tc", "gauss100_200k": "fp16_tc",
+          "ellipsoids_256": "learned_bf16_tc"}
 
 
 def _args():
@@ -59,7 +65,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="vmf_s2_50k")
+    ap.add_argument("--workload", default="torus_r4_1m")
     ap.add_argument("--forms", default="")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
@@ -258,26 +264,72 @@ def _traffic(stage: str, form: str, workload: str):
     return rec["dram_bytes_per_launch"]
 
 
-def _fp16_distance_error(spec: Spec, nbr: np.ndarray, rows: int = 2000) -> dict:
-    """Relative error of the FP16 tile distance against FP64 on sampled neighbour pairs:
-    both points recentred on a shared centre (the query's) and rounded to FP16, the
-    distance formed in FP64 from the rounded operands (the FP32 accumulation adds
-    only rounding at the 1e-7 level)."""
-    rng = np.random.default_rng(0)
-    idx = rng.choice(spec.n, min(rows, spec.n), replace=False)
-    q = spec.x[idx].astype(np.float64)
-    errs = []
-    for j in range(0, nbr.shape[1], max(1, nbr.shape[1] // 8)):
-        c = spec.x[nbr[idx, j]].astype(np.float64)
-        cen = q + 0.5 * (rng.random(q.shape) - 0.5) * np.abs(q - c).max(axis=1, keepdims=True)
-        qh = (q - cen).astype(np.float16).astype(np.float64)
-        ch = (c - cen).astype(np.float16).astype(np.float64)
-        exact = ((q - c) ** 2).sum(1)
-        approx = (qh * qh).sum(1) + (ch * ch).sum(1) - 2 * (qh * ch).sum(1)
-        ok = exact > 0
-        errs.append(np.abs(approx[ok] - exact[ok]) / exact[ok])
-    e = np.concatenate(errs)
-    return {"max_rel": float(e.max()), "rms_rel": float(np.sqrt((e * e).mean())), "pairs": int(e.size)}
+def _train_radius(vb, spec: Spec, a, dev):
+    """The learned radius (trained once, not timed) on a separate draw of about a.train_n points of
+    the same law, on that draw's exact distances to its k'-th neighbour, k' = k n_train / n (the
+    distance to the k-th neighbour at the timed size, whatever the cloud's effective dimension);
+    the spread of the residual on the training set sets the inflation (3 sigma).  A batch of
+    clouds trains on a separate batch, each target shifted by (1/d) ln(n_b / n_ref) so that clouds
+    of every size share one network, and the timed build adds (1/d) ln(n_ref / n_b) per cloud.
+    Also returns the constant-radius ablation: one global radius for every point, the training
+    targets' mean inflated by 3 standard deviations."""
+    import torch
+    from paper_2104_15124_gb300 import workloads as W
+    if spec.cloud_ptr is None:
+        w = spec.w
+        kp = max(1, int(round(spec.k * a.train_n / spec.n)))
+        xtr = torch.from_numpy(W.Workload(w.name, a.train_n, w.m, w.k, w.d, w.c, w.beta, w.margin, 103).sample()).to(dev)
+        _, d2tr = vb.knn(xtr, kp)
+        target = 0.5 * torch.log(d2tr[:, kp - 1]).float()
+        cloud_shift = None
+        what = f"log distance to neighbour k'={kp} of a {a.train_n}-point draw"
+    else:
+        b = BATCHED[spec.name]
+        n_ref = 0.5 * (b["n_lo"] + b["n_hi"])
+        ntr = max(1, int(round(a.train_n / n_ref)))
+        bt = W.ellipsoids(ntr, b["n_lo"], b["n_hi"], b["seed"] + 100)
+        xtr = torch.from_numpy(bt.x).to(dev)
+        parts = []
+        for c in range(ntr):
+            lo, hi = int(bt.cloud_ptr[c]), int(bt.cloud_ptr[c + 1])
+            _, d2c = vb.knn(xtr[lo:hi].contiguous(), spec.k)
+            parts.append(0.5 * torch.log(d2c[:, spec.k - 1]) + math.log((hi - lo) / n_ref) / spec.d)
+        target = torch.cat(parts).float()
+        sizes = np.diff(spec.cloud_ptr).astype(np.float64)
+        cloud_shift = (np.log(n_ref / sizes) / spec.d).astype(np.float32)
+        what = f"log distance to neighbour k={spec.k} in its own cloud, {ntr} training clouds, size-normalised"
+    net = vb.train_radius_model(xtr, target, epochs=a.train_epochs, batch=4096, seed=103)
+    resid = (target - net.predict(xtr)).float()
+    shift = float(resid.mean())
+    infl = math.exp(3.0 * float(resid.std()))
+    const = math.exp(float(target.mean()) + 3.0 * float(target.std()))
+    const_r = torch.full((spec.n,), const, dtype=torch.float32, device=dev)
+    note = {"train_points": int(xtr.shape[0]), "target": what, "epochs": a.train_epochs, "log_shift": shift,
+            "inflate": infl, "const_radius": const, "resid_std": float(resid.std()), "target_std": float(target.std())}
+    return net, shift, infl, cloud_shift, const_r, note
+
+
+def _tile_distance_error(vb, spec: Spec, xt, fmt: str) -> dict:
+    """Relative error of the 16-bit tile distances the search kernel itself produced, against
+    FP64: one vb_knn call with the diagnostic output on returns, for every row, the candidates
+    its search kept and their tile distances before the FP64 rescoring; the exact squared
+    distances of the same pairs come from the FP64 coordinates (for a batch: its first cloud)."""
+    import torch
+    x = xt
+    if spec.cloud_ptr is not None:
+        x = xt[: int(spec.cloud_ptr[1])].contiguous()
+    nbr, _, idx, d16 = vb.knn(x, spec.k, tensor_cores=fmt, debug=True)
+    ok = idx >= 0
+    rows = torch.arange(x.shape[0], device=x.device)[:, None].expand_as(idx)[ok]
+    cols = idx[ok].long()
+    x64 = x.double()
+    d64 = ((x64[rows] - x64[cols]) ** 2).sum(1)
+    dt = d16[ok].double()
+    pos = d64 > 0
+    rel = (dt[pos] - d64[pos]).abs() / d64[pos]
+    return {"max_rel": float(rel.max()), "rms_rel": float(rel.pow(2).mean().sqrt()), "pairs": int(rel.numel()),
+            "what": f"every kept candidate of every row ({'first cloud' if spec.cloud_ptr is not None else 'all rows'})"
+                    f", {fmt} tile distance vs FP64"}
 
 
 def main():
@@ -306,35 +358,29 @@ def main():
 
     # ---------------- forms
     batched = spec.cloud_ptr is not None
-    forms = ["plain_fp32", "fp16_tc"] + (["learned_fp32", "learned_fp16_tc"] if not batched and spec.m <= 16 else [])
+    lowdim = spec.m <= 16
+    forms = ["plain_fp32", "fp16_tc", "bf16_tc"]
+    if lowdim:
+        forms += ["learned_bf16_tc"] if batched else ["learned_fp32", "learned_fp16_tc", "learned_bf16_tc",
+                                                      "const_radius_fp32"]
+    target = TARGET.get(spec.name, "plain_fp32")
     if a.forms:
-        forms = ["plain_fp32"] + [f for f in forms if f in a.forms.split(",") and f != "plain_fp32"]
-    net, shift, infl = None, 0.0, 1.5
-    if any(f.startswith("learned") for f in forms):
-        # The learned radius: trained once (not timed) on a separate 100k-point draw of the same law,
-        # on that run's exact distances to its k'-th neighbour, k' = k * n_train / n (at the scale of
-        # the timed workload, whatever the cloud's effective dimension); the spread of its residual on
-        # the training set sets the inflation (3 sigma).
-        from paper_2104_15124_gb300 import workloads as W
-        w = spec.w
-        kp = max(1, int(round(spec.k * a.train_n / spec.n)))
-        wt = W.Workload(w.name, a.train_n, w.m, w.k, w.d, w.c, w.beta, w.margin, 103)
-        xtr = torch.from_numpy(wt.sample()).to(dev)
-        _, d2tr = vb.knn(xtr, kp)
-        target = 0.5 * torch.log(d2tr[:, kp - 1]).float()
-        net = vb.train_radius_model(xtr, target, epochs=a.train_epochs, batch=4096, seed=103)
-        resid = (target - net.predict(xtr)).float()
-        shift = float(resid.mean())
-        infl = math.exp(3.0 * float(resid.std()))
-        train_note = {"train_points": a.train_n, "target": f"log distance to neighbour k'={kp}", "epochs": a.train_epochs,
-                      "log_shift": shift, "inflate": infl}
+        keep = set(a.forms.split(",")) | {"plain_fp32", target}
+        forms = [f for f in forms if f in keep]
+    net, shift, infl, cloud_shift, const_r = None, 0.0, 1.5, None, None
+    if any(f.startswith("learned") or f.startswith("const") for f in forms):
+        net, shift, infl, cloud_shift, const_r, train_note = _train_radius(vb, spec, a, dev)
 
     def make(form):
         kw = dict(device=dev, cloud_ptr=spec.cloud_ptr)
-        if form.endswith("fp16_tc"):
+        if "fp16_tc" in form:
             kw["tensor_cores"] = "fp16"
+        elif "bf16_tc" in form:
+            kw["tensor_cores"] = "bf16"
         if form.startswith("learned"):
-            kw.update(mlp=net, log_shift=shift, inflate=infl)
+            kw.update(mlp=net, log_shift=shift, inflate=infl, cloud_log_shift=cloud_shift)
+        elif form.startswith("const"):
+            kw.update(radius=const_r, inflate=1.0)
         return vb.Builder(spec.n, spec.m, spec.k, d=spec.d, c=spec.c, beta=spec.beta, **kw)
 
     builders = {f: make(f) for f in forms}
@@ -387,7 +433,7 @@ def main():
     for f, b in builders.items():   # every form: the same matrix, bit for bit
         assert torch.equal(b.out.nbr, ref.nbr), f
         assert torch.equal(b.out.val[:nnz], ref.val[:nnz]), f
-    best = min(forms, key=lambda f: res[f]["total_s"])
+    best = target if target in res else "plain_fp32"   # the headline: the configuration's named form
     r0 = res[best]
     builder = builders[best]
     total_s = r0["total_s"]
@@ -443,12 +489,12 @@ def main():
             return {"bound": "alu", "unit": "Gentries/s", "achieved": ach, "peak": peak, "frac": ach / peak,
                     "what": f"{G} kernel values per off-diagonal entry, {EX2_PER_ENTRY} ex2 on the SFU "
                             f"({N_SM} SM x {SFU_PER_SM_CLK}/clk x {f_mhz:.0f} MHz / {EX2_PER_ENTRY})"}
-        if stage == "knn_tile" and best.endswith("fp16_tc"):
+        if stage == "knn_tile" and best.endswith("_tc"):
             ach = cand * 2 * spec.m / s / 1e12
             return {"bound": "tensor", "unit": "TFLOP/s", "achieved": ach, "peak": tensor_tflops,
                     "frac": ach / tensor_tflops,
                     "what": f"{int(cand)} candidate pairs x 2 m (m = {spec.m}; the MMA runs K = {KP}) FLOP of "
-                            f"FP16 tcgen05.mma; peak = dense bf16 {src} (FP16 rate equal)"}
+                            f"16-bit tcgen05.mma; peak = dense bf16 {src} (FP16 rate equal)"}
         if stage == "knn_tile":
             ach = cand * (3 * spec.m + 2) / s / 1e9
             peak = N_SM * FP32_PER_SM_CLK * f_mhz * 1e6 / 1e9
@@ -473,12 +519,15 @@ def main():
     droof["kernel"] = dom
     droof["traffic"] = _traffic(dom, best, spec.name)
 
+    sizes = np.diff(spec.cloud_ptr) if batched else np.array([spec.n])
+    pairs_all = float(np.sum(sizes.astype(np.float64) * (sizes - 1)))
     cfg = dict(spec.config)
     cfg.update({"form": best, "nnz": nnz, "l2": "flushed between steps (256 MiB write)",
                 "parallelism": f"replicas x{ws}", "timing": "CUDA-graph replay of the whole build per step"})
     line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * total_s / a.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+            "vs_baseline": None, "dtype": {"bf16": "bf16+f32", "fp16": "f16+f32"}.get(best.split("_")[-2], "f32"),
+            "data": "synthetic", "config": cfg,
             "forms": {f: {"ms_per_step": 1e3 * res[f]["total_s"] / a.steps,
                           "points_per_s": job_throughput(spec.n, a.steps, ws, res[f]["total_s"]),
                           "knn_ms": round(res[f]["stage_ms"].get("knn_tile", 0.0), 4),
@@ -487,11 +536,19 @@ def main():
                           "knn_fallback_rows": res[f]["rep"]["knn_fallback_rows"] // steps_prof,
                           "autotuned": {kk: v for kk, v in shapes[f].items() if kk != "knn_ms"}} for f in forms},
             "vs_plain_fp32": res["plain_fp32"]["total_s"] / total_s,
+            "comparison": {"target_form": best, "target_points_per_s": value,
+                           "plain_fp32_points_per_s": job_throughput(spec.n, a.steps, ws, res["plain_fp32"]["total_s"]),
+                           "target_over_plain": res["plain_fp32"]["total_s"] / total_s},
             "e2e": {"value": job_throughput(spec.n, a.steps, ws, e2e_s), "unit": "points/s", "h2d_bytes_per_step": int(spec.x.nbytes),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s / a.steps},
             "gpu_launches": int(r0["launches"] * a.steps), "roofline": droof, "kernels": kernels,
             "knn": {"candidate_pairs_per_step": int(cand),
                     "candidate_pairs_per_s": cand / (stage_ms["knn_tile"] / 1e3) if "knn_tile" in stage_ms else None,
+                    "n2_equivalent_pairs_per_s": (pairs_all / ((stage_ms.get("knn_order", 0.0) + stage_ms["knn_tile"]
+                                                               + stage_ms.get("knn_fallback", 0.0)) / 1e3)
+                                                  if "knn_tile" in stage_ms else None),
+                    "n2_equivalent_note": "n (n - 1) pairs (per cloud, summed) over the whole kNN stage time: the "
+                                          "rate a brute-force search would need, not pairs evaluated",
                     "heap_levels_per_step": rep["knn_heap_levels"] // steps_prof,
                     "insert_rounds_per_step": rep["knn_insert_rounds"] // steps_prof,
                     "tiles_staged_per_step": rep["knn_tiles_staged"] // steps_prof},
@@ -500,8 +557,8 @@ def main():
         line["learned_radius"] = train_note
     if rank == 0 and not batched and spec.m <= 16:
         line["gradient"] = _gradient_timing(vb, ref, xt, peaks, src)
-    if "fp16_tc" in forms:
-        line["fp16_distance_error"] = _fp16_distance_error(spec, ref.nbr.cpu().numpy())
+    line["tile_distance_error"] = {fmt: _tile_distance_error(vb, spec, xt, fmt) for fmt in ("fp16", "bf16")
+                                   if f"{fmt}_tc" in forms}
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         v, dt, what = _oracle_points_per_s(spec)
         line["cpu_baseline"] = {"value": v, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",

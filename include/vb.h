@@ -126,8 +126,8 @@ vb_status vb_profile_read(vb_ctx* ctx, float* ms, int64_t* launches);
  * output is therefore exact, identical to a brute-force FP64 search. */
 
 #define VB_PREC_FP32 0      /* FP32 ALU distances */
-#define VB_PREC_BF16 1      /* BF16 tensor-core distance tiles (tcgen05.mma, FP32 accumulation) with FP64 rescoring;
-                               radius-first search (VB_PRUNE_LEARNED) only */
+#define VB_PREC_BF16 1      /* BF16 tensor-core distance tiles (tcgen05.mma, FP32 accumulation) with FP64 rescoring
+                               (the staged kernel, operands recentred on every query tile) */
 #define VB_PREC_FP16 2      /* the same with FP16 tiles (11-bit significand: an 8x narrower error band) */
 #define VB_PRUNE_NONE    0  /* visit every candidate tile (brute force) */
 #define VB_PRUNE_EXACT   1  /* skip tiles whose box distance exceeds the running k+margin-th distance */
@@ -173,6 +173,11 @@ typedef struct {
                                 heap keys, half the shared memory, first pass; tiles that need more than
                                 255 candidate-tile visits or fail the certificate are redone with full
                                 keys) or VB_KEYS_FULL (64-bit keys only; always when m > 16) */
+    float* dbg_d2;           /* diagnostic (NULL = off), 16-bit searches: n x (k + margin) device floats; row i
+                                receives the 16-bit tile distances of the candidates its search kept, ascending,
+                                before the FP64 rescoring (the kernel's own tile arithmetic) */
+    int32_t* dbg_idx;        /* with dbg_d2: n x (k + margin) device int32, the original index of each of those
+                                candidates (-1 for an unused slot) */
 } vb_knn_params;
 
 /* Launch-shape autotuner (a16).  Times vb_knn on the caller's input for every
@@ -350,7 +355,10 @@ vb_status vb_spmv(vb_ctx* ctx, const vb_graph* g, const float* val, const double
  *     that loads the library holds it until the process exits.
  *   - The first call on each device resolves the array's device address
  *     (cudaGetSymbolAddress, with that device current) and caches it; make
- *     that first call before any stream capture.
+ *     that first call before any stream capture.  The cache is never
+ *     refreshed: after cudaDeviceReset() (or any teardown of the device's
+ *     primary context) the cached address is stale, so do not call this
+ *     entry point in a process that has reset the device.
  *   - All calls share the one array and it keeps the last call's contents.
  *     Nothing in it has to start at zero (each call overwrites every row it
  *     reads), but calls whose work can overlap on the GPU (several streams,
@@ -378,7 +386,8 @@ vb_status vb_spmv_laplacian_noalloc(void* stream, const vb_graph* g, const float
  * Returns VB_ERR_NOT_CONVERGED (outputs still written) when max_iter ran out. */
 typedef struct {
     int32_t ell;        /* nonzero eigenpairs wanted (ell + 1 are computed), ell >= 1 */
-    int32_t block;      /* subspace size, multiple of 32, <= 128 (0 = max(2 (ell + 1), ell + 17) rounded up) */
+    int32_t block;      /* subspace size, multiple of 32, <= 128 (0 = max(2 (ell + 1), ell + 17) rounded up to
+                           a multiple of 32, capped at 128 while ell <= 111) */
     int32_t degree;     /* Chebyshev filter degree per iteration (0 = 30) */
     int32_t max_iter;   /* outer iterations (0 = 60) */
     double tol;         /* stop once the wanted Ritz values move by < tol * max |lambda_j| twice (0 = 1e-7) */

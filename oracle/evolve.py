@@ -16,7 +16,7 @@ Each step therefore runs the whole method of this package on the current samples
   4. the update above.  The Gaussian increments W are inputs (the caller draws them), so
      the step is a deterministic function of its arguments.
 
-Readings (also listed in the design doc):
+Readings of the paper this module takes:
   R14 g is centred on the samples, g - mean(g) (the paper's g = g' - g-bar with the sample
       mean for the expectation under psi(.; t)).
   R15 the kernel's diagonal scales the eigenvalues by (1 - self weight); the solve divides

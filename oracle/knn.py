@@ -3,6 +3,11 @@
 `knn` calls the plain C brute force in knn_bf.c (compiled by `build()` with
 -ffp-contract=off, OpenMP over rows).  `knn_dense` is an independent numpy
 brute force over the full distance matrix, used to pin the C code on small n.
+`knn_large` returns the same lists at sizes where the brute force takes too
+long: a library primitive (scipy's k-d tree, or FP64 matrix products and a
+top-k) proposes candidates, the canonical distance ranks them, and rows whose
+k-th distance is not certified against the candidates left out go to the brute
+force.
 
 Definition (Sec. 2.1, Eq. for b^2 and I(x, k)): the k nearest *other* samples,
 ordered by the canonical FP64 squared distance, ties broken by smaller index.
@@ -118,3 +123,68 @@ def knn_dense(x: np.ndarray, k: int):
         nbr[i] = j[order]
         out[i] = dj[order]
     return nbr, out
+
+
+def _certified_rows(x: np.ndarray, k: int, cand: np.ndarray, bound: np.ndarray):
+    """Exact lists from candidate sets: the canonical FP64 distances of every row's
+    candidates (cand [n, c], c > k, any order), sorted by (d2, j); a row is certified
+    when its k-th canonical distance lies below `bound` (a lower bound on the canonical
+    distance of every point outside its candidate set).  Rows that are not certified,
+    or whose candidates include the point itself fewer or more than once, are
+    recomputed by the brute force."""
+    n = x.shape[0]
+    rows = np.repeat(np.arange(n, dtype=np.int64), cand.shape[1])
+    d2 = pair_d2(x, rows, cand.ravel().astype(np.int64)).reshape(cand.shape)
+    own = cand == np.arange(n)[:, None]
+    d2 = np.where(own, np.inf, d2)
+    order = np.lexsort((cand, d2), axis=1)[:, :k]
+    nbr = np.take_along_axis(cand, order, axis=1).astype(np.int32)
+    out = np.take_along_axis(d2, order, axis=1)
+    bad = (out[:, k - 1] >= bound) | (own.sum(axis=1) != 1)
+    if bad.any():
+        r = np.nonzero(bad)[0]
+        nbr[r], out[r] = knn_rows(x, k, r)
+    return nbr, out, int(bad.sum())
+
+
+def knn_large(x: np.ndarray, k: int, margin: int = 16, block: int = 2048):
+    """The same exact lists as knn() for large n, with library primitives choosing
+    candidates and the canonical FP64 distance deciding:
+      m <= 8: scipy's k-d tree (exact Euclidean k + margin + 1 nearest, self included);
+      m > 8:  FP64 |x|^2 + |y|^2 - 2 x.y by matrix products over row blocks, then the
+              k + margin + 1 smallest per row (torch.topk on the CPU).
+    Every kept row's k-th canonical distance must lie below a lower bound on the
+    canonical distance of every candidate left out (the (k + margin + 1)-th candidate's
+    distance, less a bound on the candidate distance's rounding error); other rows go
+    to the brute force.  Returns (nbr, nbr_d2, rows sent to the brute force)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    n, m = x.shape
+    c = min(n, k + margin + 1)
+    x64 = x.astype(np.float64)
+    if m <= 8:
+        from scipy.spatial import cKDTree
+        dist, cand = cKDTree(x64).query(x64, c, workers=-1)
+        # the tree's FP64 Euclidean distance is within a few ulps of the canonical one
+        bound = (dist[:, -1] ** 2) * (1.0 - 1e-12)
+        cand = cand[:, :-1] if c < n else cand
+        return _certified_rows(x, k, cand.astype(np.int64), bound if c < n else np.full(n, np.inf))
+    import torch
+    X = torch.from_numpy(x64)
+    XT = X.T.contiguous()
+    sq = (X * X).sum(1)
+    cand = np.empty((n, c), dtype=np.int64)
+    bound = np.empty(n)
+    # |y|^2 - 2 x.y ranks the candidates of row x like the squared distance; adding |x|^2
+    # gives a value within (m + 2) 2^-52 (|x| + |y|)^2 of the exact squared distance, and
+    # the canonical sum lies within m 2^-53 of that
+    nrm = sq.sqrt()
+    for r0 in range(0, n, block):
+        r1 = min(n, r0 + block)
+        D = torch.addmm(sq[None, :], X[r0:r1], XT, beta=1.0, alpha=-2.0)
+        v, i = torch.topk(D, c, dim=1, largest=False, sorted=True)
+        cand[r0:r1] = i.numpy()
+        err = (m + 3) * 2.0 ** -52 * (nrm[r0:r1] + nrm.max()) ** 2
+        bound[r0:r1] = (v[:, -1] + sq[r0:r1] - err).numpy() * (1.0 - 1e-12)
+    if c == n:
+        bound[:] = np.inf
+    return _certified_rows(x, k, cand[:, :-1] if c < n else cand, bound)

@@ -15,7 +15,7 @@ paper's order and notation:
   solve      f~ = Lambda^-1 g~, g~ = Q^T S^2 g / n, f = Q f~, Eqs. (LS minimiser, f_LS), Sec. 3.1
   gradient   grad u . grad v from the eigenpairs and C-hat_ljk = <phi_l, phi_j * phi_k>_S, Sec. 3.2
 
-Readings where the paper is silent or ambiguous (each also listed in the design doc):
+Readings where the paper is silent or ambiguous:
   R1 sparsity: the matrix lives on E = diagonal U kNN U kNN^T (no delta_tol drop).
   R2 self is excluded from the kNN lists and from b; k_bw = k unless given.
   R3 the diagonal (j = i) is part of every kernel sum, as in Algorithm 1 (j from i).
@@ -127,8 +127,10 @@ def sweep(p: Pattern, rho: np.ndarray, scale: float, xi: np.ndarray) -> Sweep:
     """Eq. (bandwidth sensitivity): chi_xi = sum_ij exp(-d2_ij / (scale 2^xi rho_i rho_j)),
     chi'_xi = (log chi_{xi+delta} - log chi_xi) / (delta log 2), maximised over the grid.
     scale = 1, rho = b gives the density sweep; scale = 4, rho = P the operator sweep (R6)."""
-    t = p.d2 / (scale * rho[p.row] * rho[p.col])
-    chi = np.array([np.sum(np.exp(-t / 2.0 ** xg)) for xg in xi])
+    import torch
+    t = torch.from_numpy(p.d2 / (scale * rho[p.row] * rho[p.col]))
+    # one FP64 sum per grid point; torch's CPU ops spread the exponentials over the host cores
+    chi = np.array([float(torch.exp(-t / 2.0 ** float(xg)).sum()) for xg in xi])
     delta = xi[1] - xi[0]
     chip = (np.log(chi[1:]) - np.log(chi[:-1])) / (delta * math.log(2.0))
     g = int(np.argmax(chip))

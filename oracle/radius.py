@@ -13,7 +13,7 @@ per-entry test; the pattern is that of the brute-force Algorithm 1.  Because the
 set depends on eps, a self-tuning sweep over eps_xi^2 = 2^xi has one pattern per grid
 point (Eq. (bandwidth sensitivity) summed over that pattern).
 
-Readings (also listed in the design doc):
+Readings of the paper this module takes:
   R11 the test exp(-t) > delta_tol is taken as t < tau with tau = -log(delta_tol)
       computed once in FP64 (exp is strictly decreasing, so the two agree up to the
       rounding of exp; the threshold form is the one two implementations can evaluate

@@ -47,7 +47,7 @@ c_i32, c_i64, c_f32, c_f64, c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_floa
 class KnnParams(ctypes.Structure):
     _fields_ = [("k", c_i32), ("margin", c_i32), ("precision", c_i32), ("prune", c_i32), ("radius", c_p),
                 ("mlp", c_p), ("radius_inflate", c_f32), ("radius_log_shift", c_f32), ("cloud_log_shift", c_p),
-                ("seed_tiles", c_i32), ("tc_variant", c_i32), ("heap_keys", c_i32)]
+                ("seed_tiles", c_i32), ("tc_variant", c_i32), ("heap_keys", c_i32), ("dbg_d2", c_p), ("dbg_idx", c_p)]
 
 
 class GraphC(ctypes.Structure):
@@ -257,12 +257,14 @@ class Graph:
 # ----------------------------------------------------------------------------- the calls
 def knn(x: torch.Tensor, k: int, margin: int = 16, prune: bool = True, radius: torch.Tensor | None = None,
         inflate: float = 0.0, mlp=None, log_shift: float = 0.0, tensor_cores: str | None = None,
-        tc_variant: str = "auto", seed_tiles: int = 0, heap_keys: str = "compact"):
+        tc_variant: str = "auto", seed_tiles: int = 0, heap_keys: str = "compact", debug: bool = False):
     """Exact kNN (vb_knn): returns (nbr int32 [n, k], nbr_d2 fp64 [n, k]).  With `radius` (per-point
     guess of the k-th neighbour distance) or a learned `mlp`, the radius-first search runs;
     tensor_cores = "fp16" or "bf16" computes its distance tiles on the tensor cores, with the
     kernel tc_variant = "auto", "staged" or "pipelined" (VB_TC_*); seed_tiles and heap_keys
-    ("compact" or "full") as in vb_knn_params."""
+    ("compact" or "full") as in vb_knn_params.  debug=True (16-bit tiles) also returns the
+    candidates each row kept and their 16-bit tile distances before rescoring:
+    (nbr, nbr_d2, dbg_idx int32 [n, k + margin], dbg_d2 fp32 [n, k + margin])."""
     n, m = x.shape
     dev = x.device
     mode = VB_PRUNE_LEARNED if (radius is not None or mlp is not None) else (VB_PRUNE_EXACT if prune else VB_PRUNE_NONE)
@@ -274,8 +276,14 @@ def knn(x: torch.Tensor, k: int, margin: int = 16, prune: bool = True, radius: t
     p.heap_keys = {"compact": VB_KEYS_COMPACT, "full": VB_KEYS_FULL}[heap_keys]
     nbr = torch.empty((n, k), dtype=torch.int32, device=dev)
     d2 = torch.empty((n, k), dtype=torch.float64, device=dev)
+    if debug:
+        dbg_idx = torch.full((n, k + margin), -1, dtype=torch.int32, device=dev)
+        dbg_d2 = torch.full((n, k + margin), float("nan"), dtype=torch.float32, device=dev)
+        p.dbg_idx, p.dbg_d2 = _p(dbg_idx), _p(dbg_d2)
     ws = _ws(lib().vb_knn_workspace(n, m, ctypes.byref(p)), dev)
     _check(lib().vb_knn(c_p(_ctx(dev)), _p(x), n, m, ctypes.byref(p), _p(nbr), _p(d2), _p(ws), ws.numel()), "vb_knn")
+    if debug:
+        return nbr, d2, dbg_idx, dbg_d2
     return nbr, d2
 
 
@@ -512,16 +520,20 @@ class Builder:
     With cloud_ptr (B + 1 offsets of the rows of each point cloud) it runs the
     batched build vb_build_batch: every per-cloud scalar output then holds B
     values (chi: B x G) and the CSR is block-diagonal.  cloud_log_shift (B floats)
-    adds a per-cloud term to a learned radius.  graph() records one build in a
-    CUDA graph for replay."""
+    adds a per-cloud term to a learned radius.  `radius` (n floats on the device,
+    original order) runs the radius-first search with a given guess of every
+    point's k-th neighbour distance instead of a learned one.  graph() records one
+    build in a CUDA graph for replay."""
 
     def __init__(self, n: int, m: int, k: int, d: float, c: float, beta: float = -0.25, margin: int = 16,
                  k_bw: int | None = None, prune: bool = True, device=None, grid=(XI_LO, XI_HI, DXI),
                  mlp: "Mlp | None" = None, log_shift: float = 0.0, inflate: float = 0.0,
-                 tensor_cores: str | None = None, cloud_ptr=None, cloud_log_shift=None):
+                 tensor_cores: str | None = None, cloud_ptr=None, cloud_log_shift=None,
+                 radius: torch.Tensor | None = None):
         dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.n, self.m, self.k, self.device = n, m, k, dev
         self.mlp = mlp   # kept alive: the C parameters point at it
+        self.radius = radius
         G = int(round((grid[1] - grid[0]) / grid[2])) + 1
         self.batched = cloud_ptr is not None
         if self.batched:
@@ -539,9 +551,12 @@ class Builder:
             self._shift = torch.as_tensor(np.asarray(cloud_log_shift, dtype=np.float32)).to(dev).contiguous()
             if self._shift.numel() != B:
                 raise ValueError("cloud_log_shift needs one value per cloud")
-        mode = VB_PRUNE_LEARNED if mlp is not None else (VB_PRUNE_EXACT if prune else VB_PRUNE_NONE)
+        if radius is not None and (radius.shape != (n,) or radius.dtype != torch.float32):
+            raise ValueError("radius must be float32 [n] (a guess of every point's k-th neighbour distance)")
+        mode = VB_PRUNE_LEARNED if (mlp is not None or radius is not None) else \
+            (VB_PRUNE_EXACT if prune else VB_PRUNE_NONE)
         prec = {None: VB_PREC_FP32, "bf16": VB_PREC_BF16, "fp16": VB_PREC_FP16}[tensor_cores]
-        self.params = BuildParams(KnnParams(k, margin, prec, mode, c_p(0),
+        self.params = BuildParams(KnnParams(k, margin, prec, mode, _p(radius),
                                             c_p(0) if mlp is None else c_p(mlp.handle()), inflate, log_shift,
                                             _p(self._shift)),
                                   0 if k_bw is None else k_bw, OpParams(c, beta, d), grid[0], grid[1], grid[2], 0)

@@ -665,6 +665,8 @@ struct TileArgs {
     uint4* lbs;                 // per CTA scratch: ntiles bounds of the four 32-query groups
     const float* trad;          // per tile: radius of its ball about the box centre (pipelined search)
     uint64_t* hdump;            // pipelined search: heaps handed to its row finish ([L][128] per query tile)
+    float* dbg_d2;              // diagnostic: kept 16-bit distances per row ([n][L], original order)
+    int32_t* dbg_idx;           // their original indices
 };
 
 constexpr int IB = 8;         // candidate distances computed per batch before any insertion
@@ -906,6 +908,14 @@ __device__ bool finalize_row_band(const TileArgs& a, uint64_t* arr, int t, int s
     }
     const uint64_t Hkey = arr[(size - 1) * COLS + t];
     const uint32_t oq = a.perm[pq];
+    if (a.dbg_d2) {   // diagnostic: the kept keys' 16-bit distances, ascending, before any rescoring
+        for (int r = 0; r < size && r < a.L; ++r) {
+            const uint64_t key = arr[r * COLS + t];
+            const uint32_t cp = (uint32_t)key;
+            a.dbg_idx[(int64_t)oq * a.L + r] = cp == 0xffffffffu ? -1 : (int32_t)a.perm[cp];
+            a.dbg_d2[(int64_t)oq * a.L + r] = __uint_as_float((uint32_t)(key >> 32));
+        }
+    }
     const double* qc = a.xs64 + pq * MP;
     int32_t* on = a.nbr + (int64_t)oq * a.k;
     double* od = a.nbr_d2 + (int64_t)oq * a.k;
@@ -2577,6 +2587,8 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
     a.nbr = nbr; a.nbr_d2 = nbr_d2; a.fb_list = w.fb_list; a.fb_count = w.fb_count; a.rep = ctx->rep;
     a.work = w.fb_count + 1;
     a.cl = cl;
+    a.dbg_d2 = p->dbg_idx ? p->dbg_d2 : nullptr;
+    a.dbg_idx = p->dbg_idx;
     const bool radius_first = p->prune == VB_PRUNE_LEARNED;
     const bool tensor = p->precision == VB_PREC_BF16 || p->precision == VB_PREC_FP16;
     int launches = 0;

@@ -308,6 +308,8 @@ static int solve_block(int ell, int block)
 {
     int B = block > 0 ? block : std::max(2 * (ell + 1), ell + 17);
     B = ((B + 31) / 32) * 32;
+    // the default stays within the 128-vector limit while it leaves 16 spare vectors
+    if (block <= 0 && B > 128 && ell + 17 <= 128) B = 128;
     return B;
 }
 constexpr int GRAM_BLOCKS = 152;
@@ -383,6 +385,10 @@ vb_status solve_run(Ctx* ctx, const vb_graph* g, int64_t cap, const float* val, 
     static bool gattr[16] = {};
     if (!gattr[ctx->device & 15]) {
         if (cudaFuncSetAttribute(gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * GRAM_ROWS * 128 * 4) !=
+            cudaSuccess)
+            return VB_ERR_CUDA;
+        // the rotation keeps the whole B x B matrix in shared memory: 64 KB at B = 128
+        if (cudaFuncSetAttribute(rotate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 4) !=
             cudaSuccess)
             return VB_ERR_CUDA;
         gattr[ctx->device & 15] = true;

@@ -86,6 +86,8 @@ extern "C" vb_status vb_knn_autotune(vb_ctx* ctx, const float* x, int64_t n, int
         for (int vs = 0; vs < nv * ns; ++vs) {
             const int vi = vs / ns, si = vs % ns;
             vb_knn_params q = *p;
+            q.dbg_d2 = nullptr;   // the diagnostic rows are sized for the caller's margin only
+            q.dbg_idx = nullptr;
             q.margin = mg;
             q.seed_tiles = seeds[si];
             if (!fp32) q.tc_variant = variants_tc[vi];
@@ -113,6 +115,8 @@ extern "C" vb_status vb_knn_autotune(vb_ctx* ctx, const float* x, int64_t n, int
     if (!(bms < INFINITY)) return VB_ERR_UNSUPPORTED;
     // leave the outputs holding the chosen shape's result (identical in any case: the search is exact)
     vb_knn_params q = *p;
+    q.dbg_d2 = nullptr;
+    q.dbg_idx = nullptr;
     q.margin = bs.margin;
     q.seed_tiles = bs.seed_tiles;
     q.tc_variant = bs.tc_variant;

@@ -88,3 +88,25 @@ def test_row_ranges_and_errors():
     # k = n - 1 returns every other point
     nbr, _ = K.knn(x[:12], 11)
     assert all(sorted(nbr[i]) == [j for j in range(12) if j != i] for i in range(12))
+
+
+@pytest.mark.parametrize("case", ["torus", "gauss100", "lattice_ties", "duplicates", "tiny"])
+def test_large_n_path_equals_bruteforce(case):
+    # the candidate-and-certificate path (k-d tree for m <= 8, FP64 matrix products for m > 8)
+    # must return the brute force's lists bit for bit, ties and duplicates included
+    from paper_2104_15124_gb300 import workloads as W
+    if case == "torus":
+        x, k = W.torus4(6000, 0.01, 3), 64
+    elif case == "gauss100":
+        x, k = W.gauss_embedded(3000, 5, 100, 1e-3, 4).x, 128
+    elif case == "lattice_ties":
+        g = np.stack(np.meshgrid(np.arange(30), np.arange(30), indexing="ij"), -1).reshape(-1, 2)
+        x, k = g.astype(np.float32), 12
+    elif case == "duplicates":
+        b = np.random.default_rng(4).standard_normal((400, 12)).astype(np.float32)
+        x, k = np.concatenate([b, b[:50], b[:50]]), 20
+    else:
+        x, k = np.random.default_rng(5).standard_normal((30, 3)).astype(np.float32), 29
+    nbr, d2 = K.knn(x, k)
+    a, b, _ = K.knn_large(x, k)
+    assert np.array_equal(a, nbr) and np.array_equal(b, d2)

@@ -177,3 +177,87 @@ def test_gaussian4d_spectrum_and_solve():
     # an eigenvector right-hand side is inverted exactly: g = phi_j  =>  f = phi_j / lambda_j
     f1 = M.spectral_solve(e, B.op.S, e.phi[:, 2])
     np.testing.assert_allclose(f1, e.phi[:, 2] / e.evals[2], rtol=1e-8, atol=1e-10)
+
+
+def test_operator_centre_worked_example():
+    # Three points on a line at 0, 1, 3 (squared distances 1, 9, 4 for the pairs (0,1), (0,2),
+    # (1,2)), b = (1, 2, 4), P = (1, 1, 2), every pair stored in both directions plus the diagonal.
+    # By hand: sum_E' d2 / (b_i b_j) = 2 (1/2 + 9/4 + 4/8) = 6.5 and
+    # sum_E' d2 / (4 P_i P_j) = 2 (1/4 + 9/8 + 4/8) = 3.75, so 4 log2(3.75 / 6.5) = -3.174...
+    # rounds to -3 and xi_c = -0.75.
+    x = np.array([[0.0], [1.0], [3.0]], dtype=np.float32)
+    p = M.full_pattern(x)
+    b = np.array([1.0, 2.0, 4.0])
+    P = np.array([1.0, 1.0, 2.0])
+    assert M.operator_centre(p, b, P) == -0.75
+    # doubling the coordinates quadruples d2 and doubles b: the density argument is unchanged,
+    # the operator argument grows 4x, so the centre moves by log2(4) = 2 to 1.25
+    assert M.operator_centre(M.full_pattern(2 * x), 2 * b, P) == 1.25
+    # rounding to the nearest quarter (not down): a ratio of 2^0.45 gives 4 * 0.45 = 1.8 -> 2 -> 0.5
+    P2 = np.full(3, 0.5 * 2.0 ** -0.225)
+    b2 = np.full(3, 1.0)
+    assert M.operator_centre(p, b2, P2) == 0.5
+
+
+def test_sphere_drift_reference_spectrum():
+    # The continuum reference for the von Mises-Fisher example of Sec. 5.2 with c = 1: at
+    # kappa = 0 the Galerkin solver must give the spherical Laplacian's -l(l+1) with
+    # multiplicity 2l + 1; at kappa = 2 it must agree with an independent finite-volume
+    # discretisation in the polar angle.
+    from oracle import spectra as SP
+    lam0 = SP.sphere_drift_spectrum(0.0, 1.0, 36)
+    expect = -np.concatenate([[l * (l + 1)] * (2 * l + 1) for l in range(6)])
+    np.testing.assert_allclose(lam0, expect, atol=1e-9)
+    lam = SP.sphere_drift_spectrum(2.0, 1.0, 33)
+    fv = SP.sphere_drift_spectrum_fd(2.0, 1.0, 33)
+    assert lam[0] == pytest.approx(0.0, abs=1e-9)
+    np.testing.assert_allclose(lam[1:], fv[1:], rtol=5e-6)
+    # the drift lifts the l = 1 triplet into the m = +-1 pair and the m = 0 level
+    assert abs(lam[1] - lam[2]) < 1e-9 and lam[3] < lam[2] - 0.1
+    # c = 0 ignores the density (Delta alone); the spectrum depends on c kappa only
+    np.testing.assert_allclose(SP.sphere_drift_spectrum(2.0, 0.0, 16), expect[:16], atol=1e-9)
+    np.testing.assert_allclose(SP.sphere_drift_spectrum(1.0, 2.0, 16), lam[:16], rtol=1e-12, atol=1e-12)
+
+
+def test_manufactured_5d_closed_form():
+    # The manufactured solve of the 5-dimensional Gaussian workload: f = z_1 exp(-|z|^2 / 4) and,
+    # for psi = N(0, I_5) and c = 1 (L = Delta - z . grad), g = L f = z_1 exp(-|z|^2/4)(0.75 |z|^2 - 4.5).
+    # Checked against central differences of f at random points, independently of the derivation.
+    rng = np.random.default_rng(0)
+    z = rng.standard_normal((50, 5))
+    f = lambda y: y[..., 0] * np.exp(-(y * y).sum(-1) / 4)
+    h = 1e-3
+    lap = np.zeros(50)
+    grad = np.zeros((50, 5))
+    for a in range(5):
+        e = np.zeros(5)
+        e[a] = h
+        lap += (f(z + e) - 2 * f(z) + f(z - e)) / h ** 2
+        grad[:, a] = (f(z + e) - f(z - e)) / (2 * h)
+    Lf = lap - (z * grad).sum(1)
+    r2 = (z * z).sum(1)
+    g = z[:, 0] * np.exp(-r2 / 4) * (0.75 * r2 - 4.5)
+    np.testing.assert_allclose(Lf, g, atol=1e-5)
+    # f has zero mean under psi (odd in z_1), as the solvability condition of Eq. (Kolmogorov problem) needs
+    zz = rng.standard_normal((200000, 5))
+    assert abs(np.mean(f(zz))) < 5e-3
+
+
+@pytest.mark.slow
+def test_gaussian4d_solve_error_falls_as_n_doubles():
+    # Sec. 5.1.2 reports the normalised error of the manufactured solve falling as n grows. With
+    # k = 48 and the kernel's self weight divided out of the spectrum (it scales every eigenvalue
+    # by 1 - w, so the solve by 1 / (1 - w)), the error falls at each doubling of n.
+    g = GOLD["gaussian4d_eigenvalues"]
+    s = GOLD["gaussian4d_solution"]
+    errs = []
+    for n in (2000, 4000, 8000):
+        x = W.gaussian(n, 4, scales=g["variances"], seed=7)
+        B = M.build(x, 48, d=4, c=1.0)
+        e = M.leading_eigenpairs(B.lhat_csr(), B.op.S, 6)
+        gv = x.astype(np.float64) @ np.array(s["g_coeffs"])
+        fv = x.astype(np.float64) @ np.array(s["f_coeffs"])
+        f = M.spectral_solve(e, B.op.S, gv) * (1.0 - _self_weight(B))
+        errs.append(np.sum((f - fv) ** 2) / np.sum(fv ** 2))   # Eq. (normalised error)
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 0.05
