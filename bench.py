@@ -318,7 +318,7 @@ def _tile_distance_error(vb, spec: Spec, xt, fmt: str) -> dict:
     x = xt
     if spec.cloud_ptr is not None:
         x = xt[: int(spec.cloud_ptr[1])].contiguous()
-    nbr, _, idx, d16 = vb.knn(x, spec.k, tensor_cores=fmt, debug=True)
+    nbr, nd2, idx, d16 = vb.knn(x, spec.k, tensor_cores=fmt, debug=True)
     ok = idx >= 0
     rows = torch.arange(x.shape[0], device=x.device)[:, None].expand_as(idx)[ok]
     cols = idx[ok].long()
@@ -327,7 +327,12 @@ def _tile_distance_error(vb, spec: Spec, xt, fmt: str) -> dict:
     dt = d16[ok].double()
     pos = d64 > 0
     rel = (dt[pos] - d64[pos]).abs() / d64[pos]
-    return {"max_rel": float(rel.max()), "rms_rel": float(rel.pow(2).mean().sqrt()), "pairs": int(rel.numel()),
+    # the error that decides the ranking: against the row's k-th neighbour distance
+    dk = nd2[:, -1][rows]
+    relk = (dt - d64).abs() / dk.clamp_min(1e-300)
+    return {"max_rel": float(rel.max()), "rms_rel": float(rel.pow(2).mean().sqrt()),
+            "max_rel_to_kth": float(relk.max()), "rms_rel_to_kth": float(relk.pow(2).mean().sqrt()),
+            "pairs": int(rel.numel()),
             "what": f"every kept candidate of every row ({'first cloud' if spec.cloud_ptr is not None else 'all rows'})"
                     f", {fmt} tile distance vs FP64"}
 

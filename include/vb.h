@@ -476,6 +476,62 @@ vb_status vb_build_batch(vb_ctx* ctx, const float* x, int64_t n, int32_t m, cons
                          const int64_t* cloud_ptr_dev, int32_t B, const vb_build_params* p,
                          const vb_build_out* out, void* ws, size_t ws_bytes);
 
+/* ------------------------------------------ the delta_tol radius pattern (Algorithm 1, Sec. 4)
+ * The paper's own sparsity: an entry of a kernel matrix K^ij = exp(-d2_ij / (eps^2 rho_i rho_j))
+ * is kept only where it exceeds delta_tol (Algorithm 1; Sec. 4 finds the candidates with a k-d
+ * tree inside the critical radius R^2 = -eps^2 b_max^2 log(delta_tol)).  The test is evaluated
+ * as t_ij < tau with t_ij = d2_ij / (eps^2 (rho_i rho_j)) (the product rho_i rho_j first, so the
+ * pattern is symmetric bit for bit) and tau = -log(delta_tol) in FP64; d2 is the canonical FP64
+ * squared distance of vb_knn; the diagonal is kept (t = 0).  The search runs on the kNN
+ * search's Morton-ordered 64-point tiles and skips a tile pair when the gap of the two boxes
+ * with the largest rho of each tile already fails the test (the critical radius per tile
+ * pair); the pairs that remain are tested one by one, so the pattern is exact.
+ *   x: n x m FP32 (device); rho: n FP64 (device, b for the density kernel, 2 psi^beta for the
+ *   operator kernel); row_ptr: n + 1 int64; col: cap int32; d2: cap FP64 (rows sorted by
+ *   column); nnz_dev: one int64.  A pattern with more than cap entries records
+ *   VB_ERR_WORKSPACE in the report and leaves col and d2 unwritten; a row of more than 2048
+ *   entries records VB_ERR_UNSUPPORTED and stays unsorted.  1 <= m <= 128. */
+size_t vb_radius_workspace(int64_t n, int32_t m);
+vb_status vb_radius_pattern(vb_ctx* ctx, const float* x, int64_t n, int32_t m, const double* rho, double eps2,
+                            double delta_tol, int64_t* row_ptr, int32_t* col, double* d2, int64_t cap,
+                            int64_t* nnz_dev, void* ws, size_t ws_bytes);
+/* Eq. (bandwidth sensitivity) with the delta_tol pattern of every grid point: on the grid
+ * xi_g = xi_lo + g dxi (G <= 64 points), chi_g = sum over the pairs (i, j) with
+ * t_ij / 2^xi_g < tau of exp(-t_ij / 2^xi_g), t_ij = d2_ij / (scale (rho_i rho_j)), every
+ * pair of the cloud considered (the diagonal adds n); then, as in vb_epsilon_tune, the first
+ * maximiser g* of chi' gives eps2 = 2^xi_{g*} and dim_est = 2 chi'_{g*}.  FP64 sums in a fixed
+ * order.  chi_dev: G FP64; eps2_dev, dim_est_dev: one FP64 each (device). */
+vb_status vb_radius_sweep(vb_ctx* ctx, const float* x, int64_t n, int32_t m, const double* rho, double scale,
+                          double xi_lo, double xi_hi, double dxi, double delta_tol, double* chi_dev, double* eps2_dev,
+                          double* dim_est_dev, void* ws, size_t ws_bytes);
+
+/* ------------------------------------------ particle evolution (Sec. 6)
+ * One explicit step of the evolution of a time-dependent density (Sec. 6, Eq. SDE and
+ * Eq. discrete sample evolution): the samples x of psi(.; t) move by
+ *     x_next = x + dt (u - grad f) + sqrt(dt) sigma W,
+ * where f solves the Kolmogorov problem L_{1,psi} f = g on the current samples (Eq.
+ * advection-diffusion-Laplace): the whole build of vb_build with c = 1, the spectral solve
+ * of vb_solve with ell eigenpairs (the constant mode dropped), and grad f by vb_gradient.
+ * The source is centred on the samples, g - mean(g), the sample mean standing for the
+ * expectation under psi(.; t).  The Gaussian draws W are inputs (the caller draws them), so
+ * a step is a deterministic function of its arguments.  Synchronises the host (vb_solve).
+ *   x, W, x_next: n x m FP32 row-major (device); u: n x m FP32 (device) or NULL (u = 0);
+ *   sigma: m x m FP32 row-major (device); g: n FP32 (device);
+ *   out: the build's caller-owned buffers, as for vb_build (p->build.op.c must be 1);
+ *   f: n FP32 (device), the solution; grad: n x m FP32 (device), grad f at the samples.
+ * Returns VB_ERR_NOT_CONVERGED (outputs still written) when the eigen-solver ran out of
+ * iterations. */
+typedef struct {
+    vb_build_params build;   /* the operator of every step (op.c = 1: L_{1,psi}) */
+    vb_solve_params solve;   /* eigenpairs of the spectral solve */
+    double dt;               /* step length, > 0 */
+} vb_evolve_params;
+
+size_t vb_evolve_workspace(int64_t n, int32_t m, const vb_evolve_params* p);
+vb_status vb_evolve_step(vb_ctx* ctx, const float* x, int64_t n, int32_t m, const vb_evolve_params* p,
+                         const float* u, const float* sigma, const float* W, const float* g,
+                         const vb_build_out* out, float* f, float* grad, float* x_next, void* ws, size_t ws_bytes);
+
 #ifdef __cplusplus
 }
 #endif

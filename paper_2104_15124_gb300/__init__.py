@@ -74,6 +74,10 @@ class SolveParams(ctypes.Structure):
                 ("seed", ctypes.c_uint64)]
 
 
+class EvolveParams(ctypes.Structure):
+    _fields_ = [("build", BuildParams), ("solve", SolveParams), ("dt", c_f64)]
+
+
 class MlpC(ctypes.Structure):
     _fields_ = [("in_dim", c_i32), ("master", c_p), ("weights", c_p), ("adam_m", c_p), ("adam_v", c_p),
                 ("in_mean", c_f32 * 16), ("in_scale", c_f32 * 16), ("out_mean", c_f32), ("out_scale", c_f32),
@@ -131,6 +135,13 @@ _SIGS = {
     "vb_tc_dot_tile": (c_i32, [c_p, c_p, c_p, c_i32, c_i32, c_p]),
     "vb_build_workspace": (c_sz, [c_i64, c_i32, ctypes.POINTER(BuildParams)]),
     "vb_build": (c_i32, [c_p, c_p, c_i64, c_i32, ctypes.POINTER(BuildParams), ctypes.POINTER(BuildOut), c_p, c_sz]),
+    "vb_radius_workspace": (c_sz, [c_i64, c_i32]),
+    "vb_radius_pattern": (c_i32, [c_p, c_p, c_i64, c_i32, c_p, c_f64, c_f64, c_p, c_p, c_p, c_i64, c_p, c_p, c_sz]),
+    "vb_radius_sweep": (c_i32, [c_p, c_p, c_i64, c_i32, c_p, c_f64, c_f64, c_f64, c_f64, c_f64, c_p, c_p, c_p, c_p,
+                                c_sz]),
+    "vb_evolve_workspace": (c_sz, [c_i64, c_i32, ctypes.POINTER(EvolveParams)]),
+    "vb_evolve_step": (c_i32, [c_p, c_p, c_i64, c_i32, ctypes.POINTER(EvolveParams), c_p, c_p, c_p, c_p,
+                               ctypes.POINTER(BuildOut), c_p, c_p, c_p, c_p, c_sz]),
     "vb_build_batch_workspace": (c_sz, [c_i64, c_i32, c_i32, ctypes.POINTER(BuildParams)]),
     "vb_build_batch": (c_i32, [c_p, c_p, c_i64, c_i32, ctypes.POINTER(c_i64), c_p, c_i32, ctypes.POINTER(BuildParams),
                                ctypes.POINTER(BuildOut), c_p, c_sz]),
@@ -641,3 +652,82 @@ def build(x: torch.Tensor, k: int, d: float, c: float, beta: float = -0.25, marg
     """The whole build, kNN to L-hat (vb_build), on x's device and current stream."""
     n, m = x.shape
     return Builder(n, m, k, d, c, beta, margin, k_bw, prune, x.device)(x, eps2_den, eps2_op)
+
+
+@dataclasses.dataclass
+class EvolveStep:
+    x_next: torch.Tensor   # [n, m] FP32 samples after the step
+    grad_f: torch.Tensor   # [n, m] FP32 grad f at the samples before the step
+    f: torch.Tensor        # [n] FP32 solution of L_{1,psi} f = g - mean(g)
+    build: Build           # the operator of the step
+    converged: bool
+
+
+def evolve_step(x: torch.Tensor, dt: float, sigma: torch.Tensor, W: torch.Tensor, g: torch.Tensor, k: int,
+                ell: int, d: float, u: torch.Tensor | None = None, beta: float = -0.25, margin: int = 16,
+                max_iter: int = 0) -> EvolveStep:
+    """One explicit step of the particle evolution of Sec. 6 (vb_evolve_step): the build of
+    L_{1,psi} on x, the spectral solve of L f = g - mean(g) with ell eigenpairs, grad f, and
+    x + dt (u - grad f) + sqrt(dt) sigma W.  x, W, u: [n, m] FP32; sigma: [m, m] FP32; g: [n] FP32."""
+    n, m = x.shape
+    dev = x.device
+    b = Builder(n, m, k, d=d, c=1.0, beta=beta, margin=margin, device=dev)
+    p = EvolveParams(b.params, SolveParams(ell, 0, 0, max_iter, 0.0, 1), dt)
+    f = torch.empty(n, dtype=torch.float32, device=dev)
+    grad = torch.empty((n, m), dtype=torch.float32, device=dev)
+    x_next = torch.empty((n, m), dtype=torch.float32, device=dev)
+    ws = _ws(lib().vb_evolve_workspace(n, m, ctypes.byref(p)), dev)
+    rc = lib().vb_evolve_step(c_p(_ctx(dev)), _p(x), n, m, ctypes.byref(p), _p(u), _p(sigma), _p(W), _p(g),
+                              ctypes.byref(b.cout), _p(f), _p(grad), _p(x_next), _p(ws), ws.numel())
+    if rc not in (0, -6):
+        _check(rc, "vb_evolve_step")
+    return EvolveStep(x_next, grad, f, b.out, rc == 0)
+
+
+@dataclasses.dataclass
+class RadiusPattern:
+    """The delta_tol pattern (vb_radius_pattern): CSR with rows sorted by column."""
+    n: int
+    row_ptr: torch.Tensor   # [n + 1] int64
+    col: torch.Tensor       # [nnz] int32
+    d2: torch.Tensor        # [nnz] FP64 canonical squared distances
+    nnz: int
+
+
+def radius_pattern(x: torch.Tensor, rho: torch.Tensor, eps2: float, delta_tol: float, cap: int = 0) -> RadiusPattern:
+    """Algorithm 1's pattern: every (i, j) with exp(-d2 / (eps^2 rho_i rho_j)) > delta_tol, evaluated as
+    d2 / (eps^2 (rho_i rho_j)) < -log(delta_tol) (vb_radius_pattern).  cap: entries to allocate (0 = 32 per
+    row to begin with); a pattern larger than cap is computed again with room for all of it."""
+    n, m = x.shape
+    dev = x.device
+    cap = cap or 32 * n
+    ws = _ws(lib().vb_radius_workspace(n, m), dev)
+    row_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    nnz = torch.empty(1, dtype=torch.int64, device=dev)
+    for _ in range(2):
+        col = torch.empty(cap, dtype=torch.int32, device=dev)
+        d2 = torch.empty(cap, dtype=torch.float64, device=dev)
+        report_reset(dev)
+        _check(lib().vb_radius_pattern(c_p(_ctx(dev)), _p(x), n, m, _p(rho), eps2, delta_tol, _p(row_ptr), _p(col),
+                                       _p(d2), cap, _p(nnz), _p(ws), ws.numel()), "vb_radius_pattern")
+        z = int(nnz.item())
+        if z <= cap:
+            raise_on_device_error(dev)
+            return RadiusPattern(n, row_ptr, col[:z], d2[:z], z)
+        cap = z
+    raise VbError(-3, "vb_radius_pattern")
+
+
+def radius_sweep(x: torch.Tensor, rho: torch.Tensor, scale: float, delta_tol: float, grid=(XI_LO, XI_HI, DXI)):
+    """Eq. (bandwidth sensitivity) over the delta_tol pattern of every grid point (vb_radius_sweep):
+    returns (chi [G], eps2 [1], dim_est [1]) on the device."""
+    n, m = x.shape
+    dev = x.device
+    G = int(round((grid[1] - grid[0]) / grid[2])) + 1
+    chi = torch.empty(G, dtype=torch.float64, device=dev)
+    eps2 = torch.empty(1, dtype=torch.float64, device=dev)
+    dim = torch.empty(1, dtype=torch.float64, device=dev)
+    ws = _ws(lib().vb_radius_workspace(n, m), dev)
+    _check(lib().vb_radius_sweep(c_p(_ctx(dev)), _p(x), n, m, _p(rho), scale, grid[0], grid[1], grid[2], delta_tol,
+                                 _p(chi), _p(eps2), _p(dim), _p(ws), ws.numel()), "vb_radius_sweep")
+    return chi, eps2, dim

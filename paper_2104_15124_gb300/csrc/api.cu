@@ -367,4 +367,77 @@ vb_status vb_build_batch(vb_ctx* ctx, const float* x, int64_t n, int32_t m, cons
     return build_run(c, x, n, m, p, o, ws, ws_bytes, cl);
 }
 
+size_t vb_radius_workspace(int64_t n, int32_t m) { return radius_ws_bytes(n, m); }
+
+vb_status vb_radius_pattern(vb_ctx* ctx, const float* x, int64_t n, int32_t m, const double* rho, double eps2,
+                            double delta_tol, int64_t* row_ptr, int32_t* col, double* d2, int64_t cap,
+                            int64_t* nnz_dev, void* ws, size_t ws_bytes)
+{
+    if (!ctx) return VB_ERR_ARG;
+    DeviceGuard g(C(ctx)->device);
+    if (!g.ok) return VB_ERR_CUDA;
+    return radius_pattern_run(C(ctx), x, n, m, rho, eps2, delta_tol, row_ptr, col, d2, cap, nnz_dev, ws, ws_bytes);
+}
+
+vb_status vb_radius_sweep(vb_ctx* ctx, const float* x, int64_t n, int32_t m, const double* rho, double scale,
+                          double xi_lo, double xi_hi, double dxi, double delta_tol, double* chi_dev, double* eps2_dev,
+                          double* dim_est_dev, void* ws, size_t ws_bytes)
+{
+    if (!ctx) return VB_ERR_ARG;
+    DeviceGuard g(C(ctx)->device);
+    if (!g.ok) return VB_ERR_CUDA;
+    return radius_sweep_run(C(ctx), x, n, m, rho, scale, xi_lo, xi_hi, dxi, delta_tol, chi_dev, eps2_dev,
+                            dim_est_dev, ws, ws_bytes);
+}
+
+size_t vb_evolve_workspace(int64_t n, int32_t m, const vb_evolve_params* p)
+{
+    if (!p || n < 2 || m < 1) return 0;
+    const int64_t cap = n * (2 * (int64_t)p->build.knn.k + 1);
+    const int32_t ell = p->solve.ell;
+    Carve c(nullptr);
+    c.take<float>(n);                            // centred source
+    c.take<double>(ell + 1);                     // eigenvalues
+    c.take<float>((size_t)(ell + 1) * n);        // eigenvectors
+    const size_t stages = std::max({build_ws(n, m, &p->build), solve_ws_bytes(n, cap, &p->solve),
+                                    gradient_ws_bytes(n, ell, m)});
+    return c.off + stages + 256;
+}
+
+vb_status vb_evolve_step(vb_ctx* ctx, const float* x, int64_t n, int32_t m, const vb_evolve_params* p,
+                         const float* u, const float* sigma, const float* W, const float* g, const vb_build_out* o,
+                         float* f, float* grad, float* x_next, void* ws, size_t ws_bytes)
+{
+    if (!ctx || !p || !o || !x || !sigma || !W || !g || !f || !grad || !x_next) return VB_ERR_ARG;
+    if (!(p->dt > 0) || p->build.op.c != 1.0 || p->solve.ell < 1 || n < 2 || m < 1 || m > 128) return VB_ERR_ARG;
+    if (x_next == x || o->cap < n * (2 * (int64_t)p->build.knn.k + 1)) return VB_ERR_ARG;
+    if (!ws || ws_bytes < vb_evolve_workspace(n, m, p)) return VB_ERR_WORKSPACE;
+    Ctx* c = C(ctx);
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return VB_ERR_CUDA;
+    const int32_t ell = p->solve.ell;
+    Carve cv(ws);
+    float* gc = cv.take<float>(n);
+    double* evals = cv.take<double>(ell + 1);
+    float* phi = cv.take<float>((size_t)(ell + 1) * n);
+    void* rest = (char*)ws + ((cv.off + 255) & ~(size_t)255);
+    const size_t rest_bytes = ws_bytes - ((cv.off + 255) & ~(size_t)255);
+    // L_{1,psi} on the current samples
+    vb_status st = build_run(c, x, n, m, &p->build, o, rest, rest_bytes, Clouds());
+    if (st) return st;
+    // f with L_{1,psi} f = g - mean(g) over ell eigenpairs (Sec. 3.1), then grad f (Sec. 3.2)
+    st = evolve_centre_launch(c->stream, g, n, gc);
+    if (st) return st;
+    vb_graph gr{n, o->row_ptr, o->col, o->ed2};
+    int32_t iters = 0;
+    const vb_status solved = solve_run(c, &gr, o->cap, o->val, o->S, &p->solve, evals, phi, gc, f, &iters, rest,
+                                       rest_bytes);
+    if (solved != VB_OK && solved != VB_ERR_NOT_CONVERGED) return solved;
+    st = gradient_run(c, n, ell, evals, phi, o->S, f, x, m, grad, rest, rest_bytes);
+    if (st) return st;
+    st = evolve_update_launch(c->stream, x, n, m, u, grad, sigma, W, p->dt, x_next);
+    c->launches += 2;
+    return st != VB_OK ? st : solved;
+}
+
 }  // extern "C"

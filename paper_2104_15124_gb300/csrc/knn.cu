@@ -29,6 +29,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <type_traits>
 
 namespace vb {
 
@@ -896,24 +897,59 @@ struct Band {
 // df >= B (the largest kept key, or the radius sentinel), so none can lie below
 // dk when dk < (B - E_dk(B)) (1 - 2 gamma); far operands clamped to +-30000 in FP16
 // lie at exact distance >= 4e8, which the certificate also requires dk to stay below.
-template <int MP, int COLS>
-__device__ bool finalize_row_band(const TileArgs& a, uint64_t* arr, int t, int size, int64_t pq, int64_t ncl,
-                                  unsigned& levels, const Band& bd, float qn)
+// Keys of the 16-bit searches.  Full (64-bit): FP32 bits of the tile distance << 32 | sorted
+// position; the radius sentinel carries position 0xffffffff.  Compact (32-bit, the staged
+// kernel at m <= 16): the distance bits truncated to 18 << 14 | slot, slot = visit << 6 | lane,
+// with the CTA's table of the tile of every visit; slot 0x3fff marks a sentinel.  A compact key
+// stands for a bucket [lo, hi] of distances: lo bounds every distance of the bucket from
+// below (the scan's stop test and the certificate use it), hi from above (the filter).
+template <class K> struct BandKey;
+template <> struct BandKey<uint64_t> {
+    static constexpr uint64_t EMPTY = ~0ull;
+    static __device__ __forceinline__ bool none(uint64_t k) { return (uint32_t)k == 0xffffffffu; }
+    static __device__ __forceinline__ float lo(uint64_t k) { return __uint_as_float((uint32_t)(k >> 32)); }
+    static __device__ __forceinline__ uint32_t hi_bits(uint64_t k) { return (uint32_t)(k >> 32); }
+    static __device__ __forceinline__ uint32_t pos(uint64_t k, const int*) { return (uint32_t)k; }
+    static __device__ __forceinline__ uint64_t make(uint32_t dbits, int, int, uint32_t cp)
+    {
+        return ((uint64_t)dbits << 32) | cp;
+    }
+    static __device__ __forceinline__ uint64_t sentinel(uint32_t r2bits) { return ((uint64_t)r2bits << 32) | 0xffffffffu; }
+};
+template <> struct BandKey<uint32_t> {
+    static constexpr uint32_t EMPTY = ~0u;
+    static __device__ __forceinline__ bool none(uint32_t k) { return (k & 0x3fffu) == 0x3fffu; }
+    static __device__ __forceinline__ float lo(uint32_t k) { return __uint_as_float((k >> 14) << 13); }
+    static __device__ __forceinline__ uint32_t hi_bits(uint32_t k) { return k == ~0u ? ~0u : (((k >> 14) << 13) | 0x1fffu); }
+    static __device__ __forceinline__ uint32_t pos(uint32_t k, const int* vtab)
+    {
+        return (uint32_t)vtab[(k >> 6) & 0xffu] * TILE + (k & 63u);
+    }
+    static __device__ __forceinline__ uint32_t make(uint32_t dbits, int vis, int lane, uint32_t)
+    {
+        return ((dbits >> 13) << 14) | ((uint32_t)vis << 6) | (uint32_t)lane;
+    }
+    static __device__ __forceinline__ uint32_t sentinel(uint32_t r2bits) { return ((r2bits >> 13) << 14) | 0x3fffu; }
+};
+
+template <int MP, int COLS, class K = uint64_t>
+__device__ bool finalize_row_band(const TileArgs& a, K* arr, int t, int size, int64_t pq, int64_t ncl,
+                                  unsigned& levels, const Band& bd, float qn, const int* vtab = nullptr)
 {
+    using BK = BandKey<K>;
     for (int e = size - 1; e > 0; --e) {
-        const uint64_t top = arr[t];
-        const uint64_t key = arr[e * COLS + t];
+        const K top = arr[t];
+        const K key = arr[e * COLS + t];
         arr[e * COLS + t] = top;
         sift_down<COLS>(arr, t, 0, e, key, levels);
     }
-    const uint64_t Hkey = arr[(size - 1) * COLS + t];
+    const K Hkey = arr[(size - 1) * COLS + t];
     const uint32_t oq = a.perm[pq];
     if (a.dbg_d2) {   // diagnostic: the kept keys' 16-bit distances, ascending, before any rescoring
         for (int r = 0; r < size && r < a.L; ++r) {
-            const uint64_t key = arr[r * COLS + t];
-            const uint32_t cp = (uint32_t)key;
-            a.dbg_idx[(int64_t)oq * a.L + r] = cp == 0xffffffffu ? -1 : (int32_t)a.perm[cp];
-            a.dbg_d2[(int64_t)oq * a.L + r] = __uint_as_float((uint32_t)(key >> 32));
+            const K key = arr[r * COLS + t];
+            a.dbg_idx[(int64_t)oq * a.L + r] = BK::none(key) ? -1 : (int32_t)a.perm[BK::pos(key, vtab)];
+            a.dbg_d2[(int64_t)oq * a.L + r] = BK::lo(key);
         }
     }
     const double* qc = a.xs64 + pq * MP;
@@ -936,12 +972,13 @@ __device__ bool finalize_row_band(const TileArgs& a, uint64_t* arr, int t, int s
         double djb[FB], dfb[FB];
 #pragma unroll
         for (int u = 0; u < FB; ++u) {
-            const uint64_t key = r0 + u < size ? arr[(r0 + u) * COLS + t] : ~0ull;
-            cpb[u] = (uint32_t)key;
-            dfb[u] = (double)__uint_as_float((uint32_t)(key >> 32));
+            const K key = r0 + u < size ? arr[(r0 + u) * COLS + t] : BK::EMPTY;
+            const bool none = BK::none(key);
+            cpb[u] = none ? 0xffffffffu : BK::pos(key, vtab);
+            dfb[u] = (double)BK::lo(key);
             ojb[u] = 0;
             djb[u] = 0.0;
-            if (cpb[u] != 0xffffffffu) {
+            if (!none) {
                 ojb[u] = (int32_t)a.perm[cpb[u]];
                 if constexpr (QR) djb[u] = canon_d2_q64<MP>(qv, a.xs64 + (int64_t)cpb[u] * MP, a.m);
                 else djb[u] = canon_d2_64(qc, a.xs64 + (int64_t)cpb[u] * MP, a.m);
@@ -972,8 +1009,8 @@ __device__ bool finalize_row_band(const TileArgs& a, uint64_t* arr, int t, int s
     if (out < k) { atomicAdd(&a.rep->knn_rows_short, 1ull); return false; }
     // every candidate was kept (a small cloud without a radius, or an unfilled heap); with a
     // radius the candidates beyond it were never kept, so the certificate decides
-    if ((ncl - 1 <= (int64_t)size && !a.r2) || Hkey == ~0ull) return true;
-    const double B = (double)__uint_as_float((uint32_t)(Hkey >> 32));
+    if ((ncl - 1 <= (int64_t)size && !a.r2) || Hkey == BK::EMPTY) return true;
+    const double B = (double)BK::lo(Hkey);
     const bool cert = isfinite(B) && dk < 4e8 &&
                       dk < (B - bd.E(qn, dk, B)) * a.cert_factor - (double)a.m * 1.1754943508222875e-38;
     if (!cert) atomicAdd(&a.rep->knn_rows_uncertified, 1ull);
@@ -1422,9 +1459,11 @@ template <> struct Half16<true> {
     static constexpr float clampv = kHalfClamp;
 };
 
-template <int MP, bool F16>
+template <int MP, bool F16, bool K32 = false>
 __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
 {
+    using KT = typename std::conditional<K32, uint32_t, uint64_t>::type;
+    using BK = BandKey<KT>;
     constexpr int KP = MP < 16 ? 16 : MP;
     using HT = Half16<F16>;
     using half_t = typename HT::T;
@@ -1434,7 +1473,7 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
     half_t* sb = sa + T2 * KP;                                 // [TILE][KP]
     float* sqb = (float*)(sb + TILE * KP);                     // [TILE]
     uint64_t* slist = (uint64_t*)(sqb + TILE);                 // [SCAP]
-    uint64_t* buf = slist + SCAP;                              // [C][T2] max-heaps
+    KT* buf = (KT*)(slist + SCAP);                             // [C][T2] max-heaps
     __shared__ float sqlo[MP], sqhi[MP], scen[MP];
     __shared__ uint32_t sred[4];
     __shared__ int s_tile, s_fail, s_abort;
@@ -1444,6 +1483,8 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
     __shared__ float s_amax[4];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tmem_base;
+    __shared__ int vtab[K32 ? VMAX + 1 : 1];   // compact keys: the tile of every visit number
+    __shared__ int s_nvis;
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t nt = a.ntiles;
@@ -1468,6 +1509,7 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
         if (t == 0) {
             s_tile = atomicAdd(a.work, 1);
             s_fail = 0;
+            s_nvis = 0;
         }
         __syncthreads();
         const int64_t qs = s_tile;
@@ -1520,11 +1562,11 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
         }
         const float qn = sqrtf(sqa);
         const float R2 = rmode && valid ? __fmul_ru(a.r2[p], a.r2_scale) : INFINITY;
-        const uint64_t sentinel = rmode ? (((uint64_t)__float_as_uint(R2) << 32) | 0xffffffffu) : ~0ull;
+        const KT sentinel = rmode ? BK::sentinel(__float_as_uint(R2)) : BK::EMPTY;
         for (int sl = 0; sl < C; ++sl) buf[sl * T2 + t] = sentinel;
-        uint64_t heapmax = sentinel;
+        KT heapmax = sentinel;
         {
-            const uint32_t wr = __reduce_max_sync(0xffffffffu, valid ? (uint32_t)(sentinel >> 32) : 0u);
+            const uint32_t wr = __reduce_max_sync(0xffffffffu, valid ? BK::hi_bits(sentinel) : 0u);
             const uint32_t wa = __reduce_max_sync(0xffffffffu, valid ? __float_as_uint(qn) : 0u);
             if (lane == 0) { sred[warp] = wr; s_amax[warp] = __uint_as_float(wa); }
         }
@@ -1548,9 +1590,18 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
                     const float g = fmaxf(fmaxf(a.tlo[ct * MP + r] - qr[r], qr[r] - a.thi[ct * MP + r]), 0.f);
                     acc = fmaf(g, g, acc);
                 }
-                need = __float_as_uint(__fmul_rd(acc, a.lb_factor)) <= (uint32_t)(heapmax >> 32);
+                need = __float_as_uint(__fmul_rd(acc, a.lb_factor)) <= BK::hi_bits(heapmax);
             }
             if (!__syncthreads_or(need)) return true;
+            int vis = 0;   // compact keys: this visit's number (the same in every thread)
+            if constexpr (K32) {
+                vis = s_nvis;
+                if (vis >= VMAX) {   // more visits than the table holds: the FP32 search redoes the tile
+                    if (t == 0) s_fail = 1;
+                    __syncthreads();   // every thread sees the flag before the loops test it
+                    return false;
+                }
+            }
             staged += t == 0;
             if (t < TILE) {   // candidate operand: row t of tile ct
                 const int64_t cp = ct * TILE + t;
@@ -1575,6 +1626,12 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
             tc::fence_before_sync();
             __syncthreads();
             tc::fence_after_sync();
+            if constexpr (K32) {
+                if (t == 0) {   // read again only after the barriers that end this visit
+                    vtab[vis] = (int)ct;
+                    s_nvis = vis + 1;
+                }
+            }
             if (t == 0) {
                 constexpr uint32_t sbo = (uint32_t)(KP / 8) * 128;
 #pragma unroll
@@ -1594,7 +1651,7 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
                 return false;
             }
             if (need) evaluated += TILE;
-            const uint32_t hb = (uint32_t)(heapmax >> 32);
+            const uint32_t hb = BK::hi_bits(heapmax);
             float hmf = hb == 0xffffffffu ? INFINITY : __uint_as_float(hb);
 #pragma unroll 1
             for (int ch = 0; ch < TILE / 32; ++ch) {
@@ -1621,18 +1678,18 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
 #pragma unroll
                     for (int j = 0; j < 32; ++j) d = j == i ? v[j] : d;
                     const int64_t cp = ct * TILE + ch * 32 + i;
-                    const uint64_t key = ((uint64_t)__float_as_uint(fmaxf(d, 0.f)) << 32) | (uint32_t)cp;
+                    const KT key = BK::make(__float_as_uint(fmaxf(d, 0.f)), vis, ch * 32 + i, (uint32_t)cp);
                     if (key < heapmax && cp != p && cp >= qlo && cp < qhi) {
                         sift_down<T2>(buf, t, 0, C, key, levels);
                         heapmax = buf[t];
                     }
                 }
-                const uint32_t h2 = (uint32_t)(heapmax >> 32);
+                const uint32_t h2 = BK::hi_bits(heapmax);
                 hmf = h2 == 0xffffffffu ? INFINITY : __uint_as_float(h2);
             }
             tc::fence_before_sync();
             // tile threshold = largest heap bound among the tile's valid queries
-            const uint32_t wmax = __reduce_max_sync(0xffffffffu, valid ? (uint32_t)(heapmax >> 32) : 0u);
+            const uint32_t wmax = __reduce_max_sync(0xffffffffu, valid ? BK::hi_bits(heapmax) : 0u);
             if (lane == 0) sred[warp] = wmax;
             __syncthreads();
             thr_blk = max(max(sred[0], sred[1]), max(sred[2], sred[3]));
@@ -1644,10 +1701,10 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
         const int64_t sw = (a.nseed - 1) / 2;   // tiles on each side
         const int64_t s_lo = rmode || far ? 0 : max(ct_lo, 2 * qs - sw);
         const int64_t s_hi = rmode || far ? 0 : min(ct_hi, 2 * qs + 2 + sw);
-        for (int64_t ct = s_lo; ct < s_hi && !s_abort; ++ct)
+        for (int64_t ct = s_lo; ct < s_hi && !s_abort && !s_fail; ++ct)
             if (!visit(ct)) break;
         // every other tile whose box lower bound does not exceed the tile bound, nearest first
-        for (int64_t c0 = ct_lo; c0 < ct_hi && !far && !s_abort;) {
+        for (int64_t c0 = ct_lo; c0 < ct_hi && !far && !s_abort && !s_fail;) {
             int cnt = 0;
             for (; c0 < ct_hi; c0 += T2) {
                 const int64_t ct = c0 + t;
@@ -1690,8 +1747,8 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
         }
         if (s_abort) break;
 
-        bool ok = !far;
-        if (valid && ok) ok = finalize_row_band<MP, T2>(a, buf, t, C, p, qhi - qlo, levels, bd, qn);
+        bool ok = !far && !s_fail;   // s_fail here: the visit table overflowed (compact keys)
+        if (valid && ok) ok = finalize_row_band<MP, T2, KT>(a, buf, t, C, p, qhi - qlo, levels, bd, qn, vtab);
         if (valid && !ok) s_fail = 1;
         __syncthreads();
         if (t == 0 && s_fail) {
@@ -2389,11 +2446,14 @@ static size_t tile_smem(int L)
            (K32 ? VMAX * sizeof(int) : 0);
 }
 
+// The staged search keeps compact 32-bit heap keys at m <= 16 (visits of a query tile stay
+// far below the visit table there), full 64-bit keys for wider inputs.
+template <int MP> constexpr bool tc_compact() { return MP <= 16; }
 template <int MP>
 static size_t tc_smem(int C)
 {
     constexpr int KP = MP < 16 ? 16 : MP;
-    return (size_t)T2 * KP * 2 + TILE * KP * 2 + TILE * 4 + SCAP * 8 + (size_t)C * T2 * 8;
+    return (size_t)T2 * KP * 2 + TILE * KP * 2 + TILE * 4 + SCAP * 8 + (size_t)C * T2 * (tc_compact<MP>() ? 4 : 8);
 }
 
 template <int MP, bool F16>
@@ -2406,13 +2466,14 @@ static vb_status launch_tc(TileArgs a, cudaStream_t s)
     int dev = 0;
     cudaGetDevice(&dev);
     if (!attr_set[dev & 15]) {
-        if (cudaFuncSetAttribute(knn_tc_kernel<MP, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(knn_tc_kernel<MP, F16, tc_compact<MP>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(220 * 1024)) != cudaSuccess ||
-            cudaFuncSetAttribute(knn_tc_kernel<MP, F16>, cudaFuncAttributePreferredSharedMemoryCarveout,
+            cudaFuncSetAttribute(knn_tc_kernel<MP, F16, tc_compact<MP>()>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
             return VB_ERR_CUDA;
         cudaFuncAttributes fa;
-        if (cudaFuncGetAttributes(&fa, knn_tc_kernel<MP, F16>) != cudaSuccess) return VB_ERR_CUDA;
+        if (cudaFuncGetAttributes(&fa, knn_tc_kernel<MP, F16, tc_compact<MP>()>) != cudaSuccess) return VB_ERR_CUDA;
         static_smem[dev & 15] = (int)fa.sharedSizeBytes;
         if (cudaDeviceGetAttribute(&sms[dev & 15], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&smem_sm[dev & 15], cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
@@ -2426,7 +2487,7 @@ static vb_status launch_tc(TileArgs a, cudaStream_t s)
     const int per_sm = std::max(1, std::min(8, smem_sm[dev & 15] / per_cta));
     const int64_t nst = (a.ntiles + 1) / 2;
     const int64_t grid = std::min<int64_t>(nst, (int64_t)per_sm * sms[dev & 15]);
-    knn_tc_kernel<MP, F16><<<(unsigned)grid, T2, sm, s>>>(a);
+    knn_tc_kernel<MP, F16, tc_compact<MP>()><<<(unsigned)grid, T2, sm, s>>>(a);
     return last_launch();
 }
 
@@ -2507,26 +2568,17 @@ static vb_status launch_tile(const TileArgs& a, cudaStream_t s)
     return launch_tile_m<MP, MP, K32>(a, s);
 }
 
-vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_params* p, int32_t* nbr,
-                  double* nbr_d2, void* ws, size_t ws_bytes, Clouds cl)
+// a1: the spatial order of the points (Morton key on the coordinates, or on the projections on
+// the leading principal axes when m > 4; then the cloud id above it in a batch), the sorted
+// coordinates in FP32 and FP64, and the boxes of 64-point tiles and 64-tile super-tiles.
+// perm (sorted position -> original index) is w.val[*cur] afterwards.
+static vb_status order_points(Ctx* ctx, const float* x, int64_t n, int32_t m, const KnnWs& w, Clouds cl,
+                              const uint32_t** perm_out)
 {
-    if (cl.B < 1 || (cl.B > 1 && !cl.ptr)) return VB_ERR_ARG;
-    if (!x || !nbr || !nbr_d2 || !p || n < 2 || n >= INT32_MAX || m < 1 || m > 128) return VB_ERR_ARG;
-    if (p->k < 1 || (int64_t)p->k > n - 1 || p->margin < 0 || p->k + p->margin > 256) return VB_ERR_ARG;
-    if (p->precision < VB_PREC_FP32 || p->precision > VB_PREC_FP16) return VB_ERR_UNSUPPORTED;
-    if (p->precision != VB_PREC_FP32 && p->prune == VB_PRUNE_NONE) return VB_ERR_UNSUPPORTED;
-    if (p->prune == VB_PRUNE_LEARNED && !p->radius && !p->mlp) return VB_ERR_ARG;
-    if (p->prune < VB_PRUNE_NONE || p->prune > VB_PRUNE_LEARNED) return VB_ERR_ARG;
-    KnnWs w;
-    Carve c(ws);
-    size_t need = knn_plan(c, n, m, p, &w);
-    if (!ws || ws_bytes < need) return VB_ERR_WORKSPACE;
     cudaStream_t s = ctx->stream;
     const int mp = pad_dim(m), md = morton_dims(m), bits = morton_bits(md);
     const int64_t ntiles = (n + TILE - 1) / TILE, npad = (ntiles + (ntiles & 1)) * TILE;
     const int nblk = (int)((n + RADIX_ITEMS - 1) / RADIX_ITEMS);
-
-    mark(ctx, VB_STAGE_KNN_ORDER, 0);
     bbox_init_kernel<<<1, 32, 0, s>>>(w.bbox, w.fb_count);
     const unsigned bbox_grid = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 4);
     if (m <= 4) {
@@ -2572,7 +2624,63 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
     tile_box_kernel<<<(unsigned)((ntiles * 32 + 255) / 256), 256, 0, s>>>(w.xs, n, ntiles, m, mp, w.tlo, w.thi);
     super_box_kernel<<<(unsigned)(((ntiles + TILE - 1) / TILE * 32 + 255) / 256), 256, 0, s>>>(w.tlo, w.thi, ntiles, mp,
                                                                                               w.slo, w.shi);
-    vb_status st = last_launch();
+    *perm_out = perm;
+    return last_launch();
+}
+
+size_t order_ws_bytes(int64_t n, int32_t m)
+{
+    vb_knn_params p = {};
+    p.k = 1;
+    p.precision = VB_PREC_FP32;
+    p.prune = VB_PRUNE_EXACT;
+    Carve c(nullptr);
+    return knn_plan(c, n, m, &p, nullptr);
+}
+
+vb_status order_run(Ctx* ctx, const float* x, int64_t n, int32_t m, void* ws, size_t ws_bytes, PointOrder* o)
+{
+    if (!x || !o || n < 1 || n >= INT32_MAX || m < 1 || m > 128) return VB_ERR_ARG;
+    vb_knn_params p = {};
+    p.k = 1;
+    p.precision = VB_PREC_FP32;
+    p.prune = VB_PRUNE_EXACT;
+    KnnWs w;
+    Carve c(ws);
+    if (!ws || ws_bytes < knn_plan(c, n, m, &p, &w)) return VB_ERR_WORKSPACE;
+    const uint32_t* perm = nullptr;
+    vb_status st = order_points(ctx, x, n, m, w, Clouds(), &perm);
+    if (st != VB_OK) return st;
+    o->xs64 = w.xs64;
+    o->tlo = w.tlo;
+    o->thi = w.thi;
+    o->perm = perm;
+    o->mp = pad_dim(m);
+    o->ntiles = (n + TILE - 1) / TILE;
+    return VB_OK;
+}
+
+vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_params* p, int32_t* nbr,
+                  double* nbr_d2, void* ws, size_t ws_bytes, Clouds cl)
+{
+    if (cl.B < 1 || (cl.B > 1 && !cl.ptr)) return VB_ERR_ARG;
+    if (!x || !nbr || !nbr_d2 || !p || n < 2 || n >= INT32_MAX || m < 1 || m > 128) return VB_ERR_ARG;
+    if (p->k < 1 || (int64_t)p->k > n - 1 || p->margin < 0 || p->k + p->margin > 256) return VB_ERR_ARG;
+    if (p->precision < VB_PREC_FP32 || p->precision > VB_PREC_FP16) return VB_ERR_UNSUPPORTED;
+    if (p->precision != VB_PREC_FP32 && p->prune == VB_PRUNE_NONE) return VB_ERR_UNSUPPORTED;
+    if (p->prune == VB_PRUNE_LEARNED && !p->radius && !p->mlp) return VB_ERR_ARG;
+    if (p->prune < VB_PRUNE_NONE || p->prune > VB_PRUNE_LEARNED) return VB_ERR_ARG;
+    KnnWs w;
+    Carve c(ws);
+    size_t need = knn_plan(c, n, m, p, &w);
+    if (!ws || ws_bytes < need) return VB_ERR_WORKSPACE;
+    cudaStream_t s = ctx->stream;
+    const int mp = pad_dim(m);
+    const int64_t ntiles = (n + TILE - 1) / TILE, npad = (ntiles + (ntiles & 1)) * TILE;
+
+    mark(ctx, VB_STAGE_KNN_ORDER, 0);
+    const uint32_t* perm = nullptr;
+    vb_status st = order_points(ctx, x, n, m, w, cl, &perm);
     if (st != VB_OK) return st;
     mark(ctx, VB_STAGE_KNN_ORDER, 1);
 

@@ -101,8 +101,31 @@ __device__ __forceinline__ void standardise(const MlpK& k, const float* x, int l
     for (int r = 0; r < k.in; ++r) xin[r] = (x[row * ld + r] - k.mean[r]) / k.scale[r];
 }
 
+// Forward pass for inference only: the hidden layer stays in registers and the second
+// layer is folded into the output as it is formed (no per-sample arrays in local memory).
+// The same operations in the same order as forward(), so the same bits.
+__device__ __forceinline__ float forward_infer(const MlpK& k, const float* W, const float* xin)
+{
+    const Off o(k.in);
+    float h1[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        float s = W[o.b1 + j];
+        for (int r = 0; r < k.in; ++r) s = fmaf(W[o.w1 + j * k.in + r], xin[r], s);
+        h1[j] = gelu(s);
+    }
+    float out = W[o.b3];
+    for (int j = 0; j < H; ++j) {
+        float s = W[o.b2 + j];
+#pragma unroll
+        for (int i = 0; i < H; ++i) s = fmaf(W[o.w2 + j * H + i], h1[i], s);
+        out = fmaf(W[o.w3 + j], gelu(s), out);
+    }
+    return out;
+}
+
 // ------------------------------------------------------------------ inference
-__global__ void __launch_bounds__(128) mlp_predict_kernel(MlpK k, const float* __restrict__ x, int ld, int64_t n,
+__global__ void __launch_bounds__(128, 4) mlp_predict_kernel(MlpK k, const float* __restrict__ x, int ld, int64_t n,
                                                           float* y, int mode, float shift, float inflate,
                                                           const float* __restrict__ cloud_shift, Clouds cl)
 {
@@ -110,9 +133,9 @@ __global__ void __launch_bounds__(128) mlp_predict_kernel(MlpK k, const float* _
     load_weights(k, W);
     __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        float xin[VB_MLP_MAX_IN], z1[H], h1[H], z2[H];
+        float xin[VB_MLP_MAX_IN];
         standardise(k, x, ld, i, xin);
-        const float logr = k.out_mean + k.out_scale * forward(k, W, xin, z1, h1, z2);
+        const float logr = k.out_mean + k.out_scale * forward_infer(k, W, xin);
         if (mode == 0) {
             y[i] = logr;
         } else {   // squared radius bound for the radius-first kNN search

@@ -563,21 +563,21 @@ vb_status centre_run(Ctx* ctx, const vb_graph* g, const double* b, const double*
 }
 
 // ------------------------------------------------------------------ a12 / a13 operator and L-hat
-struct OpVec {
-    float* iPh;   // 1 / P as an unevaluated pair hi + lo of floats
-    float* iPl;
-    float* qa;    // q^-alpha
-    float* iS;    // 1 / S
+// The per-point values every entry gathers from its column j, packed in one 16-byte record so
+// that a gather is one sector: 1 / P as an unevaluated pair (hi, lo) of floats, q^-alpha (set
+// by the q pass) and 1 / S (set by the D pass).
+struct __align__(16) PointOp {
+    float iPh, iPl, qa, iS;
 };
 
-__global__ void recip_pair_kernel(const double* __restrict__ v, int64_t n, float* hi, float* lo)
+__global__ void recip_pair_kernel(const double* __restrict__ v, int64_t n, PointOp* pv)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double r = 1.0 / v[i];
     const float h = (float)r;
-    hi[i] = h;
-    lo[i] = (float)(r - (double)h);
+    pv[i].iPh = h;
+    pv[i].iPl = (float)(r - (double)h);
 }
 
 // K_{eps,beta}^ij = 2^-u, u = ed2 * (c1 * (iP_i * iP_j)), c1 = log2(e) / (4 eps^2).  The
@@ -614,13 +614,28 @@ __global__ void op_const_kernel(const double* __restrict__ eps2, int B, C1* out)
     out[b] = r;
 }
 
+// A lane's next UNR entries with their column records gathered, all loads in flight together.
 template <int LPR>
+__device__ __forceinline__ void load_op_entries(const int32_t* __restrict__ col, const float* __restrict__ ed2,
+                                                const PointOp* __restrict__ pv, int64_t e0, int64_t re, int32_t* jj,
+                                                float* xx, PointOp* pj)
+{
+    load_entries<LPR>(col, ed2, e0, re, jj, xx);
+#pragma unroll
+    for (int u = 0; u < UNR; ++u)
+        if (jj[u] >= 0) pj[u] = pv[jj[u]];
+}
+
+// q pass: q_i = psi_i^(-beta d) sum_j K^ij; with ALPHA0 (alpha = 0, so q^-alpha = 1 and
+// K~ = K) the same row sum is also D_i, and the pass writes D, S = P D^(1/2) and 1 / S
+// too: the D pass would add the same values in the same order.
+template <int LPR, bool ALPHA0>
 __global__ void __launch_bounds__(kRowThreads) q_kernel(const int64_t* __restrict__ row_ptr,
                                                       const int32_t* __restrict__ col, const float* __restrict__ ed2,
-                                                      int64_t n, const double* __restrict__ psi,
-                                                      const float* __restrict__ iPh, const float* __restrict__ iPl,
+                                                      int64_t n, const double* __restrict__ psi, PointOp* pv,
                                                       const C1* __restrict__ cop, Clouds cl, double beta, double d,
-                                                      double alpha, double* q, float* qa)
+                                                      double alpha, double* q, const double* __restrict__ P,
+                                                      double* D, double* S)
 {
     const float mbd = (float)(-beta * d), malpha = (float)(-alpha);
     RowGroup<LPR> it;
@@ -629,21 +644,29 @@ __global__ void __launch_bounds__(kRowThreads) q_kernel(const int64_t* __restric
         const bool ok = i < n;
         const C1 c1 = cop[ok ? cloud_id(cl, i) : 0];
         const int64_t rb = ok ? row_ptr[i] : 0, re = ok ? row_ptr[i + 1] : 0;
-        const float ph = ok ? iPh[i] : 0.f, pl = ok ? iPl[i] : 0.f;
+        const float ph = ok ? pv[i].iPh : 0.f, pl = ok ? pv[i].iPl : 0.f;
         float s = 0.f;
         for (int64_t e0 = rb + it.sub; e0 < re; e0 += UNR * LPR) {
             int32_t jj[UNR];
             float xx[UNR];
-            load_entries<LPR>(col, ed2, e0, re, jj, xx);
+            PointOp pj[UNR];
+            load_op_entries<LPR>(col, ed2, pv, e0, re, jj, xx, pj);
 #pragma unroll
             for (int u = 0; u < UNR; ++u)
-                if (jj[u] >= 0) s += k_op(xx[u], ph, pl, iPh[jj[u]], iPl[jj[u]], c1.h, c1.l);
+                if (jj[u] >= 0) s += k_op(xx[u], ph, pl, pj[u].iPh, pj[u].iPl, c1.h, c1.l);
         }
-        const double tot = (double)RowGroup<LPR>::sum(s);
+        const float sum = RowGroup<LPR>::sum(s);
         if (ok && it.sub == 0) {
-            const float qi = pow_sfu((float)psi[i], mbd) * (float)tot;
+            const float qi = pow_sfu((float)psi[i], mbd) * sum;
             q[i] = (double)qi;
-            qa[i] = pow_sfu(qi, malpha);
+            pv[i].qa = pow_sfu(qi, malpha);
+            if constexpr (ALPHA0) {
+                const double tot = (double)sum;
+                const double si = P[i] * sqrt(tot);
+                D[i] = tot;
+                S[i] = si;
+                pv[i].iS = (float)(1.0 / si);
+            }
         }
     }
 }
@@ -651,10 +674,8 @@ __global__ void __launch_bounds__(kRowThreads) q_kernel(const int64_t* __restric
 template <int LPR>
 __global__ void __launch_bounds__(kRowThreads) d_kernel(const int64_t* __restrict__ row_ptr,
                                                       const int32_t* __restrict__ col, const float* __restrict__ ed2,
-                                                      int64_t n, const float* __restrict__ iPh,
-                                                      const float* __restrict__ iPl, const float* __restrict__ qa,
-                                                      const double* __restrict__ P, const C1* __restrict__ cop,
-                                                      Clouds cl, double* D, double* S, float* iS)
+                                                      int64_t n, PointOp* pv, const double* __restrict__ P,
+                                                      const C1* __restrict__ cop, Clouds cl, double* D, double* S)
 {
     RowGroup<LPR> it;
     for (int64_t b0 = it.base; b0 < n; b0 += it.step) {
@@ -662,17 +683,17 @@ __global__ void __launch_bounds__(kRowThreads) d_kernel(const int64_t* __restric
         const bool ok = i < n;
         const C1 c1 = cop[ok ? cloud_id(cl, i) : 0];
         const int64_t rb = ok ? row_ptr[i] : 0, re = ok ? row_ptr[i + 1] : 0;
-        const float ph = ok ? iPh[i] : 0.f, pl = ok ? iPl[i] : 0.f, qi = ok ? qa[i] : 0.f;
+        const PointOp pi = ok ? pv[i] : PointOp{0.f, 0.f, 0.f, 0.f};
         float s = 0.f;
         for (int64_t e0 = rb + it.sub; e0 < re; e0 += UNR * LPR) {
             int32_t jj[UNR];
             float xx[UNR];
-            load_entries<LPR>(col, ed2, e0, re, jj, xx);
+            PointOp pj[UNR];
+            load_op_entries<LPR>(col, ed2, pv, e0, re, jj, xx, pj);
 #pragma unroll
             for (int u = 0; u < UNR; ++u) {
                 if (jj[u] < 0) continue;
-                const int32_t j = jj[u];
-                s += k_op(xx[u], ph, pl, iPh[j], iPl[j], c1.h, c1.l) * (qi * qa[j]);
+                s += k_op(xx[u], pi.iPh, pi.iPl, pj[u].iPh, pj[u].iPl, c1.h, c1.l) * (pi.qa * pj[u].qa);
             }
         }
         const double tot = (double)RowGroup<LPR>::sum(s);
@@ -680,7 +701,7 @@ __global__ void __launch_bounds__(kRowThreads) d_kernel(const int64_t* __restric
             const double si = P[i] * sqrt(tot);
             D[i] = tot;
             S[i] = si;
-            iS[i] = (float)(1.0 / si);
+            pv[i].iS = (float)(1.0 / si);
         }
     }
 }
@@ -689,9 +710,8 @@ template <int LPR>
 __global__ void __launch_bounds__(kRowThreads) lhat_kernel(const int64_t* __restrict__ row_ptr,
                                                          const int32_t* __restrict__ col,
                                                          const float* __restrict__ ed2, int64_t n,
-                                                         const float* __restrict__ iPh, const float* __restrict__ iPl,
-                                                         const float* __restrict__ qa, const float* __restrict__ iS,
-                                                         const double* __restrict__ S, const C1* __restrict__ cop,
+                                                         const PointOp* __restrict__ pv, const double* __restrict__ S,
+                                                         const C1* __restrict__ cop,
                                                          const double* __restrict__ eps2_dev, Clouds cl, float* val)
 {
     RowGroup<LPR> it;
@@ -702,22 +722,23 @@ __global__ void __launch_bounds__(kRowThreads) lhat_kernel(const int64_t* __rest
         const C1 c1 = cop[cb];
         const float ie = c1.ie;
         const int64_t rb = ok ? row_ptr[i] : 0, re = ok ? row_ptr[i + 1] : 0;
-        const float ph = ok ? iPh[i] : 0.f, pl = ok ? iPl[i] : 0.f, qi = ok ? qa[i] : 0.f, si = ok ? iS[i] : 0.f;
+        const PointOp pi = ok ? pv[i] : PointOp{0.f, 0.f, 0.f, 0.f};
         float off = 0.f;
         int64_t diag = -1;
         for (int64_t e0 = rb + it.sub; e0 < re; e0 += UNR * LPR) {
             int32_t jj[UNR];
             float xx[UNR];
-            load_entries<LPR>(col, ed2, e0, re, jj, xx);
+            PointOp pj[UNR];
+            load_op_entries<LPR>(col, ed2, pv, e0, re, jj, xx, pj);
 #pragma unroll
             for (int u = 0; u < UNR; ++u) {
                 const int64_t e = e0 + u * LPR;
                 const int32_t j = jj[u];
                 if (j < 0) continue;
                 if (j == i) { diag = e; continue; }
-                const float kt = k_op(xx[u], ph, pl, iPh[j], iPl[j], c1.h, c1.l) * (qi * qa[j]);
+                const float kt = k_op(xx[u], pi.iPh, pi.iPl, pj[u].iPh, pj[u].iPl, c1.h, c1.l) * (pi.qa * pj[u].qa);
                 off += kt;
-                val[e] = kt * (si * iS[j]) * ie;
+                val[e] = kt * (pi.iS * pj[u].iS) * ie;
             }
         }
         const double tot = (double)RowGroup<LPR>::sum(off);
@@ -731,7 +752,7 @@ __global__ void __launch_bounds__(kRowThreads) lhat_kernel(const int64_t* __rest
 size_t kernel_csr_ws_bytes(int64_t n, int B)
 {
     Carve c(nullptr);
-    for (int i = 0; i < 4; ++i) c.take<float>(n);
+    c.take<PointOp>(n);
     c.take<C1>(B);
     return c.off;
 }
@@ -743,11 +764,7 @@ vb_status kernel_csr_run(Ctx* ctx, const vb_graph* g, const double* psi, const d
     if (!g || !g->row_ptr || !psi || !P || !op || !eps2_op_dev || !val || !q || !D || !S) return VB_ERR_ARG;
     if (!(op->d > 0) || cl.B < 1 || (cl.B > 1 && !cl.ptr)) return VB_ERR_ARG;
     Carve c(ws);
-    OpVec v;
-    v.iPh = c.take<float>(g->n);
-    v.iPl = c.take<float>(g->n);
-    v.qa = c.take<float>(g->n);
-    v.iS = c.take<float>(g->n);
+    PointOp* pv = c.take<PointOp>(g->n);
     C1* cop = c.take<C1>(cl.B);
     if (!ws || ws_bytes < c.off) return VB_ERR_WORKSPACE;
     // Sec. 2.2: c = 2 - 2 alpha + d beta + 2 beta
@@ -755,7 +772,7 @@ vb_status kernel_csr_run(Ctx* ctx, const vb_graph* g, const double* psi, const d
     cudaStream_t s = ctx->stream;
     const int64_t n = g->n;
     mark(ctx, VB_STAGE_OPERATOR, 0);
-    recip_pair_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, n, v.iPh, v.iPl);
+    recip_pair_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, n, pv);
     op_const_kernel<<<(unsigned)((cl.B + 255) / 256), 256, 0, s>>>(eps2_op_dev, cl.B, cop);
 #define VB_ROWS(K, ...)                                                        \
     switch (lpr) {                                                             \
@@ -763,14 +780,27 @@ vb_status kernel_csr_run(Ctx* ctx, const vb_graph* g, const double* psi, const d
         case 16: K<16><<<kRowBlocks, kRowThreads, 0, s>>>(__VA_ARGS__); break; \
         default: K<32><<<kRowBlocks, kRowThreads, 0, s>>>(__VA_ARGS__); break; \
     }
-    VB_ROWS(q_kernel, g->row_ptr, g->col, g->ed2, n, psi, v.iPh, v.iPl, cop, cl, op->beta, op->d, alpha, q, v.qa)
-    VB_ROWS(d_kernel, g->row_ptr, g->col, g->ed2, n, v.iPh, v.iPl, v.qa, P, cop, cl, D, S, v.iS)
+#define VB_ROWS2(K, A0, ...)                                                       \
+    switch (lpr) {                                                                 \
+        case 8: K<8, A0><<<kRowBlocks, kRowThreads, 0, s>>>(__VA_ARGS__); break;   \
+        case 16: K<16, A0><<<kRowBlocks, kRowThreads, 0, s>>>(__VA_ARGS__); break; \
+        default: K<32, A0><<<kRowBlocks, kRowThreads, 0, s>>>(__VA_ARGS__); break; \
+    }
+    if (alpha == 0.0) {   // K~ = K: one pass gives q, D and S
+        VB_ROWS2(q_kernel, true, g->row_ptr, g->col, g->ed2, n, psi, pv, cop, cl, op->beta, op->d, alpha, q, P, D, S)
+        ctx->launches += 1;
+    } else {
+        VB_ROWS2(q_kernel, false, g->row_ptr, g->col, g->ed2, n, psi, pv, cop, cl, op->beta, op->d, alpha, q, P, D, S)
+        VB_ROWS(d_kernel, g->row_ptr, g->col, g->ed2, n, pv, P, cop, cl, D, S)
+        ctx->launches += 2;
+    }
     mark(ctx, VB_STAGE_OPERATOR, 1);
     mark(ctx, VB_STAGE_LHAT, 0);
-    VB_ROWS(lhat_kernel, g->row_ptr, g->col, g->ed2, n, v.iPh, v.iPl, v.qa, v.iS, S, cop, eps2_op_dev, cl, val)
+    VB_ROWS(lhat_kernel, g->row_ptr, g->col, g->ed2, n, pv, S, cop, eps2_op_dev, cl, val)
 #undef VB_ROWS
+#undef VB_ROWS2
     mark(ctx, VB_STAGE_LHAT, 1);
-    ctx->launches += 5;
+    ctx->launches += 3;
     return last_launch();
 }
 

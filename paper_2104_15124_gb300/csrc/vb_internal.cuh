@@ -137,6 +137,19 @@ vb_status gradient_run(Ctx* ctx, int64_t n, int32_t ell, const double* evals, co
 size_t knn_plan(Carve& c, int64_t n, int32_t m, const vb_knn_params* p, struct KnnWs* w);
 vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_params* p, int32_t* nbr,
                   double* nbr_d2, void* ws, size_t ws_bytes, Clouds cl = Clouds());
+// The kNN search's spatial order, for other tile searches (knn.cu): sorted coordinates in FP64
+// (exact copies, [.][mp] rows), boxes of 64-point tiles ([ntiles][mp]), perm = sorted
+// position -> original index.  The pointers live in the workspace given to order_run.
+struct PointOrder {
+    const double* xs64;
+    const float* tlo;
+    const float* thi;
+    const uint32_t* perm;
+    int mp;
+    int64_t ntiles;
+};
+size_t order_ws_bytes(int64_t n, int32_t m);
+vb_status order_run(Ctx* ctx, const float* x, int64_t n, int32_t m, void* ws, size_t ws_bytes, PointOrder* o);
 // symmetric union (graph.cu)
 size_t graph_plan_bytes(int64_t n, int32_t k);
 vb_status graph_run(Ctx* ctx, int64_t n, int32_t k, const int32_t* nbr, const double* nbr_d2, int64_t* row_ptr,
@@ -174,6 +187,20 @@ size_t solve_ws_bytes(int64_t n, int64_t cap, const vb_solve_params* p);
 vb_status solve_run(Ctx* ctx, const vb_graph* g, int64_t cap, const float* val, const double* S,
                     const vb_solve_params* p, double* evals, float* phi, const float* rhs, float* f, int32_t* iters,
                     void* ws, size_t ws_bytes);
+
+// the delta_tol radius pattern and its per-grid-point sweep (radius.cu)
+size_t radius_ws_bytes(int64_t n, int32_t m);
+vb_status radius_pattern_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const double* rho, double eps2,
+                             double delta_tol, int64_t* row_ptr, int32_t* col, double* d2, int64_t cap,
+                             int64_t* nnz_dev, void* ws, size_t ws_bytes);
+vb_status radius_sweep_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const double* rho, double scale,
+                           double xi_lo, double xi_hi, double dxi, double delta_tol, double* chi, double* eps2,
+                           double* dim, void* ws, size_t ws_bytes);
+
+// particle evolution (evolve.cu): gc = g - mean(g); the explicit sample update
+vb_status evolve_centre_launch(cudaStream_t s, const float* g, int64_t n, float* gc);
+vb_status evolve_update_launch(cudaStream_t s, const float* x, int64_t n, int m, const float* u, const float* grad,
+                               const float* sigma, const float* W, double dt, float* x_next);
 
 // exclusive scan of n int32 counts into n + 1 int64 offsets (graph.cu)
 size_t scan_ws_bytes(int64_t n);
