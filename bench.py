@@ -309,7 +309,7 @@ def _train_radius(vb, spec: Spec, a, dev):
     return net, shift, infl, cloud_shift, const_r, note
 
 
-def _tile_distance_error(vb, spec: Spec, xt, fmt: str) -> dict:
+def _tile_distance_error(vb, spec: Spec, xt, fmt: str, variant: str = "auto") -> dict:
     """Relative error of the 16-bit tile distances the search kernel itself produced, against
     FP64: one vb_knn call with the diagnostic output on returns, for every row, the candidates
     its search kept and their tile distances before the FP64 rescoring; the exact squared
@@ -318,7 +318,7 @@ def _tile_distance_error(vb, spec: Spec, xt, fmt: str) -> dict:
     x = xt
     if spec.cloud_ptr is not None:
         x = xt[: int(spec.cloud_ptr[1])].contiguous()
-    nbr, nd2, idx, d16 = vb.knn(x, spec.k, tensor_cores=fmt, debug=True)
+    nbr, nd2, idx, d16 = vb.knn(x, spec.k, tensor_cores=fmt, tc_variant=variant, debug=True)
     ok = idx >= 0
     rows = torch.arange(x.shape[0], device=x.device)[:, None].expand_as(idx)[ok]
     cols = idx[ok].long()
@@ -334,7 +334,7 @@ def _tile_distance_error(vb, spec: Spec, xt, fmt: str) -> dict:
             "max_rel_to_kth": float(relk.max()), "rms_rel_to_kth": float(relk.pow(2).mean().sqrt()),
             "pairs": int(rel.numel()),
             "what": f"every kept candidate of every row ({'first cloud' if spec.cloud_ptr is not None else 'all rows'})"
-                    f", {fmt} tile distance vs FP64"}
+                    f", {fmt} tile distance ({variant} kernel, the form's autotuned choice) vs FP64"}
 
 
 def main():
@@ -369,9 +369,11 @@ def main():
         forms += ["learned_bf16_tc"] if batched else ["learned_fp32", "learned_fp16_tc", "learned_bf16_tc",
                                                       "const_radius_fp32"]
     target = TARGET.get(spec.name, "plain_fp32")
-    if a.forms:
-        keep = set(a.forms.split(",")) | {"plain_fp32", target}
+    if a.forms:   # a subset (plain_fp32, the comparison, always runs); the target heads the line if present
+        keep = set(a.forms.split(",")) | {"plain_fp32"}
         forms = [f for f in forms if f in keep]
+        if target not in forms:
+            target = "plain_fp32"
     net, shift, infl, cloud_shift, const_r = None, 0.0, 1.5, None, None
     if any(f.startswith("learned") or f.startswith("const") for f in forms):
         net, shift, infl, cloud_shift, const_r, train_note = _train_radius(vb, spec, a, dev)
@@ -562,8 +564,8 @@ def main():
         line["learned_radius"] = train_note
     if rank == 0 and not batched and spec.m <= 16:
         line["gradient"] = _gradient_timing(vb, ref, xt, peaks, src)
-    line["tile_distance_error"] = {fmt: _tile_distance_error(vb, spec, xt, fmt) for fmt in ("fp16", "bf16")
-                                   if f"{fmt}_tc" in forms}
+    line["tile_distance_error"] = {fmt: _tile_distance_error(vb, spec, xt, fmt, shapes[f"{fmt}_tc"].get("tc_variant", "auto"))
+                                   for fmt in ("fp16", "bf16") if f"{fmt}_tc" in forms}
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         v, dt, what = _oracle_points_per_s(spec)
         line["cpu_baseline"] = {"value": v, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",

@@ -242,6 +242,10 @@ vb_status vb_mlp_gradient(vb_ctx* ctx, const vb_mlp* mlp, const float* x, int32_
                           float* grad, float* loss_dev, void* ws, size_t ws_bytes);
 /* y[i] = predicted log radius of row i of x [n][ld] (BF16 weights, FP32 arithmetic). */
 vb_status vb_mlp_predict(vb_ctx* ctx, const vb_mlp* mlp, const float* x, int32_t ld, int64_t n, float* y);
+/* The same prediction on the tensor cores, as the radius-first kNN search evaluates it: 128 rows per
+ * step, each layer one chain of tcgen05.mma (BF16 x BF16, FP32 accumulation in tensor memory), so the
+ * inputs and hidden activations are rounded to BF16 (relative 2^-9) where vb_mlp_predict keeps FP32. */
+vb_status vb_mlp_predict_tc(vb_ctx* ctx, const vb_mlp* mlp, const float* x, int32_t ld, int64_t n, float* y);
 
 /* ------------------------------------------------- symmetric pattern (a6)
  * The sparsity pattern of the kernel matrices: the diagonal (Algorithm 1

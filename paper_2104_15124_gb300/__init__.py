@@ -132,6 +132,7 @@ _SIGS = {
                                    c_p, c_p, c_sz]),
     "vb_mlp_gradient": (c_i32, [c_p, ctypes.POINTER(MlpC), c_p, c_i32, c_p, c_i64, c_p, c_p, c_p, c_sz]),
     "vb_mlp_predict": (c_i32, [c_p, ctypes.POINTER(MlpC), c_p, c_i32, c_i64, c_p]),
+    "vb_mlp_predict_tc": (c_i32, [c_p, ctypes.POINTER(MlpC), c_p, c_i32, c_i64, c_p]),
     "vb_tc_dot_tile": (c_i32, [c_p, c_p, c_p, c_i32, c_i32, c_p]),
     "vb_build_workspace": (c_sz, [c_i64, c_i32, ctypes.POINTER(BuildParams)]),
     "vb_build": (c_i32, [c_p, c_p, c_i64, c_i32, ctypes.POINTER(BuildParams), ctypes.POINTER(BuildOut), c_p, c_sz]),
@@ -443,11 +444,13 @@ class Mlp:
                                      _p(loss), _p(ws), ws.numel()), "vb_mlp_gradient")
         return grad, loss
 
-    def predict(self, x: torch.Tensor) -> torch.Tensor:
+    def predict(self, x: torch.Tensor, tensor_cores: bool = False) -> torch.Tensor:
+        """Predicted log radius per row (vb_mlp_predict; vb_mlp_predict_tc, the tensor-core form the
+        radius-first search uses, with tensor_cores=True)."""
         n, ld = x.shape
         y = torch.empty(n, dtype=torch.float32, device=self.device)
-        _check(lib().vb_mlp_predict(c_p(_ctx(self.device)), ctypes.byref(self.c), _p(x), ld, n, _p(y)),
-               "vb_mlp_predict")
+        f = lib().vb_mlp_predict_tc if tensor_cores else lib().vb_mlp_predict
+        _check(f(c_p(_ctx(self.device)), ctypes.byref(self.c), _p(x), ld, n, _p(y)), "vb_mlp_predict")
         return y
 
 

@@ -2705,7 +2705,7 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
             const float inflate = p->radius_inflate > 0.f ? p->radius_inflate : 1.5f;
             if (p->mlp) {
                 st = mlp_radius_r2(s, p->mlp, w.xs, n, m, mp, p->radius_log_shift, inflate, w.r2, p->cloud_log_shift,
-                                   cl);
+                                   cl, ctx->rep);
             } else {
                 radius_gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p->radius, perm, n, inflate, w.r2);
                 st = last_launch();

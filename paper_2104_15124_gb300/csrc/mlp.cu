@@ -11,6 +11,7 @@
 // a training run is bitwise reproducible.  Adam updates the FP32 master and
 // refreshes the BF16 copy.
 #include "vb_internal.cuh"
+#include "tc.cuh"
 
 #include <cuda_bf16.h>
 
@@ -125,7 +126,7 @@ __device__ __forceinline__ float forward_infer(const MlpK& k, const float* W, co
 }
 
 // ------------------------------------------------------------------ inference
-__global__ void __launch_bounds__(128, 4) mlp_predict_kernel(MlpK k, const float* __restrict__ x, int ld, int64_t n,
+__global__ void __launch_bounds__(128) mlp_predict_kernel(MlpK k, const float* __restrict__ x, int ld, int64_t n,
                                                           float* y, int mode, float shift, float inflate,
                                                           const float* __restrict__ cloud_shift, Clouds cl)
 {
@@ -355,13 +356,175 @@ static vb_status grad_run(Ctx* ctx, const vb_mlp* m, const float* x, int ld, con
     return last_launch();
 }
 
+// ------------------------------------------------------------------ inference on the tensor cores
+// The radius guesses of the kNN search: 128 samples per step, one thread and one tensor-memory
+// lane per sample.  Layer 1 is one tcgen05.mma (M = 128 samples, N = 64 hidden units, K = 16:
+// the standardised inputs, zero-padded) and layer 2 four (K = 64), both BF16 x BF16 with FP32
+// accumulation in tensor memory; biases, GELU and the output layer run in FP32 on the values
+// read back with tcgen05.ld.  Weights (BF16) stay in shared memory as the B operands.  The
+// activations are rounded to BF16 where the FP32 forward keeps them in FP32, a relative change
+// of about 2^-9 that only moves a radius guess (the search stays exact for any guess).
+constexpr int MI = 128;   // samples per step
+constexpr uint32_t MLP_TMEM_COLS = 128;   // D1 in columns [0, 64), D2 in [64, 128)
+constexpr size_t MI_A1 = MI * 16 * 2, MI_B1 = H * 16 * 2, MI_A2 = MI * H * 2, MI_B2 = H * H * 2;
+constexpr size_t MI_SMEM = MI_A1 + MI_B1 + MI_A2 + MI_B2 + 3 * H * sizeof(float) + 16;
+
+__global__ void __launch_bounds__(MI) mlp_radius_tc_kernel(MlpK k, const float* __restrict__ xs, int ld, int64_t n,
+                                                           float* r2, int mode, float shift, float inflate,
+                                                           const float* __restrict__ cloud_shift, Clouds cl,
+                                                           DevReport* rep)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __nv_bfloat16* a1 = (__nv_bfloat16*)smem;
+    __nv_bfloat16* b1w = (__nv_bfloat16*)(smem + MI_A1);
+    __nv_bfloat16* a2 = (__nv_bfloat16*)(smem + MI_A1 + MI_B1);
+    __nv_bfloat16* b2w = (__nv_bfloat16*)(smem + MI_A1 + MI_B1 + MI_A2);
+    float* bias1 = (float*)(smem + MI_A1 + MI_B1 + MI_A2 + MI_B2);
+    float* bias2 = bias1 + H;
+    float* w3 = bias2 + H;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_abort;
+    const int t = threadIdx.x, warp = t >> 5;
+    const Off o(k.in);
+    // B operands: row j (hidden unit) holds its input weights along K
+    for (int e = t; e < H * 16; e += MI) {
+        const int j = e / 16, r = e % 16;
+        const __nv_bfloat16 v = r < k.in ? k.wb[o.w1 + j * k.in + r] : __float2bfloat16_rn(0.f);
+        *(__nv_bfloat16*)((char*)b1w + tc::operand_offset(j, r, 16)) = v;
+    }
+    for (int e = t; e < H * H; e += MI) {
+        const int j = e / H, i = e % H;
+        *(__nv_bfloat16*)((char*)b2w + tc::operand_offset(j, i, H)) = k.wb[o.w2 + j * H + i];
+    }
+    for (int j = t; j < H; j += MI) {
+        bias1[j] = __bfloat162float(k.wb[o.b1 + j]);
+        bias2[j] = __bfloat162float(k.wb[o.b2 + j]);
+        w3[j] = __bfloat162float(k.wb[o.w3 + j]);
+    }
+    const float b3 = __bfloat162float(k.wb[o.b3]);
+    if (warp == 0) tc::tmem_alloc(&tmem_base, MLP_TMEM_COLS);
+    if (t == 0) { tc::mbar_init(&bar, 1); s_abort = 0; }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tb = tmem_base;
+    const uint32_t lane_addr = tb + ((uint32_t)(warp * 32) << 16);
+    constexpr uint32_t idesc = tc::idesc_bf16(MI, H);
+    uint32_t phase = 0;
+    for (int64_t base = (int64_t)blockIdx.x * MI; base < n; base += (int64_t)gridDim.x * MI) {
+        const int64_t i = base + t;
+        const bool valid = i < n;
+        // layer-1 operand: the standardised inputs of this thread's sample, K padded to 16
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int r = 8 * c + e;
+                const float xv = valid && r < k.in ? (xs[i * ld + r] - k.mean[r]) / k.scale[r] : 0.f;
+                v[e] = __float2bfloat16_rn(xv);
+            }
+            *(uint4*)((char*)a1 + tc::operand_offset(t, 8 * c, 16)) = *(const uint4*)v;
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (t == 0) {
+            tc::mma_bf16(tb, tc::smem_desc(tc::smem_addr(a1), 128, 256), tc::smem_desc(tc::smem_addr(b1w), 128, 256),
+                         idesc, 0u);
+            tc::mma_commit(&bar);
+        }
+        bool done = tc::mbar_wait(&bar, phase);
+        phase ^= 1u;
+        tc::fence_after_sync();
+        if (__syncthreads_or(!done)) {
+            if (t == 0) { report_error(rep, VB_ERR_TIMEOUT); s_abort = 1; }
+            break;
+        }
+        {
+            float z[H];
+            tc::tmem_ld64(lane_addr, z);
+#pragma unroll
+            for (int c = 0; c < H / 8; ++c) {
+                __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16_rn(gelu(z[8 * c + e] + bias1[8 * c + e]));
+                *(uint4*)((char*)a2 + tc::operand_offset(t, 8 * c, H)) = *(const uint4*)v;
+            }
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (t == 0) {
+#pragma unroll
+            for (int sk = 0; sk < H / 16; ++sk)
+                tc::mma_bf16(tb + 64, tc::smem_desc(tc::smem_addr(a2) + sk * 256, 128, (H / 8) * 128),
+                             tc::smem_desc(tc::smem_addr(b2w) + sk * 256, 128, (H / 8) * 128), idesc, sk > 0 ? 1u : 0u);
+            tc::mma_commit(&bar);
+        }
+        done = tc::mbar_wait(&bar, phase);
+        phase ^= 1u;
+        tc::fence_after_sync();
+        if (__syncthreads_or(!done)) {
+            if (t == 0) { report_error(rep, VB_ERR_TIMEOUT); s_abort = 1; }
+            break;
+        }
+        float z[H];
+        tc::tmem_ld64(lane_addr + 64, z);
+        float out = b3;
+#pragma unroll
+        for (int j = 0; j < H; ++j) out = fmaf(w3[j], gelu(z[j] + bias2[j]), out);
+        if (valid) {
+            const float logr = k.out_mean + k.out_scale * out;
+            if (mode == 0) {
+                r2[i] = logr;
+            } else {   // squared radius bound for the radius-first kNN search
+                const float sh = cloud_shift ? shift + cloud_shift[cloud_of(cl.ptr, cl.B, i)] : shift;
+                const float r = expf(logr + sh) * inflate;
+                r2[i] = __fmul_ru(r, r);
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();   // the operands of the next step overwrite these only after every read
+    }
+    if (s_abort) {   // a bounded wait ran out: no further step was issued; the tensor memory goes back
+        tc::fence_before_sync();
+    }
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tb, MLP_TMEM_COLS);
+}
+
+static vb_status mlp_tc_launch(cudaStream_t s, const vb_mlp* mlp, const float* xs, int ld, int64_t n, float* out,
+                               int mode, float shift, float inflate, const float* cloud_shift, Clouds cl,
+                               DevReport* rep)
+{
+    static bool attr[16] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!attr[dev & 15]) {
+        if (cudaFuncSetAttribute(mlp_radius_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MI_SMEM + 1024) !=
+            cudaSuccess)
+            return VB_ERR_CUDA;
+        attr[dev & 15] = true;
+    }
+    // 4 CTAs per SM (128 tensor-memory columns each), persistent over the sample tiles
+    const int64_t tiles = (n + MI - 1) / MI;
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, 152 * 4);
+    mlp_radius_tc_kernel<<<grid, MI, MI_SMEM + 1024, s>>>(mk(mlp), xs, ld, n, out, mode, shift, inflate, cloud_shift,
+                                                          cl, rep);
+    return last_launch();
+}
+
 vb_status mlp_radius_r2(cudaStream_t s, const vb_mlp* mlp, const float* xs, int64_t n, int m, int mp, float shift,
-                        float inflate, float* r2, const float* cloud_shift, Clouds cl)
+                        float inflate, float* r2, const float* cloud_shift, Clouds cl, DevReport* rep)
 {
     if (!mlp || mlp->in_dim < 1 || mlp->in_dim > VB_MLP_MAX_IN || mlp->in_dim > m || !mlp->weights) return VB_ERR_ARG;
-    mlp_predict_kernel<<<152 * 4, 128, pred_smem(mlp->in_dim), s>>>(mk(mlp), xs, mp, n, r2, 1, shift, inflate,
-                                                                     cloud_shift, cl);
-    return last_launch();
+    return mlp_tc_launch(s, mlp, xs, mp, n, r2, 1, shift, inflate, cloud_shift, cl, rep);
 }
 
 }  // namespace vb
@@ -428,6 +591,15 @@ vb_status vb_mlp_train_epoch(vb_ctx* ctx, vb_mlp* m, const float* x, int32_t ld,
         if ((st = last_launch()) != VB_OK) return st;
     }
     return VB_OK;
+}
+
+vb_status vb_mlp_predict_tc(vb_ctx* ctx, const vb_mlp* m, const float* x, int32_t ld, int64_t n, float* y)
+{
+    if (!ctx || !m || !x || !y || n < 1 || ld < m->in_dim || m->in_dim < 1 || m->in_dim > VB_MLP_MAX_IN)
+        return VB_ERR_ARG;
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    c->launches += 1;
+    return mlp_tc_launch(c->stream, m, x, ld, n, y, 0, 0.f, 1.f, nullptr, Clouds(), c->rep);
 }
 
 vb_status vb_mlp_predict(vb_ctx* ctx, const vb_mlp* m, const float* x, int32_t ld, int64_t n, float* y)

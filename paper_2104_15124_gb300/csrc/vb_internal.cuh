@@ -180,7 +180,7 @@ vb_status spmv_run(Ctx* ctx, const vb_graph* g, const float* val, const double* 
 // learned radius (mlp.cu): R2[pos] = (inflate exp(net(xs[pos]) + shift + cloud_shift[cloud]))^2
 // for sorted points (sorted positions keep the clouds' ranges)
 vb_status mlp_radius_r2(cudaStream_t s, const vb_mlp* mlp, const float* xs, int64_t n, int m, int mp, float shift,
-                        float inflate, float* r2, const float* cloud_shift = nullptr, Clouds cl = Clouds());
+                        float inflate, float* r2, const float* cloud_shift, Clouds cl, DevReport* rep);
 
 // eigen-solve (solve.cu)
 size_t solve_ws_bytes(int64_t n, int64_t cap, const vb_solve_params* p);

@@ -97,9 +97,11 @@ def test_graph_replay_is_bitwise_identical(vb, batch):
     g.replay()
     torch.cuda.synchronize()
     vb.raise_on_device_error()
+    nnz = out.graph.nnz   # entries past nnz are never written (the caller's buffer keeps what it held)
     for f, v in eager.items():
-        assert torch.equal(getattr(out, f), v), f
-    assert torch.equal(out.graph.col, eager_col)
+        got = getattr(out, f)
+        assert torch.equal(got[:nnz] if f == "val" else got, v[:nnz] if f == "val" else v), f
+    assert torch.equal(out.graph.col[:nnz], eager_col[:nnz])
 
 
 def test_single_cloud_batch_equals_build(vb):

@@ -52,6 +52,25 @@ def test_mlp_gradient_matches_fp64_oracle(vb):
     np.testing.assert_allclose(pred, -2.0 + 0.3 * OM.forward(theta, Xs), rtol=0, atol=1e-4)
 
 
+def test_tensor_core_inference_matches_fp32_forward(vb):
+    # the tcgen05 forward of the radius-first search (BF16 activations) against the FP32 forward
+    # and the FP64 oracle at the same BF16 weights: the hidden activations' BF16 rounding (2^-9
+    # relative) bounds the difference; ragged n (not a multiple of the 128-row step)
+    x = W.sphere_vmf(3001, 2.0, 41)
+    net = vb.Mlp(3, seed=11)
+    mean, scale = x.mean(0), x.std(0)
+    net.set_standardisation(mean, scale, -3.0, 0.5)
+    p32 = net.predict(_t(x)).cpu().numpy().astype(np.float64)
+    ptc = net.predict(_t(x), tensor_cores=True).cpu().numpy().astype(np.float64)
+    theta = net.bf16_weights().cpu().numpy().astype(np.float64)
+    Xs = (x.astype(np.float64) - mean.astype(np.float32)) / scale.astype(np.float32)
+    ref = -3.0 + 0.5 * OM.forward(theta, Xs)
+    spread = np.abs(ref - ref.mean()).max() + 1e-3
+    assert np.abs(ptc - ref).max() <= 2e-2 * spread + 2e-3
+    assert np.abs(ptc - p32).max() <= 2e-2 * spread + 2e-3
+    assert np.all(np.isfinite(ptc))
+
+
 def test_training_fits_log_radius(vb):
     # von Mises-Fisher on S^2 (kappa = 2): the density, hence r_k, varies about 7-fold from pole to pole
     x = W.sphere_vmf(20000, 2.0, 103)
