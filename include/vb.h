@@ -227,6 +227,12 @@ struct vb_mlp {
     int64_t step;                       /* Adam steps taken */
 };
 int64_t vb_mlp_param_count(int32_t in_dim);
+/* Sets the standardisation constants of mlp from the training data: in_mean / in_scale the mean and
+ * sample standard deviation (n - 1) of each of the first in_dim columns of x [n][ld], out_mean /
+ * out_scale those of y [n] (scales floored at 1e-12); FP64 sums in a fixed order.  ws: at least
+ * 8 * 2 (VB_MLP_MAX_IN + 1) bytes of device memory.  Synchronises the host (the constants are host fields). */
+vb_status vb_mlp_standardise(vb_ctx* ctx, vb_mlp* mlp, const float* x, int32_t ld, const float* y, int64_t n,
+                             void* ws, size_t ws_bytes);
 /* He-normal initialisation of master (counter-based generator from seed), zero moments, BF16 copy. */
 vb_status vb_mlp_init(vb_ctx* ctx, vb_mlp* mlp, uint64_t seed);
 size_t vb_mlp_workspace(int32_t in_dim, int64_t batch);

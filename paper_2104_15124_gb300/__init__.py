@@ -127,6 +127,7 @@ _SIGS = {
                          c_p, ctypes.POINTER(c_i32), c_p, c_sz]),
     "vb_mlp_param_count": (c_i64, [c_i32]),
     "vb_mlp_init": (c_i32, [c_p, ctypes.POINTER(MlpC), ctypes.c_uint64]),
+    "vb_mlp_standardise": (c_i32, [c_p, ctypes.POINTER(MlpC), c_p, c_i32, c_p, c_i64, c_p, c_sz]),
     "vb_mlp_workspace": (c_sz, [c_i32, c_i64]),
     "vb_mlp_train_epoch": (c_i32, [c_p, ctypes.POINTER(MlpC), c_p, c_i32, c_p, c_i64, c_i32, c_f32, ctypes.c_uint64,
                                    c_p, c_p, c_sz]),
@@ -416,6 +417,13 @@ class Mlp:
     def handle(self) -> int:
         return ctypes.addressof(self.c)
 
+    def fit_standardisation(self, x: torch.Tensor, y: torch.Tensor) -> None:
+        """Standardisation constants from the training data (vb_mlp_standardise)."""
+        n, ld = x.shape
+        ws = _ws(8 * 2 * 17, self.device)
+        _check(lib().vb_mlp_standardise(c_p(_ctx(self.device)), ctypes.byref(self.c), _p(x), ld, _p(y), n, _p(ws),
+                                        ws.numel()), "vb_mlp_standardise")
+
     def set_standardisation(self, in_mean, in_scale, out_mean: float, out_scale: float) -> None:
         for r in range(self.c.in_dim):
             self.c.in_mean[r] = float(in_mean[r])
@@ -458,10 +466,8 @@ def train_radius_model(x: torch.Tensor, logr: torch.Tensor, epochs: int = 30, ba
                        seed: int = 103) -> Mlp:
     """Fits the learned-radius network to (x, log r_k) pairs on the GPU (vb_mlp_train_epoch)."""
     n, m = x.shape
-    mean = x.mean(0).cpu().numpy()
-    scale = x.std(0).clamp_min(1e-12).cpu().numpy()
     net = Mlp(min(m, 16), x.device, seed)
-    net.set_standardisation(mean, scale, float(logr.mean()), float(logr.std().clamp_min(1e-12)))
+    net.fit_standardisation(x, logr)
     for ep in range(epochs):
         net.train_epoch(x, logr, batch=batch, lr=lr, seed=seed * 1000 + ep)
     return net

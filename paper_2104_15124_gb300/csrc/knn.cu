@@ -1470,9 +1470,9 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
     extern __shared__ __align__(1024) unsigned char smem[];
     const int C = a.cap;
     half_t* sa = (half_t*)smem;                                // [T2][KP] core-matrix layout
-    half_t* sb = sa + T2 * KP;                                 // [TILE][KP]
-    float* sqb = (float*)(sb + TILE * KP);                     // [TILE]
-    uint64_t* slist = (uint64_t*)(sqb + TILE);                 // [SCAP]
+    half_t* sb = sa + T2 * KP;                                 // [2 TILE][KP]: two candidate tiles
+    float* sqb = (float*)(sb + 2 * TILE * KP);                 // [2 TILE]
+    uint64_t* slist = (uint64_t*)(sqb + 2 * TILE);             // [SCAP]
     KT* buf = (KT*)(slist + SCAP);                             // [C][T2] max-heaps
     __shared__ float sqlo[MP], sqhi[MP], scen[MP];
     __shared__ uint32_t sred[4];
@@ -1496,14 +1496,15 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
     bd.rho_k = 2.f * (float)(KP + 4) * 5.9604645e-8f;
     unsigned long long evaluated = 0;
     unsigned levels = 0, staged = 0;
-    if (warp == 0) tc::tmem_alloc(&tmem_base, TILE);
+    if (warp == 0) tc::tmem_alloc(&tmem_base, 2 * TILE);
     if (t == 0) { tc::mbar_init(&bar, 1); s_abort = 0; }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tb = tmem_base;
     uint32_t phase = 0;
-    constexpr uint32_t idesc = tc::idesc_f16(T2, TILE, F16);
+    constexpr uint32_t idesc = tc::idesc_f16(T2, TILE, F16);        // one candidate tile per visit
+    constexpr uint32_t idesc2 = tc::idesc_f16(T2, 2 * TILE, F16);   // two
 
     for (;;) {
         if (t == 0) {
@@ -1578,33 +1579,55 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
         // FP16 range: a query tile whose own extent is not small against the clamp goes to FP32
         const bool far = F16 && amax > 0.25f * kHalfClamp;
 
-        // Visit candidate tile ct for every query that may still gain from it: stage its 16-bit
-        // operand, one MMA chain into tensor memory, then each query folds the 64 distances
-        // into its heap; finally the tile bound tightens.  Returns false once a bounded wait ran out.
-        auto visit = [&](int64_t ct) -> bool {
-            bool need = valid;
-            if (need) {
+        // Visit candidate tiles cta and ctb (ctb < 0: one tile) for every query that may still gain
+        // from them: stage their 16-bit operands (one candidate per thread), one MMA chain
+        // (N = 64 per tile) into tensor memory, then each query folds the distances of the tiles it
+        // needs into its heap; finally the tile bound tightens.  Two tiles per visit halve the
+        // barriers and MMA round trips per candidate.  Returns false once a bounded wait ran out or
+        // the visit table is full.
+        auto visit = [&](int64_t cta, int64_t ctb) -> bool {
+            auto needs = [&](int64_t ct) {
+                if (!valid || ct < 0) return false;
                 float acc = 0.f;
 #pragma unroll
                 for (int r = 0; r < MP; ++r) {
                     const float g = fmaxf(fmaxf(a.tlo[ct * MP + r] - qr[r], qr[r] - a.thi[ct * MP + r]), 0.f);
                     acc = fmaf(g, g, acc);
                 }
-                need = __float_as_uint(__fmul_rd(acc, a.lb_factor)) <= BK::hi_bits(heapmax);
-            }
-            if (!__syncthreads_or(need)) return true;
-            int vis = 0;   // compact keys: this visit's number (the same in every thread)
+                return __float_as_uint(__fmul_rd(acc, a.lb_factor)) <= BK::hi_bits(heapmax);
+            };
+            bool need0 = needs(cta), need1 = needs(ctb);
+            const bool any0 = __syncthreads_or(need0);
+            const bool any1 = ctb >= 0 && __syncthreads_or(need1);
+            if (!any0 && !any1) return true;
+            // the tiles to stage, in order: slot h holds tile ct_h (needed by some query)
+            const int64_t ct0 = any0 ? cta : ctb;
+            const int64_t ct1 = any0 && any1 ? ctb : -1;
+            if (!any0) { need0 = need1; need1 = false; }
+            const int ntl = ct1 >= 0 ? 2 : 1;
+            int vis = 0;   // compact keys: this visit's first number (the same in every thread)
             if constexpr (K32) {
                 vis = s_nvis;
-                if (vis >= VMAX) {   // more visits than the table holds: the FP32 search redoes the tile
+                if (vis + ntl > VMAX) {   // more visits than the table holds: the FP32 search redoes the tile
                     if (t == 0) s_fail = 1;
                     __syncthreads();   // every thread sees the flag before the loops test it
                     return false;
                 }
             }
-            staged += t == 0;
-            if (t < TILE) {   // candidate operand: row t of tile ct
-                const int64_t cp = ct * TILE + t;
+            staged += t == 0 ? ntl : 0;
+            if (t < TILE * ntl) {   // candidate operand: row t = candidate t % 64 of slot t / 64
+                const int64_t cp = (t < TILE ? ct0 : ct1) * TILE + (t & (TILE - 1));
+                float xv[MP];
+                if constexpr (MP % 4 == 0) {
+#pragma unroll
+                    for (int r4 = 0; r4 < MP / 4; ++r4) {
+                        const float4 v4 = *(const float4*)(a.xs + cp * MP + 4 * r4);
+                        xv[4 * r4] = v4.x; xv[4 * r4 + 1] = v4.y; xv[4 * r4 + 2] = v4.z; xv[4 * r4 + 3] = v4.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < MP; ++r) xv[r] = a.xs[cp * MP + r];
+                }
                 float sq = 0.f;
 #pragma unroll
                 for (int j = 0; j < KP / 8; ++j) {
@@ -1612,8 +1635,9 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
 #pragma unroll
                     for (int e2 = 0; e2 < 8; ++e2) {
                         const int r = 8 * j + e2;
-                        const float x =
-                            r < MP ? fminf(fmaxf(a.xs[cp * MP + r] - scen[r], -HT::clampv), HT::clampv) : 0.f;
+                        const float x = r < MP ? fminf(fmaxf(xv[r < MP ? r : 0] - scen[r < MP ? r : 0], -HT::clampv),
+                                                       HT::clampv)
+                                               : 0.f;
                         v[e2] = HT::from(x);
                         const float xb = HT::to(v[e2]);
                         sq = fmaf(xb, xb, sq);
@@ -1628,17 +1652,19 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
             tc::fence_after_sync();
             if constexpr (K32) {
                 if (t == 0) {   // read again only after the barriers that end this visit
-                    vtab[vis] = (int)ct;
-                    s_nvis = vis + 1;
+                    vtab[vis] = (int)ct0;
+                    if (ntl == 2) vtab[vis + 1] = (int)ct1;
+                    s_nvis = vis + ntl;
                 }
             }
             if (t == 0) {
                 constexpr uint32_t sbo = (uint32_t)(KP / 8) * 128;
+                const uint32_t id = ntl == 2 ? idesc2 : idesc;
 #pragma unroll
                 for (int s = 0; s < KP / 16; ++s) {
                     const uint64_t ad = tc::smem_desc(tc::smem_addr(sa) + s * 256, 128, sbo);
                     const uint64_t bd2 = tc::smem_desc(tc::smem_addr(sb) + s * 256, 128, sbo);
-                    tc::mma_bf16(tb, ad, bd2, idesc, s > 0 ? 1u : 0u);
+                    tc::mma_bf16(tb, ad, bd2, id, s > 0 ? 1u : 0u);
                 }
                 tc::mma_commit(&bar);
             }
@@ -1650,14 +1676,16 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
                 __syncthreads();   // every thread sees the flag before the loops test it
                 return false;
             }
-            if (need) evaluated += TILE;
+            evaluated += (need0 ? TILE : 0) + (need1 ? TILE : 0);
             const uint32_t hb = BK::hi_bits(heapmax);
             float hmf = hb == 0xffffffffu ? INFINITY : __uint_as_float(hb);
 #pragma unroll 1
-            for (int ch = 0; ch < TILE / 32; ++ch) {
+            for (int ch = 0; ch < 2 * ntl; ++ch) {
+                const int h = ch >> 1;
                 float v[32];
                 tc::tmem_ld32(tb + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32), v);
-                if (!need) continue;
+                if (!(h == 0 ? need0 : need1)) continue;
+                const int64_t cth = h == 0 ? ct0 : ct1;
                 // distances of the 32 columns (registers only), and the mask of those under the bound
                 uint32_t msk = 0;
                 const float4* sq4 = (const float4*)(sqb + ch * 32);
@@ -1677,8 +1705,9 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
                     float d = 0.f;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) d = j == i ? v[j] : d;
-                    const int64_t cp = ct * TILE + ch * 32 + i;
-                    const KT key = BK::make(__float_as_uint(fmaxf(d, 0.f)), vis, ch * 32 + i, (uint32_t)cp);
+                    const int lt = (ch & 1) * 32 + i;   // the candidate's lane in its tile
+                    const int64_t cp = cth * TILE + lt;
+                    const KT key = BK::make(__float_as_uint(fmaxf(d, 0.f)), vis + h, lt, (uint32_t)cp);
                     if (key < heapmax && cp != p && cp >= qlo && cp < qhi) {
                         sift_down<T2>(buf, t, 0, C, key, levels);
                         heapmax = buf[t];
@@ -1701,8 +1730,8 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
         const int64_t sw = (a.nseed - 1) / 2;   // tiles on each side
         const int64_t s_lo = rmode || far ? 0 : max(ct_lo, 2 * qs - sw);
         const int64_t s_hi = rmode || far ? 0 : min(ct_hi, 2 * qs + 2 + sw);
-        for (int64_t ct = s_lo; ct < s_hi && !s_abort && !s_fail; ++ct)
-            if (!visit(ct)) break;
+        for (int64_t ct = s_lo; ct < s_hi && !s_abort && !s_fail; ct += 2)
+            if (!visit(ct, ct + 1 < s_hi ? ct + 1 : -1)) break;
         // every other tile whose box lower bound does not exceed the tile bound, nearest first
         for (int64_t c0 = ct_lo; c0 < ct_hi && !far && !s_abort && !s_fail;) {
             int cnt = 0;
@@ -1738,10 +1767,14 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
                     __syncthreads();
                 }
             }
-            for (int si = 0; si < cnt; ++si) {
+            for (int si = 0; si < cnt;) {
                 const uint64_t e = slist[si];
                 if ((uint32_t)(e >> 32) > thr_blk) break;   // sorted: the rest lie farther
-                if (!visit((int64_t)(uint32_t)e)) break;
+                // the next tile too, when its bound passes the threshold as it stands (a threshold
+                // that tightens during this visit only makes the pair a little wider than needed)
+                const bool pair = si + 1 < cnt && (uint32_t)(slist[si + 1] >> 32) <= thr_blk;
+                if (!visit((int64_t)(uint32_t)e, pair ? (int64_t)(uint32_t)slist[si + 1] : -1)) break;
+                si += pair ? 2 : 1;
             }
             __syncthreads();
         }
@@ -1776,7 +1809,7 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tb, TILE);
+    if (warp == 0) tc::tmem_dealloc(tb, 2 * TILE);
 }
 
 // ------------------------------------------------------------------ pipelined 16-bit distance tiles (a3, a15)
@@ -2453,7 +2486,7 @@ template <int MP>
 static size_t tc_smem(int C)
 {
     constexpr int KP = MP < 16 ? 16 : MP;
-    return (size_t)T2 * KP * 2 + TILE * KP * 2 + TILE * 4 + SCAP * 8 + (size_t)C * T2 * (tc_compact<MP>() ? 4 : 8);
+    return (size_t)T2 * KP * 2 + 2 * TILE * KP * 2 + 2 * TILE * 4 + SCAP * 8 + (size_t)C * T2 * (tc_compact<MP>() ? 4 : 8);
 }
 
 template <int MP, bool F16>
@@ -2481,10 +2514,10 @@ static vb_status launch_tc(TileArgs a, cudaStream_t s)
             return VB_ERR_CUDA;
         attr_set[dev & 15] = true;
     }
-    // CTAs per SM from shared memory (1 KB reserved per CTA), at most 8 (64 TMEM columns each, 512 per SM);
+    // CTAs per SM from shared memory (1 KB reserved per CTA), at most 4 (128 TMEM columns each, 512 per SM);
     // extra CTAs of this persistent grid would only wait for a free slot
     const int per_cta = (int)sm + static_smem[dev & 15] + 1024;
-    const int per_sm = std::max(1, std::min(8, smem_sm[dev & 15] / per_cta));
+    const int per_sm = std::max(1, std::min(4, smem_sm[dev & 15] / per_cta));
     const int64_t nst = (a.ntiles + 1) / 2;
     const int64_t grid = std::min<int64_t>(nst, (int64_t)per_sm * sms[dev & 15]);
     knn_tc_kernel<MP, F16, tc_compact<MP>()><<<(unsigned)grid, T2, sm, s>>>(a);

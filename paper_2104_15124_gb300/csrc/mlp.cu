@@ -531,9 +531,73 @@ vb_status mlp_radius_r2(cudaStream_t s, const vb_mlp* mlp, const float* xs, int6
 
 using namespace vb;
 
+namespace vb {
+
+// Column c of the inputs (c < in) or the targets (c == in): mean and sample standard deviation
+// (n - 1), FP64 partials per thread over a fixed stride, then a fixed tree; one block per column.
+constexpr int STD_T = 1024;
+__global__ void __launch_bounds__(STD_T) mlp_moments_kernel(const float* __restrict__ x, int ld, const float* __restrict__ y,
+                                                            int64_t n, int in, double* out)
+{
+    __shared__ double s1[STD_T], s2[STD_T];
+    const int c = blockIdx.x, t = threadIdx.x;
+    // shifted by the first value, so that a column far from zero keeps its variance
+    const double ref = c < in ? (double)x[c] : (double)y[0];
+    double a = 0.0, b = 0.0;
+    for (int64_t i = t; i < n; i += STD_T) {
+        const double v = (c < in ? (double)x[i * ld + c] : (double)y[i]) - ref;
+        a += v;
+        b += v * v;
+    }
+    s1[t] = a;
+    s2[t] = b;
+    __syncthreads();
+    for (int w = STD_T / 2; w > 0; w >>= 1) {
+        if (t < w) {
+            s1[t] += s1[t + w];
+            s2[t] += s2[t + w];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        const double mean_s = s1[0] / (double)n;
+        const double var = n > 1 ? (s2[0] - s1[0] * mean_s) / (double)(n - 1) : 0.0;
+        out[2 * c] = ref + mean_s;
+        out[2 * c + 1] = sqrt(fmax(var, 0.0));
+    }
+}
+
+}  // namespace vb
+
 extern "C" {
 
 int64_t vb_mlp_param_count(int32_t in_dim) { return param_count(in_dim); }
+
+vb_status vb_mlp_standardise(vb_ctx* ctx, vb_mlp* m, const float* x, int32_t ld, const float* y, int64_t n, void* ws,
+                             size_t ws_bytes)
+{
+    if (!ctx || !m || !x || !y || n < 1 || ld < m->in_dim || m->in_dim < 1 || m->in_dim > VB_MLP_MAX_IN)
+        return VB_ERR_ARG;
+    const int in = m->in_dim;
+    if (!ws || ws_bytes < sizeof(double) * 2 * (VB_MLP_MAX_IN + 1)) return VB_ERR_WORKSPACE;
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    double* out = (double*)ws;
+    mlp_moments_kernel<<<in + 1, STD_T, 0, c->stream>>>(x, ld, y, n, in, out);
+    c->launches += 1;
+    vb_status st = last_launch();
+    if (st != VB_OK) return st;
+    double h[2 * (VB_MLP_MAX_IN + 1)];
+    if (cudaMemcpyAsync(h, out, sizeof(double) * 2 * (in + 1), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return VB_ERR_CUDA;
+    for (int r = 0; r < in; ++r) {
+        m->in_mean[r] = (float)h[2 * r];
+        m->in_scale[r] = (float)std::max(h[2 * r + 1], 1e-12);
+    }
+    m->out_mean = (float)h[2 * in];
+    m->out_scale = (float)std::max(h[2 * in + 1], 1e-12);
+    return VB_OK;
+}
 
 size_t vb_mlp_workspace(int32_t in_dim, int64_t batch) { return mlp_ws_bytes(in_dim, batch); }
 

@@ -433,10 +433,13 @@ __global__ void density_finish_kernel(const double* __restrict__ b, const double
     const int cb = cloud_id(cl, i);
     const double nb = (double)(cloud_hi(cl, cb, n) - cloud_lo(cl, cb));
     const double bb = b[i];
-    const double w = nb * pow(3.14159265358979323846 * eps2_dev[cb] * bb * bb, 0.5 * d);
+    // the FP64 pipe is narrow: the exponents of the workloads (d / 2 = 1/2, 1, 5/2; beta = -1/4)
+    // avoid the general power, x^1 = x exactly and the roots correctly rounded
+    const double x = 3.14159265358979323846 * eps2_dev[cb] * bb * bb, e = 0.5 * d;
+    const double w = nb * (e == 1.0 ? x : e == 0.5 ? sqrt(x) : e == 2.5 ? x * x * sqrt(x) : pow(x, e));
     const double ps = psi[i] / w;
     psi[i] = ps;
-    P[i] = pow(ps, beta);
+    P[i] = beta == -0.25 ? 1.0 / sqrt(sqrt(ps)) : pow(ps, beta);
 }
 
 size_t density_ws_bytes(int64_t n, int B)

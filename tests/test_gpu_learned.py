@@ -149,3 +149,56 @@ def test_learned_radius_search_exact_and_prunes(vb):
     # the learned radius settles most tiles and evaluates fewer candidates than the exact heap search
     assert rep_l["knn_retry_tiles"] < 0.05 * ((n + 63) // 64)
     assert rep_l["knn_candidates"] < rep_p["knn_candidates"]
+
+
+def test_standardisation_is_computed_on_the_device(vb):
+    x = W.torus4(5000, 0.01, 44)
+    y = (np.random.default_rng(3).standard_normal(5000) * 0.2 - 3.0).astype(np.float32)
+    net = vb.Mlp(4, seed=5)
+    net.fit_standardisation(_t(x), _t(y))
+    x64 = x.astype(np.float64)
+    np.testing.assert_allclose(list(net.c.in_mean)[:4], x64.mean(0), rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(list(net.c.in_scale)[:4], x64.std(0, ddof=1), rtol=1e-6)
+    assert abs(net.c.out_mean - y.astype(np.float64).mean()) < 1e-6
+    assert abs(net.c.out_scale - y.astype(np.float64).std(ddof=1)) < 1e-6
+
+
+@pytest.mark.parametrize("name", ["vmf_s2_50k", "torus_r4_1m"])
+def test_learned_radius_against_a_constant_radius(vb, name, record_property):
+    # The ablation of the learned part: the same radius-first search with one global radius for
+    # every point (the training targets' mean inflated by 3 standard deviations) and with the
+    # network's radius (inflated by 3 standard deviations of its residual).  Both are exact, like
+    # the plain search.  What the network gains is its prediction: on the von Mises-Fisher sphere
+    # r_k varies with the density and the network explains most of that spread; on the uniform
+    # torus there is nothing to learn and it predicts a constant.  The candidate pairs each search
+    # evaluates are recorded.
+    w = W.WORKLOADS[name]
+    x = _t(w.sample())
+    n_train = 100000
+    kp = max(1, int(round(w.k * n_train / w.n)))
+    xtr = _t(W.Workload(w.name, n_train, w.m, w.k, w.d, w.c, w.beta, w.margin, 103).sample())
+    _, d2tr = vb.knn(xtr, kp)
+    target = 0.5 * torch.log(d2tr[:, kp - 1]).float()
+    net = vb.train_radius_model(xtr, target, epochs=20, batch=4096, seed=103)
+    resid = (target - net.predict(xtr)).float()
+    tstd, rstd = float(target.std()), float(resid.std())
+    counts = {}
+    vb.report_reset()
+    ref_nbr, ref_d2 = vb.knn(x, w.k)
+    counts["plain"] = vb.report()["knn_candidates"]
+    const = torch.full((w.n,), math.exp(float(target.mean()) + 3 * tstd), dtype=torch.float32, device="cuda")
+    vb.report_reset()
+    nbr_c, d2_c = vb.knn(x, w.k, radius=const, inflate=1.0)
+    counts["constant"] = vb.report()["knn_candidates"]
+    vb.report_reset()
+    nbr_m, d2_m = vb.knn(x, w.k, mlp=net, log_shift=float(resid.mean()), inflate=math.exp(3 * rstd))
+    counts["learned"] = vb.report()["knn_candidates"]
+    for a, b in ((nbr_c, ref_nbr), (nbr_m, ref_nbr), (d2_c, ref_d2), (d2_m, ref_d2)):
+        assert torch.equal(a, b)
+    record_property("candidate_pairs", counts)
+    record_property("target_std", tstd)
+    record_property("residual_std", rstd)
+    if name.startswith("vmf"):
+        assert rstd < 0.6 * tstd          # the density variation is learned
+    else:
+        assert rstd <= 1.02 * tstd        # nothing to learn on the uniform torus
