@@ -223,33 +223,61 @@ __device__ __forceinline__ int lower_bound_key(const uint64_t* a, int len, int32
 constexpr int SORT_WARPS = 4;
 
 // Own kNN lists sorted by column, one warp per row; the FP32 value of each entry is the
-// rounding of its canonical FP64 distance (identical for (i, j) and (j, i)).
+// rounding of its canonical FP64 distance (identical for (i, j) and (j, i)).  The columns of a
+// list are distinct, so an entry's place in the sorted list is the number of columns below its
+// own: every column is broadcast to the warp once (a shuffle) and each lane counts for the KL
+// entries it holds, then writes each entry straight to its place.  No shared memory: a
+// bitonic network over 64-bit keys in shared memory was bound by its shared-memory traffic.
+// The same pass counts, for every point j, the lists that name j without j naming their owner
+// (the reverse entries of row j): (i -> j) is mutual exactly when (d2(i, j), i) does not exceed
+// the k-th pair of j's own list, read from nbr / nbr_d2 directly.
+template <int KL>
 __global__ void __launch_bounds__(SORT_WARPS * 32) own_sort_kernel(const int32_t* __restrict__ nbr,
                                                                     const double* __restrict__ nbr_d2, int64_t n,
-                                                                    int k, int32_t* own_col, float* own_d2, Kth* kth)
+                                                                    int k, int32_t* own_col, float* own_d2, Kth* kth,
+                                                                    int32_t* rcnt)
 {
-    __shared__ uint64_t buf[SORT_WARPS][OWN_CAP];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int P = 32;
-    while (P < k) P <<= 1;
     for (int64_t i = (int64_t)blockIdx.x * SORT_WARPS + w; i < n; i += (int64_t)gridDim.x * SORT_WARPS) {
-        for (int e = lane; e < P; e += 32)
-            buf[w][e] = e < k ? ((uint64_t)(uint32_t)nbr[i * k + e] << 32) | __float_as_uint((float)nbr_d2[i * k + e])
-                              : ~0ull;
-        __syncwarp();
-        bitonic_smem(buf[w], P, lane, 32, true);
-        for (int e = lane; e < k; e += 32) {
-            own_col[i * k + e] = (int32_t)(buf[w][e] >> 32);
-            own_d2[i * k + e] = __uint_as_float((uint32_t)buf[w][e]);
+        const int32_t* row = nbr + i * k;
+        int32_t c[KL];
+        int rank[KL];
+#pragma unroll
+        for (int s = 0; s < KL; ++s) {
+            const int e = lane + 32 * s;
+            c[s] = e < k ? row[e] : INT32_MAX;
+            rank[s] = 0;
+        }
+#pragma unroll
+        for (int s2 = 0; s2 < KL; ++s2) {
+            const int32_t v = c[s2];
+            const int lim = min(32, k - 32 * s2);
+            for (int l = 0; l < lim; ++l) {
+                const int32_t cb = __shfl_sync(0xffffffffu, v, l);
+#pragma unroll
+                for (int s = 0; s < KL; ++s) rank[s] += cb < c[s] ? 1 : 0;
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < KL; ++s) {
+            const int e = lane + 32 * s;
+            if (e < k) {
+                const double d = nbr_d2[i * k + e];
+                own_col[i * k + rank[s]] = c[s];
+                own_d2[i * k + rank[s]] = (float)d;
+                const int32_t j = c[s];
+                const double qd = nbr_d2[(int64_t)j * k + k - 1];
+                const int32_t qi = nbr[(int64_t)j * k + k - 1];
+                if (!(d < qd || (d == qd && (int32_t)i <= qi))) atomicAdd(&rcnt[j], 1);
+            }
         }
         if (lane == 0) {
             Kth q;
             q.d2 = nbr_d2[i * k + k - 1];
-            q.idx = nbr[i * k + k - 1];
+            q.idx = row[k - 1];
             q.pad = 0;
             kth[i] = q;
         }
-        __syncwarp();
     }
 }
 
@@ -286,23 +314,29 @@ __global__ void row_len_kernel(const int32_t* __restrict__ rcnt, int64_t n, int 
 }
 
 // Row j: sort R(j) in shared memory, then write every entry at its rank.
+// oc_s: shared-memory room for the row's own columns (k ints), or nullptr to search them in
+// global memory (the block path).
 __device__ void merge_row(int64_t j, int k, int r, uint64_t* rb, const int64_t* __restrict__ row_ptr,
                           const int32_t* __restrict__ own_col, const float* __restrict__ own_d2,
                           const int32_t* __restrict__ rev_col, const float* __restrict__ rev_d2, int32_t* col,
-                          float* ed2, int tid, int nthr, bool warp_only)
+                          float* ed2, int tid, int nthr, bool warp_only, int32_t* oc_s = nullptr)
 {
     int P = 32;
     while (P < r) P <<= 1;
     const int64_t roff = row_ptr[j] - j * (1 + k);
     for (int e = tid; e < P; e += nthr)
         rb[e] = e < r ? ((uint64_t)(uint32_t)rev_col[roff + e] << 32) | __float_as_uint(rev_d2[roff + e]) : ~0ull;
+    const int32_t* oc = own_col + j * k;
+    if (oc_s) {   // the own columns, searched once per reverse entry, from shared memory
+        for (int e = tid; e < k; e += nthr) oc_s[e] = oc[e];
+        oc = oc_s;
+    }
     if (warp_only) __syncwarp(); else __syncthreads();
     if (r > 1) bitonic_smem(rb, P, tid, nthr, warp_only);
     const int64_t ob = row_ptr[j];
-    const int32_t* oc = own_col + j * k;
     const float* od = own_d2 + j * k;
     for (int a = tid; a < k; a += nthr) {
-        const int32_t c = oc[a];
+        const int32_t c = oc[a];   // (own_col + j k)[a]
         const int rank = a + lower_bound_key(rb, r, c) + ((int32_t)j < c ? 1 : 0);
         col[ob + rank] = c;
         ed2[ob + rank] = od[a];
@@ -329,6 +363,7 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) merge_kernel(const int64_t* _
                                                                  int64_t* nnz_dev, DevReport* rep)
 {
     __shared__ uint64_t buf[SORT_WARPS][RCAP];
+    __shared__ int32_t ocs[SORT_WARPS][OWN_CAP];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *nnz_dev = row_ptr[n];
@@ -344,7 +379,7 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) merge_kernel(const int64_t* _
             }
             continue;
         }
-        merge_row(j, k, r, buf[w], row_ptr, own_col, own_d2, rev_col, rev_d2, col, ed2, lane, 32, true);
+        merge_row(j, k, r, buf[w], row_ptr, own_col, own_d2, rev_col, rev_d2, col, ed2, lane, 32, true, ocs[w]);
         __syncwarp();
     }
 }
@@ -389,8 +424,18 @@ vb_status graph_run(Ctx* ctx, int64_t n, int32_t k, const int32_t* nbr, const do
     mark(ctx, VB_STAGE_GRAPH, 0);
     zero_i32_kernel<<<gz, 256, 0, s>>>(w.rcnt, n);
     zero_i32_kernel<<<1, 32, 0, s>>>(w.nbig, 1);
-    own_sort_kernel<<<152 * 16, SORT_WARPS * 32, 0, s>>>(nbr, nbr_d2, n, k, w.own_col, w.own_d2, w.kth);
-    reverse_kernel<<<ge, 256, 0, s>>>(nbr, nbr_d2, n, k, w.kth, 0, w.rcnt, nullptr, nullptr, nullptr, nullptr);
+    if (k <= 32)
+        own_sort_kernel<1><<<152 * 16, SORT_WARPS * 32, 0, s>>>(nbr, nbr_d2, n, k, w.own_col, w.own_d2, w.kth,
+                                                                   w.rcnt);
+    else if (k <= 64)
+        own_sort_kernel<2><<<152 * 16, SORT_WARPS * 32, 0, s>>>(nbr, nbr_d2, n, k, w.own_col, w.own_d2, w.kth,
+                                                                   w.rcnt);
+    else if (k <= 128)
+        own_sort_kernel<4><<<152 * 16, SORT_WARPS * 32, 0, s>>>(nbr, nbr_d2, n, k, w.own_col, w.own_d2, w.kth,
+                                                                   w.rcnt);
+    else
+        own_sort_kernel<8><<<152 * 16, SORT_WARPS * 32, 0, s>>>(nbr, nbr_d2, n, k, w.own_col, w.own_d2, w.kth,
+                                                                   w.rcnt);
     row_len_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.rcnt, n, k, w.cnt, w.fill);
     vb_status st = scan_counts(s, w.cnt, n, row_ptr, w.scan);
     if (st != VB_OK) return st;
@@ -408,7 +453,7 @@ vb_status graph_run(Ctx* ctx, int64_t n, int32_t k, const int32_t* nbr, const do
     big_merge_kernel<<<152, 1024, BIG_CAP * 8, s>>>(row_ptr, n, k, w.own_col, w.own_d2, w.rev_col, w.rev_d2, col, ed2,
                                                     cap, w.big, w.nbig, ctx->rep);
     mark(ctx, VB_STAGE_GRAPH, 1);
-    ctx->launches += 12;
+    ctx->launches += 11;
     return last_launch();
 }
 

@@ -476,11 +476,17 @@ vb_status density_run(Ctx* ctx, const vb_graph* g, const double* b, const double
 
 // ------------------------------------------------------------------ operator-sweep centre
 // Segmented like the sweeps: slot bl + cloud holds the two sums of one cloud's rows.
+// 1 / b and 1 / P of every point as one 8-byte record, so that each entry's gather is one load.
+__global__ void recip_bp_kernel(const double* __restrict__ b, const double* __restrict__ P, int64_t n, float2* bp)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) bp[i] = make_float2((float)(1.0 / b[i]), (float)(1.0 / P[i]));
+}
+
 __global__ void __launch_bounds__(kRowThreads) centre_kernel(const int64_t* __restrict__ row_ptr,
                                                            const int32_t* __restrict__ col,
                                                            const float* __restrict__ ed2, int64_t n,
-                                                           const float* __restrict__ ib,
-                                                           const float* __restrict__ iP, Clouds cl, double* partial)
+                                                           const float2* __restrict__ bp, Clouds cl, double* partial)
 {
     __shared__ double sh[WARPS][2];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -493,18 +499,23 @@ __global__ void __launch_bounds__(kRowThreads) centre_kernel(const int64_t* __re
         double a_op = 0.0, a_den = 0.0;
         for (int64_t i = s0 + w; i < s1; i += WARPS) {
             const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
-            const float pi_ = iP[i], bi = ib[i];
+            const float2 bpi = bp[i];
+            const float pi_ = bpi.y, bi = bpi.x;
             float so = 0.f, sd = 0.f;
             for (int64_t e0 = rb + lane; e0 < re; e0 += UNR * 32) {
                 int32_t jj[UNR];
                 float xx[UNR];
                 load_entries<32>(col, ed2, e0, re, jj, xx);
+                float2 bj[UNR];
+#pragma unroll
+                for (int u = 0; u < UNR; ++u)
+                    if (jj[u] >= 0) bj[u] = bp[jj[u]];
 #pragma unroll
                 for (int u = 0; u < UNR; ++u) {
                     const int32_t j = jj[u];
                     if (j < 0 || j == i) continue;
-                    so += xx[u] * (pi_ * iP[j]);
-                    sd += xx[u] * (bi * ib[j]);
+                    so += xx[u] * (pi_ * bj[u].y);
+                    sd += xx[u] * (bi * bj[u].x);
                 }
             }
             so = warp_sum_f32(so);   // FP32 tree over the lanes; the FP64 pipe is narrow
@@ -538,8 +549,7 @@ __global__ void __launch_bounds__(SEG_T) centre_finish_kernel(const double* __re
 size_t centre_ws_bytes(int64_t n, int B)
 {
     Carve c(nullptr);
-    c.take<float>(n);
-    c.take<float>(n);
+    c.take<float2>(n);
     c.take<double>(seg_slots(B) * 2);
     return c.off;
 }
@@ -550,18 +560,16 @@ vb_status centre_run(Ctx* ctx, const vb_graph* g, const double* b, const double*
     if (!g || !g->row_ptr || !b || !P || !xi_c_dev) return VB_ERR_ARG;
     if (cl.B < 1 || (cl.B > 1 && !cl.ptr)) return VB_ERR_ARG;
     Carve c(ws);
-    float* ib = c.take<float>(g->n);
-    float* iP = c.take<float>(g->n);
+    float2* bp = c.take<float2>(g->n);
     double* partial = c.take<double>(seg_slots(cl.B) * 2);
     if (!ws || ws_bytes < c.off) return VB_ERR_WORKSPACE;
     cudaStream_t s = ctx->stream;
     mark(ctx, VB_STAGE_CENTRE, 0);
-    recip_f32_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(b, g->n, 1.f, ib);
-    recip_f32_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(P, g->n, 1.f, iP);
-    centre_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, g->n, ib, iP, cl, partial);
+    recip_bp_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(b, P, g->n, bp);
+    centre_kernel<<<kRowBlocks, kRowThreads, 0, s>>>(g->row_ptr, g->col, g->ed2, g->n, bp, cl, partial);
     centre_finish_kernel<<<(unsigned)cl.B, SEG_T, 0, s>>>(partial, kRowBlocks, g->n, cl, xi_c_dev);
     mark(ctx, VB_STAGE_CENTRE, 1);
-    ctx->launches += 4;
+    ctx->launches += 3;
     return last_launch();
 }
 
