@@ -244,6 +244,17 @@ def _gradient_timing(vb, out, xt, peaks, src, ell: int = 16, reps: int = 10) -> 
             "what": f"4 passes over the (ell + 1) x n FP32 eigenvectors + u, x, S, grad; peak hbm_gbs {src}"}
 
 
+KNN_SEARCH_STAGES = ("knn_radius", "knn_tile", "knn_retry")   # the search proper: radius, first pass, retry
+
+
+def _stage_kernel(stage: str, form: str, shape: dict) -> str:
+    """The kernel that does a stage's work (the stage's other launches are small set-up passes)."""
+    if stage == "knn_tile" and form.endswith("_tc"):
+        return "knn_tcp_kernel" if shape.get("tc_variant") == "pipelined" else "knn_tc_kernel"
+    return {"knn_tile": "knn_tile_kernel", "knn_retry": "knn_tile_kernel", "knn_radius": "mlp_radius_tc_kernel",
+            "sweep_density": "sweep57_kernel", "sweep_operator": "sweep57_kernel"}.get(stage, stage)
+
+
 def _traffic(stage: str, form: str, workload: str):
     """DRAM bytes (read + write) per launch of the dominant kernel, from the ncu capture
     recorded in profiles/traffic.json, or None when there is none for this kernel, form and
@@ -480,7 +491,8 @@ def main():
     stage_ms = r0["stage_ms"]
     rep = r0["rep"]
     steps_prof = max(3, min(a.steps, 10))
-    cand = rep["knn_candidates"] / steps_prof
+    cand_retry = rep["knn_retry_candidates"] / steps_prof          # the exact pass over handed-back tiles
+    cand = rep["knn_candidates"] / steps_prof - cand_retry          # the first search pass
     off = nnz - spec.n
     G = 57
     KP = (spec.m + 15) // 16 * 16
@@ -502,12 +514,20 @@ def main():
                     "frac": ach / tensor_tflops,
                     "what": f"{int(cand)} candidate pairs x 2 m (m = {spec.m}; the MMA runs K = {KP}) FLOP of "
                             f"16-bit tcgen05.mma; peak = dense bf16 {src} (FP16 rate equal)"}
-        if stage == "knn_tile":
-            ach = cand * (3 * spec.m + 2) / s / 1e9
+        if stage in ("knn_tile", "knn_retry"):
+            c = cand if stage == "knn_tile" else cand_retry
+            ach = c * (3 * spec.m + 2) / s / 1e9
             peak = N_SM * FP32_PER_SM_CLK * f_mhz * 1e6 / 1e9
             return {"bound": "alu", "unit": "Gop/s", "achieved": ach, "peak": peak, "frac": ach / peak,
-                    "what": f"{int(cand)} candidate pairs x {3 * spec.m + 2} FP32 ops "
+                    "what": f"{int(c)} candidate pairs x {3 * spec.m + 2} FP32 ops "
                             f"({N_SM} SM x {FP32_PER_SM_CLK} lanes x {f_mhz:.0f} MHz)"}
+        if stage == "knn_radius" and best.startswith("learned"):
+            flop = spec.n * 2 * (16 * 64 + 64 * 64)
+            ach = flop / s / 1e12
+            return {"bound": "tensor", "unit": "TFLOP/s", "achieved": ach, "peak": tensor_tflops,
+                    "frac": ach / tensor_tflops,
+                    "what": f"2 (16 x 64 + 64 x 64) FLOP per point of two BF16 tcgen05.mma layers; "
+                            f"peak = dense bf16 {src}"}
         mpad = 1 << max(2, (spec.m - 1).bit_length())
         per = {"knn_order": (spec.n, 12 * spec.m + 64 + 8 * mpad), "graph": (nnz, 40), "bandwidth": (spec.n, 8 * spec.k + 8),
                "density": (nnz, 12), "centre": (nnz, 12), "operator": (nnz, 24), "lhat": (nnz, 16),
@@ -520,10 +540,12 @@ def main():
                                                         f"(algorithmic), peak hbm_gbs {src}"}
 
     kernels = {k: dict(ms=round(v, 4), **(roof(k) or {})) for k, v in stage_ms.items()}
+    knn_ms = sum(stage_ms.get(k, 0.0) for k in KNN_SEARCH_STAGES)
     dom = max(stage_ms, key=stage_ms.get)
     droof = roof(dom) or {"bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": None}
     droof = {kk: droof[kk] for kk in ("bound", "achieved", "peak", "unit", "frac", "what") if kk in droof}
-    droof["kernel"] = dom
+    droof["stage"] = dom
+    droof["kernel"] = _stage_kernel(dom, best, shapes[best])
     droof["traffic"] = _traffic(dom, best, spec.name)
 
     sizes = np.diff(spec.cloud_ptr) if batched else np.array([spec.n])
@@ -537,7 +559,7 @@ def main():
             "data": "synthetic", "config": cfg,
             "forms": {f: {"ms_per_step": 1e3 * res[f]["total_s"] / a.steps,
                           "points_per_s": job_throughput(spec.n, a.steps, ws, res[f]["total_s"]),
-                          "knn_ms": round(res[f]["stage_ms"].get("knn_tile", 0.0), 4),
+                          "knn_ms": round(sum(res[f]["stage_ms"].get(k, 0.0) for k in KNN_SEARCH_STAGES), 4),
                           "knn_candidate_pairs": res[f]["rep"]["knn_candidates"] // steps_prof,
                           "knn_retry_tiles": res[f]["rep"]["knn_retry_tiles"] // steps_prof,
                           "knn_fallback_rows": res[f]["rep"]["knn_fallback_rows"] // steps_prof,
@@ -550,10 +572,11 @@ def main():
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s / a.steps},
             "gpu_launches": int(r0["launches"] * a.steps), "roofline": droof, "kernels": kernels,
             "knn": {"candidate_pairs_per_step": int(cand),
-                    "candidate_pairs_per_s": cand / (stage_ms["knn_tile"] / 1e3) if "knn_tile" in stage_ms else None,
-                    "n2_equivalent_pairs_per_s": (pairs_all / ((stage_ms.get("knn_order", 0.0) + stage_ms["knn_tile"]
+                    "candidate_pairs_per_s": (cand + cand_retry) / (knn_ms / 1e3) if knn_ms else None,
+                    "retry_candidate_pairs_per_step": int(cand_retry),
+                    "n2_equivalent_pairs_per_s": (pairs_all / ((stage_ms.get("knn_order", 0.0) + knn_ms
                                                                + stage_ms.get("knn_fallback", 0.0)) / 1e3)
-                                                  if "knn_tile" in stage_ms else None),
+                                                  if knn_ms else None),
                     "n2_equivalent_note": "n (n - 1) pairs (per cloud, summed) over the whole kNN stage time: the "
                                           "rate a brute-force search would need, not pairs evaluated",
                     "heap_levels_per_step": rep["knn_heap_levels"] // steps_prof,

@@ -81,6 +81,7 @@ typedef struct {
     int64_t knn_rows_short;     /* rows with fewer than k candidates kept (radius too small) */
     int64_t knn_rows_long_run;  /* rows whose FP32/16-bit ties or error band exceeded the exact-order buffer */
     int64_t knn_rows_uncertified; /* rows whose k-th FP64 distance did not clear the certificate bound */
+    int64_t knn_retry_candidates; /* the part of knn_candidates evaluated by the exact FP32 pass over handed-back tiles */
 } vb_report;
 
 /* Waits for the context's stream and copies the device report to *out. */
@@ -92,7 +93,7 @@ vb_status vb_report_reset(vb_ctx* ctx);
  * stage below is bracketed by CUDA events on the context's stream, and the
  * host counts the kernel launches it enqueues. */
 #define VB_STAGE_KNN_ORDER       0   /* bounding box, Morton keys, radix sort, gather, tile and super-tile boxes */
-#define VB_STAGE_KNN_TILE        1   /* tiled FP32 search, FP64 rescoring and certificate */
+#define VB_STAGE_KNN_TILE        1   /* first search pass (FP32 or 16-bit tiles), FP64 rescoring and certificate */
 #define VB_STAGE_KNN_FALLBACK    2   /* exact FP64 selection of uncertified rows */
 #define VB_STAGE_GRAPH           3   /* symmetric union CSR */
 #define VB_STAGE_BANDWIDTH       4
@@ -102,7 +103,9 @@ vb_status vb_report_reset(vb_ctx* ctx);
 #define VB_STAGE_SWEEP_OPERATOR  8
 #define VB_STAGE_OPERATOR        9   /* q and D passes */
 #define VB_STAGE_LHAT           10   /* L-hat CSR values */
-#define VB_NUM_STAGES           11
+#define VB_STAGE_KNN_RADIUS     11   /* per-point search radius (learned model or caller's radii) */
+#define VB_STAGE_KNN_RETRY      12   /* exact FP32 search of the query tiles the first pass handed back */
+#define VB_NUM_STAGES           13
 vb_status vb_profile_enable(vb_ctx* ctx, int32_t on);
 /* Synchronises the stream; ms[s] = duration of stage s in its most recent run
  * since the last read (negative when it did not run); *launches = kernels

@@ -88,7 +88,7 @@ class Report(ctypes.Structure):
     _fields_ = [("error", c_i32), ("warnings", c_i32), ("knn_fallback_rows", c_i64), ("knn_candidates", c_i64),
                 ("union_big_rows", c_i64), ("knn_heap_levels", c_i64), ("knn_tiles_staged", c_i64),
                 ("knn_insert_rounds", c_i64), ("knn_retry_tiles", c_i64), ("knn_rows_short", c_i64),
-                ("knn_rows_long_run", c_i64), ("knn_rows_uncertified", c_i64)]
+                ("knn_rows_long_run", c_i64), ("knn_rows_uncertified", c_i64), ("knn_retry_candidates", c_i64)]
 
 
 _SIGS = {
@@ -229,7 +229,7 @@ def raise_on_device_error(device=None) -> dict:
 
 
 STAGES = ("knn_order", "knn_tile", "knn_fallback", "graph", "bandwidth", "sweep_density", "density", "centre",
-          "sweep_operator", "operator", "lhat")
+          "sweep_operator", "operator", "lhat", "knn_radius", "knn_retry")
 
 
 def profile_enable(on: bool = True, device=None) -> None:

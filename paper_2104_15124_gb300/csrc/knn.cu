@@ -805,7 +805,8 @@ __device__ bool finalize_row(const TileArgs& a, K* arr, int t, int size, bool is
             const K key = r0 + u < size ? arr[(r0 + u) * COLS + t] : EMPTY;
             if constexpr (K32) {
                 const uint32_t slot = key & 0x3fffu, q = (key >> 14) << 13;
-                cpb[u] = key == EMPTY ? 0xffffffffu : (uint32_t)vtab[slot >> 6] * TILE + (slot & 63u);
+                // slot 0x3fff: an empty slot or a radius sentinel (visit numbers stop at VMAX - 1)
+                cpb[u] = slot == 0x3fffu ? 0xffffffffu : (uint32_t)vtab[slot >> 6] * TILE + (slot & 63u);
                 dfb[u] = __uint_as_float(q);
                 dfh[u] = __uint_as_float(q | 0x1fffu);
             } else {
@@ -862,7 +863,9 @@ __device__ bool finalize_row(const TileArgs& a, K* arr, int t, int size, bool is
     // excludes the candidates beyond it even in a small cloud, so the certificate decides there
     if ((ncl - 1 <= (int64_t)size && !a.r2) || Hkey == EMPTY) return true;
     float B;
-    if constexpr (K32) B = __uint_as_float((Hkey >> 14) << 13);   // lower edge of its bucket
+    // the lower edge of the largest kept key's bucket; a radius sentinel's own bucket holds no
+    // excluded candidate (one there has a smaller key and is kept), so the next bucket's edge
+    if constexpr (K32) B = __uint_as_float(((Hkey >> 14) + ((Hkey & 0x3fffu) == 0x3fffu ? 1u : 0u)) << 13);
     else B = __uint_as_float((uint32_t)(Hkey >> 32));
     const bool cert = isfinite(B) && dk < (double)B * a.cert_factor - (double)a.m * 1.1754943508222875e-38;
     if (!cert) atomicAdd(&a.rep->knn_rows_uncertified, 1ull);
@@ -902,7 +905,7 @@ struct Band {
 // kernel at m <= 16): the distance bits truncated to 18 << 14 | slot, slot = visit << 6 | lane,
 // with the CTA's table of the tile of every visit; slot 0x3fff marks a sentinel.  A compact key
 // stands for a bucket [lo, hi] of distances: lo bounds every distance of the bucket from
-// below (the scan's stop test and the certificate use it), hi from above (the filter).
+// below (the scan's stop test), hi from above (the filter).
 template <class K> struct BandKey;
 template <> struct BandKey<uint64_t> {
     static constexpr uint64_t EMPTY = ~0ull;
@@ -915,6 +918,7 @@ template <> struct BandKey<uint64_t> {
         return ((uint64_t)dbits << 32) | cp;
     }
     static __device__ __forceinline__ uint64_t sentinel(uint32_t r2bits) { return ((uint64_t)r2bits << 32) | 0xffffffffu; }
+    static __device__ __forceinline__ float excl(uint64_t k) { return lo(k); }
 };
 template <> struct BandKey<uint32_t> {
     static constexpr uint32_t EMPTY = ~0u;
@@ -930,6 +934,12 @@ template <> struct BandKey<uint32_t> {
         return ((dbits >> 13) << 14) | ((uint32_t)vis << 6) | (uint32_t)lane;
     }
     static __device__ __forceinline__ uint32_t sentinel(uint32_t r2bits) { return ((r2bits >> 13) << 14) | 0x3fffu; }
+    // a lower bound of every candidate left out of a heap whose largest key is k: a sentinel's
+    // own bucket holds none (a candidate there has a smaller key and is kept)
+    static __device__ __forceinline__ float excl(uint32_t k)
+    {
+        return __uint_as_float(((k >> 14) + (none(k) ? 1u : 0u)) << 13);
+    }
 };
 
 template <int MP, int COLS, class K = uint64_t>
@@ -1010,7 +1020,7 @@ __device__ bool finalize_row_band(const TileArgs& a, K* arr, int t, int size, in
     // every candidate was kept (a small cloud without a radius, or an unfilled heap); with a
     // radius the candidates beyond it were never kept, so the certificate decides
     if ((ncl - 1 <= (int64_t)size && !a.r2) || Hkey == BK::EMPTY) return true;
-    const double B = (double)BK::lo(Hkey);
+    const double B = (double)BK::excl(Hkey);
     const bool cert = isfinite(B) && dk < 4e8 &&
                       dk < (B - bd.E(qn, dk, B)) * a.cert_factor - (double)a.m * 1.1754943508222875e-38;
     if (!cert) atomicAdd(&a.rep->knn_rows_uncertified, 1ull);
@@ -1122,16 +1132,20 @@ __global__ void __launch_bounds__(TILE, MP <= 8 ? 10 : 8) knn_tile_kernel(TileAr
         KT maxkey = KO::EMPTY;
         int fill = 0;               // keys stored so far; the heap is ordered once it holds L
         uint32_t thr_blk = 0xffffffffu;
-        const bool rmode = !K32 && a.r2 != nullptr;   // compact keys: plain search only
-        if constexpr (!K32) if (rmode) {
+        const bool rmode = a.r2 != nullptr;
+        KT sentinel = KO::EMPTY;
+        if (rmode) {
             // radius-first: every slot starts as a sentinel at the query's radius bound, so only
-            // candidates inside the radius ever enter and tiles are pruned from the start
+            // candidates inside the radius ever enter and tiles are pruned from the start (appending
+            // the first L keys and ordering them once instead was slower: the one-time heapify of a
+            // lane holds up its warp)
             const float R2 = valid ? __fmul_ru(a.r2[p], a.r2_scale) : 0.f;
-            const uint64_t sentinel = ((uint64_t)__float_as_uint(R2) << 32) | 0xffffffffu;
+            if constexpr (K32) sentinel = ((__float_as_uint(R2) >> 13) << 14) | 0x3fffu;   // slot 0x3fff: no candidate
+            else sentinel = ((uint64_t)__float_as_uint(R2) << 32) | 0xffffffffu;
             for (int sl = 0; sl < L; ++sl) heap[sl * TILE + t] = sentinel;
             fill = L;
             maxkey = sentinel;
-            const uint32_t wmax = __reduce_max_sync(0xffffffffu, valid ? __float_as_uint(R2) : 0u);
+            const uint32_t wmax = __reduce_max_sync(0xffffffffu, valid ? KO::dist_hi(sentinel) : 0u);
             if (lane == 0) sred[warp] = wmax;
         }
         __syncthreads();
@@ -1408,7 +1422,10 @@ __global__ void __launch_bounds__(TILE, MP <= 8 ? 10 : 8) knn_tile_kernel(TileAr
     unsigned long long ev = evaluated;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
-    if (lane == 0 && ev) atomicAdd(&a.rep->knn_candidates, ev);
+    if (lane == 0 && ev) {
+        atomicAdd(&a.rep->knn_candidates, ev);
+        if (a.tile_list) atomicAdd(&a.rep->knn_retry_candidates, ev);   // the pass over handed-back tiles
+    }
     unsigned long long lv = levels, st = staged, rd = rounds;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -2735,6 +2752,7 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
     int launches = 0;
     if (radius_first || tensor) {
         if (radius_first) {
+            mark(ctx, VB_STAGE_KNN_RADIUS, 0);
             const float inflate = p->radius_inflate > 0.f ? p->radius_inflate : 1.5f;
             if (p->mlp) {
                 st = mlp_radius_r2(s, p->mlp, w.xs, n, m, mp, p->radius_log_shift, inflate, w.r2, p->cloud_log_shift,
@@ -2744,6 +2762,7 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
                 st = last_launch();
             }
             if (st != VB_OK) return st;
+            mark(ctx, VB_STAGE_KNN_RADIUS, 1);
             launches += 1;
         }
         if (cudaMemsetAsync(w.fail_flag, 0, sizeof(int) * 2 * ntiles, s) != cudaSuccess) return VB_ERR_CUDA;
@@ -2803,11 +2822,12 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
                 }
             }
         } else {
-            launches += 1;   // search
+            launches += 1;   // radius-first FP32 search: compact keys at m <= 16 as in the plain search
+            const bool compact = p->heap_keys != VB_KEYS_FULL && mp <= 16;
             switch (mp) {
-                case 4: st = launch_tile<4>(a, s); break;
-                case 8: st = launch_tile<8>(a, s); break;
-                case 16: st = launch_tile<16>(a, s); break;
+                case 4: st = compact ? launch_tile<4, true>(a, s) : launch_tile<4>(a, s); break;
+                case 8: st = compact ? launch_tile<8, true>(a, s) : launch_tile<8>(a, s); break;
+                case 16: st = compact ? launch_tile<16, true>(a, s) : launch_tile<16>(a, s); break;
                 case 32: st = launch_tile<32>(a, s); break;
                 case 64: st = launch_tile<64>(a, s); break;
                 default: st = launch_tile<128>(a, s); break;
@@ -2841,6 +2861,12 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
         a.work = w.fb_count + 2;
         a.tile_list = w.fail_list;
         a.tile_count = w.fb_count + 3;
+    }
+    // the exact FP32 search: the only pass, or the second over the tiles the first handed back
+    const bool retry = a.tile_list != nullptr;
+    if (retry) {
+        mark(ctx, VB_STAGE_KNN_TILE, 1);
+        mark(ctx, VB_STAGE_KNN_RETRY, 0);
     } else {
         mark(ctx, VB_STAGE_KNN_TILE, 0);
     }
@@ -2853,7 +2879,7 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
         default: st = launch_tile<128>(a, s); break;
     }
     if (st != VB_OK) return st;
-    mark(ctx, VB_STAGE_KNN_TILE, 1);
+    mark(ctx, retry ? VB_STAGE_KNN_RETRY : VB_STAGE_KNN_TILE, 1);
     mark(ctx, VB_STAGE_KNN_FALLBACK, 0);
     ctx->launches += launches;
     knn_fallback_kernel<<<152, FB_THREADS, 0, s>>>(x, n, m, p->k, w.fb_list, w.fb_count, cl, nbr, nbr_d2);

@@ -22,6 +22,7 @@ struct DevReport {
     unsigned long long knn_rows_short;
     unsigned long long knn_rows_long_run;
     unsigned long long knn_rows_uncertified;
+    unsigned long long knn_retry_candidates;
 };
 static_assert(sizeof(DevReport) == sizeof(vb_report), "report layout");
 
