@@ -329,7 +329,9 @@ def _tile_distance_error(vb, spec: Spec, xt, fmt: str, variant: str = "auto") ->
     x = xt
     if spec.cloud_ptr is not None:
         x = xt[: int(spec.cloud_ptr[1])].contiguous()
-    nbr, nd2, idx, d16 = vb.knn(x, spec.k, tensor_cores=fmt, tc_variant=variant, debug=True)
+    # full heap keys: the diagnostic output is the FP32 tile distance itself (compact keys would
+    # give the lower edge of its 2^-10 bucket)
+    nbr, nd2, idx, d16 = vb.knn(x, spec.k, tensor_cores=fmt, tc_variant=variant, debug=True, heap_keys="full")
     ok = idx >= 0
     rows = torch.arange(x.shape[0], device=x.device)[:, None].expand_as(idx)[ok]
     cols = idx[ok].long()
@@ -345,7 +347,7 @@ def _tile_distance_error(vb, spec: Spec, xt, fmt: str, variant: str = "auto") ->
             "max_rel_to_kth": float(relk.max()), "rms_rel_to_kth": float(relk.pow(2).mean().sqrt()),
             "pairs": int(rel.numel()),
             "what": f"every kept candidate of every row ({'first cloud' if spec.cloud_ptr is not None else 'all rows'})"
-                    f", {fmt} tile distance ({variant} kernel, the form's autotuned choice) vs FP64"}
+                    f", {fmt} tile distance ({variant} kernel, the form's autotuned choice; full heap keys) vs FP64"}
 
 
 def main():

@@ -172,13 +172,16 @@ typedef struct {
                                 kernel centres its operands on the whole cloud, not on each query tile,
                                 so its 16-bit error band is wider: exact either way, but with BF16 many
                                 rows go back to the FP32 search */
-    int32_t heap_keys;       /* FP32 search (not radius-first), m <= 16: VB_KEYS_COMPACT (default: 32-bit
-                                heap keys, half the shared memory, first pass; tiles that need more than
-                                255 candidate-tile visits or fail the certificate are redone with full
-                                keys) or VB_KEYS_FULL (64-bit keys only; always when m > 16) */
+    int32_t heap_keys;       /* m <= 16: VB_KEYS_COMPACT (default: 32-bit heap keys, half the shared memory;
+                                in the FP32 search, tiles that need more than 255 candidate-tile visits or
+                                fail the certificate are redone with full keys, and so are the tiles a
+                                radius-first or 16-bit first pass hands back) or VB_KEYS_FULL (64-bit keys
+                                only; always when m > 16).  The staged 16-bit search keeps compact keys at
+                                m <= 16 except with VB_KEYS_FULL at m <= 4 */
     float* dbg_d2;           /* diagnostic (NULL = off), 16-bit searches: n x (k + margin) device floats; row i
                                 receives the 16-bit tile distances of the candidates its search kept, ascending,
-                                before the FP64 rescoring (the kernel's own tile arithmetic) */
+                                before the FP64 rescoring (the kernel's own tile arithmetic; with compact keys
+                                the lower edge of the key's bucket, 2^-10 relative below the distance) */
     int32_t* dbg_idx;        /* with dbg_d2: n x (k + margin) device int32, the original index of each of those
                                 candidates (-1 for an unused slot) */
 } vb_knn_params;

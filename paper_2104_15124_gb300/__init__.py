@@ -208,11 +208,7 @@ def report(device=None) -> dict:
         if not isinstance(device, torch.device) else device
     r = Report()
     _check(lib().vb_report_read(c_p(_ctx(dev)), ctypes.byref(r)), "vb_report_read")
-    return dict(error=r.error, warnings=r.warnings, knn_fallback_rows=r.knn_fallback_rows,
-                knn_candidates=r.knn_candidates, union_big_rows=r.union_big_rows, knn_heap_levels=r.knn_heap_levels,
-                knn_tiles_staged=r.knn_tiles_staged, knn_insert_rounds=r.knn_insert_rounds,
-                knn_retry_tiles=r.knn_retry_tiles, knn_rows_short=r.knn_rows_short,
-                knn_rows_long_run=r.knn_rows_long_run, knn_rows_uncertified=r.knn_rows_uncertified)
+    return {name: getattr(r, name) for name, _ in Report._fields_}
 
 
 def report_reset(device=None) -> None:

@@ -56,7 +56,8 @@ struct KnnWs {
     float* slo;           // ceil(ntiles / 64) * MP: boxes of super-tiles (64 consecutive tiles)
     float* shi;
     int* fb_list;         // n
-    int* fb_count;        // [0] fallback rows, [1] next query tile, [2] next failed tile, [3] failed tiles
+    int* fb_count;        // [0] fallback rows, [1] next query tile, [2] next failed tile, [3] failed tiles,
+                          // [4] next tile of the second list, [5] tiles in it
     float* r2;            // n (radius search: squared radius bound per sorted point)
     int* fail_flag;       // 2 ntiles: flags of radius passes 1 and 2
     int* fail_list;       // 2 ntiles: tiles left by passes 1 and 2
@@ -698,6 +699,47 @@ __device__ __forceinline__ void sift_down(K* heap, int t, int i, int size, K key
     heap[i * COLS + t] = key;
 }
 
+// The same for a D-ary max-heap (children of node i: D i + 1 .. D i + D).  The D child loads
+// of a level are independent, so a level costs one shared-memory round trip, and the heap is
+// log_D of its size deep: fewer dependent round trips per insertion than the binary heap's.
+template <int COLS, int D, class K>
+__device__ __forceinline__ void sift_down_d(K* heap, int t, int i, int size, K key, unsigned& levels)
+{
+    for (;;) {
+        const int c = D * i + 1;
+        if (c >= size) break;
+        ++levels;
+        K ck[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) ck[j] = c + j < size ? heap[(c + j) * COLS + t] : (K)0;   // 0: no child
+        K best = ck[0];
+        int bc = c;
+#pragma unroll
+        for (int j = 1; j < D; ++j)
+            if (ck[j] > best) { best = ck[j]; bc = c + j; }
+        if (best <= key) break;
+        heap[i * COLS + t] = best;
+        i = bc;
+    }
+    heap[i * COLS + t] = key;
+}
+
+// v[i] for a run-time i in [0, N), N a power of two, from registers: a tree of selects on the
+// bits of i, log2 N deep, instead of a chain of N dependent ones.
+template <int N> struct Pick {
+    static __device__ __forceinline__ float get(const float* v, int i)
+    {
+        float h[N / 2];
+        const bool b = i & 1;
+#pragma unroll
+        for (int j = 0; j < N / 2; ++j) h[j] = b ? v[2 * j + 1] : v[2 * j];
+        return Pick<N / 2>::get(h, i >> 1);
+    }
+};
+template <> struct Pick<1> {
+    static __device__ __forceinline__ float get(const float* v, int) { return v[0]; }
+};
+
 // Floyd's bottom-up construction of a max-heap over heap[0..size).
 template <int COLS = TILE, class K>
 __device__ __forceinline__ void heapify(K* heap, int t, int size, unsigned& levels)
@@ -883,12 +925,17 @@ __device__ bool finalize_row(const TileArgs& a, K* arr, int t, int size, bool is
 // bound covers exactly the candidates that could still enter the row.
 struct Band {
     float u, dabs, rho_k;   // unit roundoff, absolute term, 2 (K + 4) 2^-24
-    __device__ double E(double qn, double D, double d) const
+    // E_D(d) with sD = sqrt(D) rounded up.  Evaluated in FP32: its own rounding (a few ulps over
+    // the dozen operations) is far inside the outer factor 1.02 (the bound itself needs 1.01),
+    // and the absolute floor covers subnormal intermediates; an overflow gives +inf, which only
+    // makes the scan longer or the certificate fail.
+    __device__ __forceinline__ float E(float qn, float sD, float d) const
     {
-        const double Z = 1.01 * (2.0 * qn + sqrt(D));
-        const double delta = (double)u * Z * 1.01 + (double)dabs;
-        return 1.01 * (2.0 * sqrt(fmax(d, 0.0)) * delta + delta * delta + (double)rho_k * Z * Z);
+        const float Z = 1.01f * (2.f * qn + sD);
+        const float delta = u * Z * 1.01f + dabs;
+        return 1.02f * (2.f * __fsqrt_ru(fmaxf(d, 0.f)) * delta + delta * delta + rho_k * Z * Z) + 1e-37f;
     }
+    static __device__ __forceinline__ float root_up(double D) { return __fsqrt_ru(__double2float_ru(D)); }
 };
 
 // Rescoring for 16-bit distance tiles, whose error band is wide enough that long
@@ -942,16 +989,16 @@ template <> struct BandKey<uint32_t> {
     }
 };
 
-template <int MP, int COLS, class K = uint64_t>
+template <int MP, int COLS, class K = uint64_t, int D = 2>
 __device__ bool finalize_row_band(const TileArgs& a, K* arr, int t, int size, int64_t pq, int64_t ncl,
                                   unsigned& levels, const Band& bd, float qn, const int* vtab = nullptr)
 {
     using BK = BandKey<K>;
-    for (int e = size - 1; e > 0; --e) {
+    for (int e = size - 1; e > 0; --e) {   // heap sort (arr is a D-ary max-heap)
         const K top = arr[t];
         const K key = arr[e * COLS + t];
         arr[e * COLS + t] = top;
-        sift_down<COLS>(arr, t, 0, e, key, levels);
+        sift_down_d<COLS, D>(arr, t, 0, e, key, levels);
     }
     const K Hkey = arr[(size - 1) * COLS + t];
     const uint32_t oq = a.perm[pq];
@@ -974,18 +1021,22 @@ __device__ bool finalize_row_band(const TileArgs& a, K* arr, int t, int size, in
     }
     int out = 0;
     double dk = INFINITY;
+    float sD = INFINITY;        // sqrt(dk), rounded up
+    double dlast = 0.0;         // the row's last entry so far, (od, on)[out - 1], kept in registers
+    int32_t ilast = 0;
     bool done = false;
     // keys are taken FB at a time: their index and coordinate loads are issued together
     for (int r0 = 0; r0 < size && !done; r0 += FB) {
         uint32_t cpb[FB];
         int32_t ojb[FB];
-        double djb[FB], dfb[FB];
+        double djb[FB];
+        float dfb[FB];
 #pragma unroll
         for (int u = 0; u < FB; ++u) {
             const K key = r0 + u < size ? arr[(r0 + u) * COLS + t] : BK::EMPTY;
             const bool none = BK::none(key);
             cpb[u] = none ? 0xffffffffu : BK::pos(key, vtab);
-            dfb[u] = (double)BK::lo(key);
+            dfb[u] = BK::lo(key);
             ojb[u] = 0;
             djb[u] = 0.0;
             if (!none) {
@@ -998,31 +1049,69 @@ __device__ bool finalize_row_band(const TileArgs& a, K* arr, int t, int size, in
         for (int u = 0; u < FB; ++u) {
             if (done) break;
             if (cpb[u] == 0xffffffffu) { done = true; break; }   // sentinel: nothing further was kept
-            if (out == k && (dfb[u] - bd.E(qn, dk, dfb[u])) * a.cert_factor > dk) { done = true; break; }
+            if (out == k && (double)__fsub_rd(dfb[u], bd.E(qn, sD, dfb[u])) * a.cert_factor > dk) {
+                done = true;
+                break;
+            }
             const double dj = djb[u];
             const int32_t oj = ojb[u];
-            if (out == k && !(dj < dk || (dj == dk && oj < on[k - 1]))) continue;
-            int pos = out < k ? out++ : k - 1;
-            while (pos > 0) {
-                const double dp = od[pos - 1];
-                const int32_t ip = on[pos - 1];
-                if (dp < dj || (dp == dj && ip < oj)) break;
-                od[pos] = dp;
-                on[pos] = ip;
-                --pos;
+            // insertion into the row, sorted by (d2, index); keys arrive nearly in order, so the
+            // common case appends after the last entry, which is compared from registers
+            if (out < k) {
+                int pos = out;
+                if (out > 0 && !(dlast < dj || (dlast == dj && ilast < oj))) {
+                    od[pos] = dlast;   // the last entry moves up one; it stays the last
+                    on[pos] = ilast;
+                    --pos;
+                    while (pos > 0) {
+                        const double dp = od[pos - 1];
+                        const int32_t ip = on[pos - 1];
+                        if (dp < dj || (dp == dj && ip < oj)) break;
+                        od[pos] = dp;
+                        on[pos] = ip;
+                        --pos;
+                    }
+                } else {
+                    dlast = dj;
+                    ilast = oj;
+                }
+                od[pos] = dj;
+                on[pos] = oj;
+                if (++out == k) {
+                    dk = dlast;
+                    sD = Band::root_up(dk);
+                }
+            } else {
+                if (!(dj < dlast || (dj == dlast && oj < ilast))) continue;
+                // the last entry drops out; the new one goes in below it
+                double ld = dj;
+                int32_t li = oj;
+                int pos = k - 1;
+                while (pos > 0) {
+                    const double dp = od[pos - 1];
+                    const int32_t ip = on[pos - 1];
+                    if (dp < dj || (dp == dj && ip < oj)) break;
+                    od[pos] = dp;
+                    on[pos] = ip;
+                    if (pos == k - 1) { ld = dp; li = ip; }
+                    --pos;
+                }
+                od[pos] = dj;
+                on[pos] = oj;
+                dlast = ld;
+                ilast = li;
+                dk = dlast;
+                sD = Band::root_up(dk);
             }
-            od[pos] = dj;
-            on[pos] = oj;
-            if (out == k) dk = od[k - 1];
         }
     }
     if (out < k) { atomicAdd(&a.rep->knn_rows_short, 1ull); return false; }
     // every candidate was kept (a small cloud without a radius, or an unfilled heap); with a
     // radius the candidates beyond it were never kept, so the certificate decides
     if ((ncl - 1 <= (int64_t)size && !a.r2) || Hkey == BK::EMPTY) return true;
-    const double B = (double)BK::excl(Hkey);
+    const float B = BK::excl(Hkey);
     const bool cert = isfinite(B) && dk < 4e8 &&
-                      dk < (B - bd.E(qn, dk, B)) * a.cert_factor - (double)a.m * 1.1754943508222875e-38;
+                      dk < (double)__fsub_rd(B, bd.E(qn, sD, B)) * a.cert_factor - (double)a.m * 1.1754943508222875e-38;
     if (!cert) atomicAdd(&a.rep->knn_rows_uncertified, 1ull);
     return cert;
 }
@@ -1260,10 +1349,7 @@ __global__ void __launch_bounds__(TILE, MP <= 8 ? 10 : 8) knn_tile_kernel(TileAr
                     while (pass) {
                         const int u = __ffs(pass) - 1;
                         pass &= pass - 1;
-                        float du = dist[0];
-#pragma unroll
-                        for (int v = 1; v < IB; ++v)
-                            if (v == u) du = dist[v];
+                        const float du = Pick<IB>::get(dist, u);
                         const int c = cb + u;
                         const int64_t cp = c0 + c;
                         const KT key = KO::make(__float_as_uint(du), vis, c, cp);
@@ -1449,12 +1535,14 @@ __global__ void __launch_bounds__(TILE, MP <= 8 ? 10 : 8) knn_tile_kernel(TileAr
 // recentred on the query tile's box centre before rounding.  As in the FP32 search,
 // candidate tiles are sorted by box distance, visited nearest first, and skipped
 // once their box distance passes the largest heap bound of the query tile, which
-// tightens after every visit; each query keeps a max-heap of its k + margin
+// tightens after every visit; each query keeps a 4-ary max-heap of its k + margin
 // smallest keys, started full of sentinels at its radius bound when a radius is
 // given (learned pruning) and at +inf otherwise.  Rows are finished by
 // finalize_row_band; a query tile with a row that is not certified goes to the
 // exact FP32 search.
 constexpr int T2 = 128;
+constexpr int TC_ARITY = 4;   // the per-query heaps are 4-ary
+constexpr int SCAP_TC = 512;  // sorted candidate-tile list: tiles in the first half, super-tiles in the second
 constexpr float kHalfClamp = 30000.f;   // FP16 operands are clamped here (finite products)
 
 // 16-bit operand types of the tiles: BF16 (8-bit significand) or FP16 (11-bit).
@@ -1463,6 +1551,7 @@ template <> struct Half16<false> {
     using T = __nv_bfloat16;
     static __device__ __forceinline__ T from(float x) { return __float2bfloat16_rn(x); }
     static __device__ __forceinline__ float to(T x) { return __bfloat162float(x); }
+    static __device__ __forceinline__ uint16_t bits(T x) { return __bfloat16_as_ushort(x); }
     static constexpr float unit = 0.00390625f;     // 2^-8
     static constexpr float dabs = 0.f;
     static constexpr float clampv = 3.0e38f;
@@ -1471,6 +1560,7 @@ template <> struct Half16<true> {
     using T = __half;
     static __device__ __forceinline__ T from(float x) { return __float2half_rn(x); }
     static __device__ __forceinline__ float to(T x) { return __half2float(x); }
+    static __device__ __forceinline__ uint16_t bits(T x) { return __half_as_ushort(x); }
     static constexpr float unit = 0.00048828125f;  // 2^-11
     static constexpr float dabs = 1.0e-6f;         // >= sqrt(128) 2^-25: subnormal spacing over 128 coordinates
     static constexpr float clampv = kHalfClamp;
@@ -1482,6 +1572,11 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
     using KT = typename std::conditional<K32, uint32_t, uint64_t>::type;
     using BK = BandKey<KT>;
     constexpr int KP = MP < 16 ? 16 : MP;
+    // m <= 4: every coordinate as a sum of two 16-bit numbers, hi + lo, and the four products
+    // hi.hi, hi.lo, lo.hi, lo.lo in the K = 16 that one MMA step runs anyway (operands
+    // A = [q_hi q_hi q_lo q_lo], B = [x_hi x_lo x_hi x_lo]): the dot product of hi + lo
+    // with FP32 accumulation, so the representation error falls from u to u^2
+    constexpr bool SPLIT = MP <= 4;
     using HT = Half16<F16>;
     using half_t = typename HT::T;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -1489,13 +1584,15 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
     half_t* sa = (half_t*)smem;                                // [T2][KP] core-matrix layout
     half_t* sb = sa + T2 * KP;                                 // [2 TILE][KP]: two candidate tiles
     float* sqb = (float*)(sb + 2 * TILE * KP);                 // [2 TILE]
-    uint64_t* slist = (uint64_t*)(sqb + 2 * TILE);             // [SCAP]
-    KT* buf = (KT*)(slist + SCAP);                             // [C][T2] max-heaps
+    uint64_t* slist = (uint64_t*)(sqb + 2 * TILE);             // [SCAP_TC]
+    KT* buf = (KT*)(slist + SCAP_TC);                          // [C][T2] max-heaps
     __shared__ float sqlo[MP], sqhi[MP], scen[MP];
     __shared__ uint32_t sred[4];
     __shared__ int s_tile, s_fail, s_abort;
     __shared__ int s_wc[2][T2 / 32];   // block_append scratch
     int apar = 0;
+    __shared__ int s_need[2][T2 / 32];   // per warp: bit h set if a query needs the visit's tile h
+    int npar = 0;
     __shared__ int64_t s_ct[2];
     __shared__ float s_amax[4];
     __shared__ __align__(8) uint64_t bar;
@@ -1508,7 +1605,8 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
     const int64_t nst = (nt + 1) / 2;
     const bool rmode = a.r2 != nullptr;
     Band bd;
-    bd.u = HT::unit;
+    // split operands: |q' - (hi + lo)| <= u^2 |q'|, plus the FP32 rounding of q - c (2^-24 |q'|)
+    bd.u = SPLIT ? HT::unit * HT::unit + 1.2e-7f : HT::unit;
     bd.dabs = HT::dabs;
     bd.rho_k = 2.f * (float)(KP + 4) * 5.9604645e-8f;
     unsigned long long evaluated = 0;
@@ -1565,18 +1663,40 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
         float sqa = 0.f;
 #pragma unroll
         for (int r = 0; r < MP; ++r) qr[r] = a.xs[p * MP + r];
+        if constexpr (SPLIT) {
+            uint16_t vh[8], vl[8];
 #pragma unroll
-        for (int j = 0; j < KP / 8; ++j) {
-            __align__(16) half_t v[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int r = 8 * j + e;
-                const float x = r < MP && valid ? fminf(fmaxf(qr[r] - scen[r], -HT::clampv), HT::clampv) : 0.f;
-                v[e] = HT::from(x);
-                const float xb = HT::to(v[e]);
-                sqa = fmaf(xb, xb, sqa);
+            for (int r = 0; r < 4; ++r) {
+                const float x = r < MP && valid ? fminf(fmaxf(qr[r < MP ? r : 0] - scen[r < MP ? r : 0], -HT::clampv),
+                                                        HT::clampv)
+                                                : 0.f;
+                const half_t h = HT::from(x);
+                const float hb = HT::to(h);
+                const half_t l = HT::from(x - hb);   // x - hb is exact in FP32
+                const float xv = hb + HT::to(l);    // exact in FP32
+                sqa = fmaf(xv, xv, sqa);
+                vh[r] = HT::bits(h);
+                vh[4 + r] = HT::bits(h);
+                vl[r] = HT::bits(l);
+                vl[4 + r] = HT::bits(l);
             }
-            *(uint4*)((char*)sa + tc::operand_offset(t, 8 * j, KP)) = *(const uint4*)v;
+            *(uint4*)((char*)sa + tc::operand_offset(t, 0, KP)) = tc::pack8(vh);
+            *(uint4*)((char*)sa + tc::operand_offset(t, 8, KP)) = tc::pack8(vl);
+        } else {
+#pragma unroll
+            for (int j = 0; j < KP / 8; ++j) {
+                uint16_t v[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int r = 8 * j + e;
+                    const float x = r < MP && valid ? fminf(fmaxf(qr[r] - scen[r], -HT::clampv), HT::clampv) : 0.f;
+                    const half_t h = HT::from(x);
+                    v[e] = HT::bits(h);
+                    const float xb = HT::to(h);
+                    sqa = fmaf(xb, xb, sqa);
+                }
+                *(uint4*)((char*)sa + tc::operand_offset(t, 8 * j, KP)) = tc::pack8(v);
+            }
         }
         const float qn = sqrtf(sqa);
         const float R2 = rmode && valid ? __fmul_ru(a.r2[p], a.r2_scale) : INFINITY;
@@ -1614,8 +1734,14 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
                 return __float_as_uint(__fmul_rd(acc, a.lb_factor)) <= BK::hi_bits(heapmax);
             };
             bool need0 = needs(cta), need1 = needs(ctb);
-            const bool any0 = __syncthreads_or(need0);
-            const bool any1 = ctb >= 0 && __syncthreads_or(need1);
+            {   // one barrier for both tiles; two halves, as a warp can be one visit ahead
+                const unsigned b0 = __ballot_sync(0xffffffffu, need0), b1 = __ballot_sync(0xffffffffu, need1);
+                if (lane == 0) s_need[npar][warp] = (b0 ? 1 : 0) | (b1 ? 2 : 0);
+            }
+            __syncthreads();
+            const int nw = s_need[npar][0] | s_need[npar][1] | s_need[npar][2] | s_need[npar][3];
+            npar ^= 1;
+            const bool any0 = nw & 1, any1 = nw & 2;
             if (!any0 && !any1) return true;
             // the tiles to stage, in order: slot h holds tile ct_h (needed by some query)
             const int64_t ct0 = any0 ? cta : ctb;
@@ -1646,20 +1772,41 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
                     for (int r = 0; r < MP; ++r) xv[r] = a.xs[cp * MP + r];
                 }
                 float sq = 0.f;
+                if constexpr (SPLIT) {
+                    uint16_t v[8];
 #pragma unroll
-                for (int j = 0; j < KP / 8; ++j) {
-                    __align__(16) half_t v[8];
-#pragma unroll
-                    for (int e2 = 0; e2 < 8; ++e2) {
-                        const int r = 8 * j + e2;
+                    for (int r = 0; r < 4; ++r) {
                         const float x = r < MP ? fminf(fmaxf(xv[r < MP ? r : 0] - scen[r < MP ? r : 0], -HT::clampv),
                                                        HT::clampv)
                                                : 0.f;
-                        v[e2] = HT::from(x);
-                        const float xb = HT::to(v[e2]);
-                        sq = fmaf(xb, xb, sq);
+                        const half_t h = HT::from(x);
+                        const float hb = HT::to(h);
+                        const half_t l = HT::from(x - hb);
+                        const float xw = hb + HT::to(l);
+                        sq = fmaf(xw, xw, sq);
+                        v[r] = HT::bits(h);
+                        v[4 + r] = HT::bits(l);
                     }
-                    *(uint4*)((char*)sb + tc::operand_offset(t, 8 * j, KP)) = *(const uint4*)v;
+                    const uint4 w = tc::pack8(v);
+                    *(uint4*)((char*)sb + tc::operand_offset(t, 0, KP)) = w;
+                    *(uint4*)((char*)sb + tc::operand_offset(t, 8, KP)) = w;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < KP / 8; ++j) {
+                        uint16_t v[8];
+#pragma unroll
+                        for (int e2 = 0; e2 < 8; ++e2) {
+                            const int r = 8 * j + e2;
+                            const float x = r < MP ? fminf(fmaxf(xv[r < MP ? r : 0] - scen[r < MP ? r : 0], -HT::clampv),
+                                                           HT::clampv)
+                                                   : 0.f;
+                            const half_t h = HT::from(x);
+                            v[e2] = HT::bits(h);
+                            const float xb = HT::to(h);
+                            sq = fmaf(xb, xb, sq);
+                        }
+                        *(uint4*)((char*)sb + tc::operand_offset(t, 8 * j, KP)) = tc::pack8(v);
+                    }
                 }
                 sqb[t] = sq;
             }
@@ -1685,19 +1832,17 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
                 }
                 tc::mma_commit(&bar);
             }
-            const bool done = tc::mbar_wait(&bar, phase);
+            // a warp reads tensor memory only if the wait ended in time for all its lanes (the load
+            // is warp-wide); the end-of-visit barrier tells every thread whether one did not
+            const bool done = __all_sync(0xffffffffu, tc::mbar_wait(&bar, phase));
             phase ^= 1u;
             tc::fence_after_sync();
-            if (__syncthreads_or(!done)) {   // a bounded wait ran out: record it and stop
-                if (t == 0) { report_error(a.rep, VB_ERR_TIMEOUT); s_abort = 1; }
-                __syncthreads();   // every thread sees the flag before the loops test it
-                return false;
-            }
+            if (!done) need0 = need1 = false;
             evaluated += (need0 ? TILE : 0) + (need1 ? TILE : 0);
             const uint32_t hb = BK::hi_bits(heapmax);
             float hmf = hb == 0xffffffffu ? INFINITY : __uint_as_float(hb);
 #pragma unroll 1
-            for (int ch = 0; ch < 2 * ntl; ++ch) {
+            for (int ch = 0; ch < (done ? 2 * ntl : 0); ++ch) {
                 const int h = ch >> 1;
                 float v[32];
                 tc::tmem_ld32(tb + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32), v);
@@ -1719,14 +1864,12 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
                 while (msk) {   // the full key test and the heap update
                     const int i = __ffs(msk) - 1;
                     msk &= msk - 1u;
-                    float d = 0.f;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) d = j == i ? v[j] : d;
+                    const float d = Pick<32>::get(v, i);
                     const int lt = (ch & 1) * 32 + i;   // the candidate's lane in its tile
                     const int64_t cp = cth * TILE + lt;
                     const KT key = BK::make(__float_as_uint(fmaxf(d, 0.f)), vis + h, lt, (uint32_t)cp);
                     if (key < heapmax && cp != p && cp >= qlo && cp < qhi) {
-                        sift_down<T2>(buf, t, 0, C, key, levels);
+                        sift_down_d<T2, TC_ARITY>(buf, t, 0, C, key, levels);
                         heapmax = buf[t];
                     }
                 }
@@ -1737,7 +1880,11 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
             // tile threshold = largest heap bound among the tile's valid queries
             const uint32_t wmax = __reduce_max_sync(0xffffffffu, valid ? BK::hi_bits(heapmax) : 0u);
             if (lane == 0) sred[warp] = wmax;
-            __syncthreads();
+            if (__syncthreads_or(!done)) {   // a bounded wait ran out: record it and stop
+                if (t == 0) { report_error(a.rep, VB_ERR_TIMEOUT); s_abort = 1; }
+                __syncthreads();   // every thread sees the flag before the loops test it
+                return false;
+            }
             thr_blk = max(max(sred[0], sred[1]), max(sred[2], sred[3]));
             return true;
         };
@@ -1749,28 +1896,16 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
         const int64_t s_hi = rmode || far ? 0 : min(ct_hi, 2 * qs + 2 + sw);
         for (int64_t ct = s_lo; ct < s_hi && !s_abort && !s_fail; ct += 2)
             if (!visit(ct, ct + 1 < s_hi ? ct + 1 : -1)) break;
-        // every other tile whose box lower bound does not exceed the tile bound, nearest first
-        for (int64_t c0 = ct_lo; c0 < ct_hi && !far && !s_abort && !s_fail;) {
-            int cnt = 0;
-            for (; c0 < ct_hi; c0 += T2) {
-                const int64_t ct = c0 + t;
-                bool keep = ct < ct_hi && (ct < s_lo || ct >= s_hi);
-                float lb = 0.f;
-                if (keep) {
-                    float acc = 0.f;
-                    for (int r = 0; r < MP; ++r) {
-                        const float g = fmaxf(fmaxf(a.tlo[ct * MP + r] - sqhi[r], sqlo[r] - a.thi[ct * MP + r]), 0.f);
-                        acc = fmaf(g, g, acc);
-                    }
-                    lb = __fmul_rd(acc, a.lb_factor);
-                    keep = __float_as_uint(lb) <= thr_blk;
-                }
-                block_append<T2 / 32>(slist, cnt, keep, ((uint64_t)__float_as_uint(lb) << 32) | (uint32_t)ct, s_wc, apar);
-                if (cnt > SCAP - T2) { c0 += T2; break; }
-            }
+        // every other tile whose box lower bound does not exceed the tile bound, nearest first.
+        // Two levels, as in the FP32 search: super-tiles (64 consecutive tiles) by their boxes,
+        // nearest first, skipped whole beyond the threshold (a super-tile's box holds its tiles'
+        // boxes); the tiles of the kept ones, two super-tiles per pass of the block, are bounded,
+        // gathered, sorted and visited.  Few super-tiles (a small cloud): tiles scanned directly.
+        // slist[0, SCAP_TC/2) holds tiles, slist[SCAP_TC/2, SCAP_TC) super-tiles.
+        auto sort_keys = [&](uint64_t* lst, int cnt) {   // ascending bitonic sort of lst[0..cnt)
             int P = 1;
             while (P < cnt) P <<= 1;
-            for (int i = cnt + t; i < P; i += T2) slist[i] = ~0ull;
+            for (int i = cnt + t; i < P; i += T2) lst[i] = ~0ull;
             __syncthreads();
             for (int size = 2; size <= P; size <<= 1) {
                 for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -1778,12 +1913,23 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
                         const int lo = 2 * i - (i & (stride - 1));
                         const int hi = lo + stride;
                         const bool up = (lo & size) == 0;
-                        const uint64_t x = slist[lo], y = slist[hi];
-                        if ((x > y) == up) { slist[lo] = y; slist[hi] = x; }
+                        const uint64_t x = lst[lo], y = lst[hi];
+                        if ((x > y) == up) { lst[lo] = y; lst[hi] = x; }
                     }
                     __syncthreads();
                 }
             }
+        };
+        auto tile_lb = [&](int64_t ct, const float* lo, const float* hi) {
+            float acc = 0.f;
+            for (int r = 0; r < MP; ++r) {
+                const float g = fmaxf(fmaxf(lo[ct * MP + r] - sqhi[r], sqlo[r] - hi[ct * MP + r]), 0.f);
+                acc = fmaf(g, g, acc);
+            }
+            return __fmul_rd(acc, a.lb_factor);
+        };
+        // visits the sorted tiles slist[0..cnt) while their bound passes the threshold
+        auto visit_sorted = [&](int cnt) {
             for (int si = 0; si < cnt;) {
                 const uint64_t e = slist[si];
                 if ((uint32_t)(e >> 32) > thr_blk) break;   // sorted: the rest lie farther
@@ -1794,11 +1940,73 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
                 si += pair ? 2 : 1;
             }
             __syncthreads();
+        };
+        uint64_t* sup = slist + SCAP_TC / 2;
+        const int64_t g_lo = ct_lo / TILE, g_hi = (ct_hi + TILE - 1) / TILE;
+        if (g_hi - g_lo <= FLAT_SUPERS) {
+            for (int64_t c0 = ct_lo; c0 < ct_hi && !far && !s_abort && !s_fail;) {
+                int cnt = 0;
+                for (; c0 < ct_hi; c0 += T2) {
+                    const int64_t ct = c0 + t;
+                    bool keep = ct < ct_hi && (ct < s_lo || ct >= s_hi);
+                    float lb = 0.f;
+                    if (keep) {
+                        lb = tile_lb(ct, a.tlo, a.thi);
+                        keep = __float_as_uint(lb) <= thr_blk;
+                    }
+                    block_append<T2 / 32>(slist, cnt, keep, ((uint64_t)__float_as_uint(lb) << 32) | (uint32_t)ct, s_wc, apar);
+                    if (cnt > SCAP_TC - T2) { c0 += T2; break; }
+                }
+                sort_keys(slist, cnt);
+                visit_sorted(cnt);
+            }
+        } else {
+            for (int64_t g0 = g_lo; g0 < g_hi && !far && !s_abort && !s_fail;) {
+                int ng = 0;
+                for (; g0 < g_hi; g0 += T2) {
+                    const int64_t g = g0 + t;
+                    bool keep = g < g_hi;
+                    float lb = 0.f;
+                    if (keep) {
+                        lb = tile_lb(g, a.slo, a.shi);
+                        keep = __float_as_uint(lb) <= thr_blk;
+                    }
+                    block_append<T2 / 32>(sup, ng, keep, ((uint64_t)__float_as_uint(lb) << 32) | (uint32_t)g, s_wc, apar);
+                    if (ng > SCAP_TC / 2 - T2) { g0 += T2; break; }
+                }
+                sort_keys(sup, ng);
+                for (int gi = 0; gi < ng && !s_abort && !s_fail;) {
+                    int cnt = 0;
+                    for (; gi < ng; gi += T2 / TILE) {
+                        if ((uint32_t)(sup[gi] >> 32) > thr_blk) {   // sorted: the rest lie farther
+                            gi = ng;
+                            break;
+                        }
+                        const int sg = gi + t / TILE;   // this thread's super-tile and tile in it
+                        int64_t ct = -1;
+                        bool keep = false;
+                        float lb = 0.f;
+                        if (sg < ng && (uint32_t)(sup[sg] >> 32) <= thr_blk) {
+                            ct = (int64_t)(uint32_t)sup[sg] * TILE + (t & (TILE - 1));
+                            keep = ct >= ct_lo && ct < ct_hi && (ct < s_lo || ct >= s_hi);
+                            if (keep) {
+                                lb = tile_lb(ct, a.tlo, a.thi);
+                                keep = __float_as_uint(lb) <= thr_blk;
+                            }
+                        }
+                        block_append<T2 / 32>(slist, cnt, keep, ((uint64_t)__float_as_uint(lb) << 32) | (uint32_t)ct, s_wc,
+                                              apar);
+                        if (cnt > SCAP_TC / 2 - T2) { gi += T2 / TILE; break; }
+                    }
+                    sort_keys(slist, cnt);
+                    visit_sorted(cnt);
+                }
+            }
         }
         if (s_abort) break;
 
         bool ok = !far && !s_fail;   // s_fail here: the visit table overflowed (compact keys)
-        if (valid && ok) ok = finalize_row_band<MP, T2, KT>(a, buf, t, C, p, qhi - qlo, levels, bd, qn, vtab);
+        if (valid && ok) ok = finalize_row_band<MP, T2, KT, TC_ARITY>(a, buf, t, C, p, qhi - qlo, levels, bd, qn, vtab);
         if (valid && !ok) s_fail = 1;
         __syncthreads();
         if (t == 0 && s_fail) {
@@ -1899,16 +2107,17 @@ __global__ void tcp_block_kernel(const float* __restrict__ xs, int64_t n, int64_
     const int row = (int)(p % TILE);
     float sq = 0.f;
     for (int j = 0; j < kp / 8; ++j) {
-        __align__(16) half_t v[8];
+        uint16_t v[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const int r = 8 * j + e;
             const float x = r < m && p < n ? fminf(fmaxf(xs[p * mp + r] - cen[r], -HT::clampv), HT::clampv) : 0.f;
-            v[e] = HT::from(x);
-            const float xb = HT::to(v[e]);
+            const half_t h = HT::from(x);
+            v[e] = HT::bits(h);
+            const float xb = HT::to(h);
             sq = fmaf(xb, xb, sq);
         }
-        *(uint4*)(tb + tc::operand_offset(row, 8 * j, kp)) = *(const uint4*)v;
+        *(uint4*)(tb + tc::operand_offset(row, 8 * j, kp)) = tc::pack8(v);
     }
     ((float*)(tb + tcp_img_bytes(kp)))[row] = sq;
 }
@@ -2497,33 +2706,35 @@ static size_t tile_smem(int L)
 }
 
 // The staged search keeps compact 32-bit heap keys at m <= 16 (visits of a query tile stay
-// far below the visit table there), full 64-bit keys for wider inputs.
+// far below the visit table there), full 64-bit keys for wider inputs, and at m <= 4 also
+// when the caller asks for full keys (their diagnostic output is the FP32 tile distance
+// itself rather than the lower edge of its bucket).
 template <int MP> constexpr bool tc_compact() { return MP <= 16; }
-template <int MP>
+template <int MP, bool K32 = tc_compact<MP>()>
 static size_t tc_smem(int C)
 {
     constexpr int KP = MP < 16 ? 16 : MP;
-    return (size_t)T2 * KP * 2 + 2 * TILE * KP * 2 + 2 * TILE * 4 + SCAP * 8 + (size_t)C * T2 * (tc_compact<MP>() ? 4 : 8);
+    return (size_t)T2 * KP * 2 + 2 * TILE * KP * 2 + 2 * TILE * 4 + SCAP_TC * 8 + (size_t)C * T2 * (K32 ? 4 : 8);
 }
 
-template <int MP, bool F16>
+template <int MP, bool F16, bool K32 = tc_compact<MP>()>
 static vb_status launch_tc(TileArgs a, cudaStream_t s)
 {
-    const size_t sm = tc_smem<MP>(a.cap);
+    const size_t sm = tc_smem<MP, K32>(a.cap);
     if (sm > 220 * 1024) return VB_ERR_UNSUPPORTED;   // k + margin too large for 128 heaps with these operands
     static bool attr_set[16] = {};
     static int sms[16] = {}, smem_sm[16] = {}, static_smem[16] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (!attr_set[dev & 15]) {
-        if (cudaFuncSetAttribute(knn_tc_kernel<MP, F16, tc_compact<MP>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(knn_tc_kernel<MP, F16, K32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(220 * 1024)) != cudaSuccess ||
-            cudaFuncSetAttribute(knn_tc_kernel<MP, F16, tc_compact<MP>()>,
+            cudaFuncSetAttribute(knn_tc_kernel<MP, F16, K32>,
                                  cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
             return VB_ERR_CUDA;
         cudaFuncAttributes fa;
-        if (cudaFuncGetAttributes(&fa, knn_tc_kernel<MP, F16, tc_compact<MP>()>) != cudaSuccess) return VB_ERR_CUDA;
+        if (cudaFuncGetAttributes(&fa, knn_tc_kernel<MP, F16, K32>) != cudaSuccess) return VB_ERR_CUDA;
         static_smem[dev & 15] = (int)fa.sharedSizeBytes;
         if (cudaDeviceGetAttribute(&sms[dev & 15], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&smem_sm[dev & 15], cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
@@ -2537,7 +2748,7 @@ static vb_status launch_tc(TileArgs a, cudaStream_t s)
     const int per_sm = std::max(1, std::min(4, smem_sm[dev & 15] / per_cta));
     const int64_t nst = (a.ntiles + 1) / 2;
     const int64_t grid = std::min<int64_t>(nst, (int64_t)per_sm * sms[dev & 15]);
-    knn_tc_kernel<MP, F16, tc_compact<MP>()><<<(unsigned)grid, T2, sm, s>>>(a);
+    knn_tc_kernel<MP, F16, K32><<<(unsigned)grid, T2, sm, s>>>(a);
     return last_launch();
 }
 
@@ -2749,6 +2960,9 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
     a.dbg_idx = p->dbg_idx;
     const bool radius_first = p->prune == VB_PRUNE_LEARNED;
     const bool tensor = p->precision == VB_PREC_BF16 || p->precision == VB_PREC_FP16;
+    // the tiles a radius-first or 16-bit first pass hands back are searched with compact keys
+    // before the full-key search takes what is left
+    const bool compact_retry = (radius_first || tensor) && p->heap_keys != VB_KEYS_FULL && mp <= 16;
     int launches = 0;
     if (radius_first || tensor) {
         if (radius_first) {
@@ -2813,7 +3027,12 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
             if (st == VB_ERR_UNSUPPORTED) {
                 launches += 1;   // staged search (its rows are finished inside)
                 switch (mp) {
-                    case 4: st = f16 ? launch_tc<4, true>(a, s) : launch_tc<4, false>(a, s); break;
+                    case 4:
+                        if (p->heap_keys == VB_KEYS_FULL)
+                            st = f16 ? launch_tc<4, true, false>(a, s) : launch_tc<4, false, false>(a, s);
+                        else
+                            st = f16 ? launch_tc<4, true>(a, s) : launch_tc<4, false>(a, s);
+                        break;
                     case 8: st = f16 ? launch_tc<8, true>(a, s) : launch_tc<8, false>(a, s); break;
                     case 16: st = f16 ? launch_tc<16, true>(a, s) : launch_tc<16, false>(a, s); break;
                     case 32: st = f16 ? launch_tc<32, true>(a, s) : launch_tc<32, false>(a, s); break;
@@ -2862,13 +3081,30 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
         a.tile_list = w.fail_list;
         a.tile_count = w.fb_count + 3;
     }
-    // the exact FP32 search: the only pass, or the second over the tiles the first handed back
+    // the exact FP32 search: the only pass, or the passes over the tiles the first handed back
     const bool retry = a.tile_list != nullptr;
     if (retry) {
         mark(ctx, VB_STAGE_KNN_TILE, 1);
         mark(ctx, VB_STAGE_KNN_RETRY, 0);
     } else {
         mark(ctx, VB_STAGE_KNN_TILE, 0);
+    }
+    if (compact_retry) {
+        // compact keys first (twice the CTAs per SM); the tiles that overflow the visit table or
+        // fail the certificate go on, through the second half of the lists, to full keys
+        a.fail_flag = w.fail_flag + ntiles;
+        a.fail_list = w.fail_list + ntiles;
+        a.fail_count = w.fb_count + 5;
+        launches += 1;
+        switch (mp) {
+            case 4: st = launch_tile<4, true>(a, s); break;
+            case 8: st = launch_tile<8, true>(a, s); break;
+            default: st = launch_tile<16, true>(a, s); break;
+        }
+        if (st != VB_OK) return st;
+        a.work = w.fb_count + 4;
+        a.tile_list = w.fail_list + ntiles;
+        a.tile_count = w.fb_count + 5;
     }
     switch (mp) {
         case 4: st = launch_tile<4>(a, s); break;

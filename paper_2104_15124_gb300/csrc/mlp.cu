@@ -419,14 +419,14 @@ __global__ void __launch_bounds__(MI) mlp_radius_tc_kernel(MlpK k, const float* 
         // layer-1 operand: the standardised inputs of this thread's sample, K padded to 16
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            __align__(16) __nv_bfloat16 v[8];
+            uint16_t v[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const int r = 8 * c + e;
                 const float xv = valid && r < k.in ? (xs[i * ld + r] - k.mean[r]) / k.scale[r] : 0.f;
-                v[e] = __float2bfloat16_rn(xv);
+                v[e] = __bfloat16_as_ushort(__float2bfloat16_rn(xv));
             }
-            *(uint4*)((char*)a1 + tc::operand_offset(t, 8 * c, 16)) = *(const uint4*)v;
+            *(uint4*)((char*)a1 + tc::operand_offset(t, 8 * c, 16)) = tc::pack8(v);
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -449,10 +449,11 @@ __global__ void __launch_bounds__(MI) mlp_radius_tc_kernel(MlpK k, const float* 
             tc::tmem_ld64(lane_addr, z);
 #pragma unroll
             for (int c = 0; c < H / 8; ++c) {
-                __align__(16) __nv_bfloat16 v[8];
+                uint16_t v[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16_rn(gelu(z[8 * c + e] + bias1[8 * c + e]));
-                *(uint4*)((char*)a2 + tc::operand_offset(t, 8 * c, H)) = *(const uint4*)v;
+                for (int e = 0; e < 8; ++e)
+                    v[e] = __bfloat16_as_ushort(__float2bfloat16_rn(gelu(z[8 * c + e] + bias1[8 * c + e])));
+                *(uint4*)((char*)a2 + tc::operand_offset(t, 8 * c, H)) = tc::pack8(v);
             }
         }
         tc::fence_async_smem();

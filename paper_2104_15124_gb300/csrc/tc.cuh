@@ -18,6 +18,14 @@ __device__ __forceinline__ uint32_t operand_offset(int row, int k, int K)
     return (uint32_t)((row >> 3) * (K >> 3) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
+// Eight 16-bit values, given as their bit patterns, as the 16 bytes of one K chunk of an
+// operand row, built in integer registers (a 16-bit array is never reread as wider words).
+__device__ __forceinline__ uint4 pack8(const uint16_t (&b)[8])
+{
+    return make_uint4((uint32_t)b[0] | ((uint32_t)b[1] << 16), (uint32_t)b[2] | ((uint32_t)b[3] << 16),
+                      (uint32_t)b[4] | ((uint32_t)b[5] << 16), (uint32_t)b[6] | ((uint32_t)b[7] << 16));
+}
+
 // Shared-memory matrix descriptor: start address, leading byte offset (between K
 // chunks), stride byte offset (between 8-row groups), descriptor version 1,
 // no swizzle.

@@ -34,6 +34,18 @@ def test_binding_covers_the_header():
     assert set(_declared()) == set(vb.EXPORTED)
 
 
+def test_report_struct_matches_the_header():
+    # the ctypes mirror of vb_report: same fields, same order, same widths
+    import paper_2104_15124_gb300 as vb
+    src = open(os.path.join(ROOT, "include", "vb.h")).read()
+    body = re.search(r"typedef struct \{(.*?)\} vb_report;", src, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"(int32_t|int64_t)\s+(\w+);", body)
+    want = [(name, ctypes.c_int32 if ty == "int32_t" else ctypes.c_int64) for ty, name in fields]
+    assert [(n, t) for n, t in vb.Report._fields_] == want
+    assert ctypes.sizeof(vb.Report) <= 256   # the context's device report block
+
+
 def test_status_strings(lib):
     f = lib.vb_status_string
     f.restype = ctypes.c_char_p

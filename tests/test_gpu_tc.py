@@ -79,3 +79,38 @@ def test_tensor_core_knn_ragged_and_small():
                 vb.raise_on_device_error()
                 assert np.array_equal(nbr.cpu().numpy(), ref_nbr), (n, m, k, prec, variant)
                 assert np.array_equal(d2.cpu().numpy(), ref_d2), (n, m, k, prec, variant)
+
+
+@pytest.mark.parametrize("prec,u,dabs", [("bf16", 2.0 ** -8, 0.0), ("fp16", 2.0 ** -11, 1e-6)])
+@pytest.mark.parametrize("name,m", [("vmf", 3), ("torus", 4)])
+def test_split_operand_tile_distances(name, m, prec, u, dabs):
+    """At m <= 4 the staged kernel writes every operand coordinate as hi + lo, two 16-bit
+    numbers, and the four products fill the K = 16 of one MMA step: the tile distances it
+    keeps (diagnostic output, full heap keys) lie within the error bound E_D(d) of the FP64
+    distances with the unit roundoff u^2 (+ 2^-23 for the FP32 centring), taking |q - c| at
+    most the diagonal of the cloud's box.  Unsplit 16-bit operands (unit roundoff u) give
+    errors of several per cent of the k-th distance on these clouds; split ones stay far
+    below 1e-3 of it."""
+    import paper_2104_15124_gb300 as vb
+    from paper_2104_15124_gb300 import workloads as W
+    n, k = 9000, 64
+    x = W.sphere_vmf(n, 2.0, 31) if name == "vmf" else W.torus4(n, 0.01, 32)
+    xt = torch.from_numpy(x).cuda()
+    nbr, nd2, idx, d16 = vb.knn(xt, k, tensor_cores=prec, tc_variant="staged", debug=True, heap_keys="full")
+    torch.cuda.synchronize()
+    vb.raise_on_device_error()
+    ref_nbr, ref_d2 = _knn_ref(x, k)
+    assert np.array_equal(nbr.cpu().numpy(), ref_nbr)
+    idx, d16 = idx.cpu().numpy(), d16.cpu().numpy().astype(np.float64)
+    rows, cols = np.nonzero(idx >= 0)
+    x64 = x.astype(np.float64)
+    d = ((x64[rows] - x64[idx[rows, cols]]) ** 2).sum(1)
+    dt = d16[rows, cols]
+    D = ref_d2[rows, k - 1]
+    diag = float(np.linalg.norm(x64.max(0) - x64.min(0)))
+    us = u * u + 2.0 ** -23
+    Z = 1.01 * (2.0 * diag + np.sqrt(D))
+    delta = 1.01 * us * Z + dabs
+    E = 1.01 * (2.0 * np.sqrt(d) * delta + delta ** 2 + 2 * (16 + 4) * 2.0 ** -24 * Z ** 2)
+    assert np.all(np.abs(dt - d) <= E)
+    assert np.max(np.abs(dt - d) / D) < 1e-3
