@@ -222,6 +222,21 @@ __device__ __forceinline__ int lower_bound_key(const uint64_t* a, int len, int32
 
 constexpr int SORT_WARPS = 4;
 
+// The k-th pair (distance, index) of every list, 16 bytes per point: the table the mutual
+// test below reads at random stays in L2, where the lists themselves (12 k bytes per point)
+// do not.
+__global__ void kth_kernel(const int32_t* __restrict__ nbr, const double* __restrict__ nbr_d2, int64_t n, int k,
+                           Kth* kth)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Kth q;
+    q.d2 = nbr_d2[i * k + k - 1];
+    q.idx = nbr[i * k + k - 1];
+    q.pad = 0;
+    kth[i] = q;
+}
+
 // Own kNN lists sorted by column, one warp per row; the FP32 value of each entry is the
 // rounding of its canonical FP64 distance (identical for (i, j) and (j, i)).  The columns of a
 // list are distinct, so an entry's place in the sorted list is the number of columns below its
@@ -230,12 +245,13 @@ constexpr int SORT_WARPS = 4;
 // bitonic network over 64-bit keys in shared memory was bound by its shared-memory traffic.
 // The same pass counts, for every point j, the lists that name j without j naming their owner
 // (the reverse entries of row j): (i -> j) is mutual exactly when (d2(i, j), i) does not exceed
-// the k-th pair of j's own list, read from nbr / nbr_d2 directly.
+// the k-th pair of j's own list (kth[j]).  A non-mutual entry carries the sign bit in own_d2
+// (distances are >= 0), so the scatter pass reads the sorted lists alone.
 template <int KL>
 __global__ void __launch_bounds__(SORT_WARPS * 32) own_sort_kernel(const int32_t* __restrict__ nbr,
                                                                     const double* __restrict__ nbr_d2, int64_t n,
-                                                                    int k, int32_t* own_col, float* own_d2, Kth* kth,
-                                                                    int32_t* rcnt)
+                                                                    int k, int32_t* own_col, float* own_d2,
+                                                                    const Kth* __restrict__ kth, int32_t* rcnt)
 {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int64_t i = (int64_t)blockIdx.x * SORT_WARPS + w; i < n; i += (int64_t)gridDim.x * SORT_WARPS) {
@@ -263,45 +279,32 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) own_sort_kernel(const int32_t
             const int e = lane + 32 * s;
             if (e < k) {
                 const double d = nbr_d2[i * k + e];
-                own_col[i * k + rank[s]] = c[s];
-                own_d2[i * k + rank[s]] = (float)d;
                 const int32_t j = c[s];
-                const double qd = nbr_d2[(int64_t)j * k + k - 1];
-                const int32_t qi = nbr[(int64_t)j * k + k - 1];
-                if (!(d < qd || (d == qd && (int32_t)i <= qi))) atomicAdd(&rcnt[j], 1);
+                const Kth q = kth[j];
+                const bool rev = !(d < q.d2 || (d == q.d2 && (int32_t)i <= q.idx));
+                own_col[i * k + rank[s]] = j;
+                own_d2[i * k + rank[s]] = rev ? -(float)d : (float)d;
+                if (rev) atomicAdd(&rcnt[j], 1);
             }
-        }
-        if (lane == 0) {
-            Kth q;
-            q.d2 = nbr_d2[i * k + k - 1];
-            q.idx = row[k - 1];
-            q.pad = 0;
-            kth[i] = q;
         }
     }
 }
 
-// Reverse candidates (i -> j, j = nbr[i][r]) that are not mutual: counted (pass 0) or
-// scattered into row j's reverse slots (pass 1).
-__global__ void reverse_kernel(const int32_t* __restrict__ nbr, const double* __restrict__ nbr_d2, int64_t n, int k,
-                               const Kth* __restrict__ kth, int pass, int32_t* rcnt,
+// The non-mutual entries (i -> j) of the sorted lists (sign bit set in own_d2), scattered
+// into row j's reverse slots.
+__global__ void reverse_kernel(const int32_t* __restrict__ own_col, const float* __restrict__ own_d2, int64_t n, int k,
                                const int64_t* __restrict__ row_ptr, int32_t* fill, int32_t* rev_col, float* rev_d2)
 {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n * k) return;
+    const float d = own_d2[e];
+    if (!signbit(d)) return;   // mutual: already in row j's own list
     const int64_t i = e / k;
-    const int32_t j = nbr[e];
-    const double d = nbr_d2[e];
-    const Kth q = kth[j];
-    if (d < q.d2 || (d == q.d2 && (int32_t)i <= q.idx)) return;   // mutual: already in row j's own list
-    if (pass == 0) {
-        atomicAdd(&rcnt[j], 1);
-        return;
-    }
+    const int32_t j = own_col[e];
     const int slot = atomicAdd(&fill[j], 1);
     const int64_t off = row_ptr[j] - (int64_t)j * (1 + k) + slot;
     rev_col[off] = (int32_t)i;
-    rev_d2[off] = (float)d;
+    rev_d2[off] = -d;
 }
 
 __global__ void row_len_kernel(const int32_t* __restrict__ rcnt, int64_t n, int k, int32_t* cnt, int32_t* fill)
@@ -339,7 +342,7 @@ __device__ void merge_row(int64_t j, int k, int r, uint64_t* rb, const int64_t* 
         const int32_t c = oc[a];   // (own_col + j k)[a]
         const int rank = a + lower_bound_key(rb, r, c) + ((int32_t)j < c ? 1 : 0);
         col[ob + rank] = c;
-        ed2[ob + rank] = od[a];
+        ed2[ob + rank] = fabsf(od[a]);   // without the non-mutual mark
     }
     for (int b = tid; b < r; b += nthr) {
         const int32_t c = (int32_t)(rb[b] >> 32);
@@ -424,6 +427,7 @@ vb_status graph_run(Ctx* ctx, int64_t n, int32_t k, const int32_t* nbr, const do
     mark(ctx, VB_STAGE_GRAPH, 0);
     zero_i32_kernel<<<gz, 256, 0, s>>>(w.rcnt, n);
     zero_i32_kernel<<<1, 32, 0, s>>>(w.nbig, 1);
+    kth_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nbr, nbr_d2, n, k, w.kth);
     if (k <= 32)
         own_sort_kernel<1><<<152 * 16, SORT_WARPS * 32, 0, s>>>(nbr, nbr_d2, n, k, w.own_col, w.own_d2, w.kth,
                                                                    w.rcnt);
@@ -439,7 +443,7 @@ vb_status graph_run(Ctx* ctx, int64_t n, int32_t k, const int32_t* nbr, const do
     row_len_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.rcnt, n, k, w.cnt, w.fill);
     vb_status st = scan_counts(s, w.cnt, n, row_ptr, w.scan);
     if (st != VB_OK) return st;
-    reverse_kernel<<<ge, 256, 0, s>>>(nbr, nbr_d2, n, k, w.kth, 1, w.rcnt, row_ptr, w.fill, w.rev_col, w.rev_d2);
+    reverse_kernel<<<ge, 256, 0, s>>>(w.own_col, w.own_d2, n, k, row_ptr, w.fill, w.rev_col, w.rev_d2);
     merge_kernel<<<152 * 16, SORT_WARPS * 32, 0, s>>>(row_ptr, n, k, w.own_col, w.own_d2, w.rev_col, w.rev_d2, col, ed2,
                                                       cap, w.big, w.nbig, nnz_dev, ctx->rep);
     static bool big_attr[16] = {};
@@ -453,7 +457,7 @@ vb_status graph_run(Ctx* ctx, int64_t n, int32_t k, const int32_t* nbr, const do
     big_merge_kernel<<<152, 1024, BIG_CAP * 8, s>>>(row_ptr, n, k, w.own_col, w.own_d2, w.rev_col, w.rev_d2, col, ed2,
                                                     cap, w.big, w.nbig, ctx->rep);
     mark(ctx, VB_STAGE_GRAPH, 1);
-    ctx->launches += 11;
+    ctx->launches += 12;
     return last_launch();
 }
 
