@@ -100,7 +100,7 @@ __host__ __device__ inline int64_t rows_per_block(int64_t n, int nblk) { return 
 inline size_t seg_slots(int B) { return (size_t)kRowBlocks + (size_t)B; }
 // The sweeps run one resident wave (three 256-thread blocks per SM, their launch bound): each
 // warp then owns a longer range of entries, which amortises its 57 end-of-range reductions.
-constexpr int kSweepBlocks = 152 * 3;
+constexpr int kSweepBlocks = 152 * 2;
 
 // Column totals over cloud b's slots (slots of G values) by a block of SEG_T threads:
 // thread t sums column t % 64 over the slots bl = t / 64, t / 64 + SEG_PARTS, ... (reads of
@@ -212,7 +212,50 @@ __global__ void __launch_bounds__(kRowThreads) sweep_kernel(const int64_t* __res
 // its lanes stride that range's entries, so every lane stays busy whatever the
 // row lengths; the row of an entry is tracked by a cursor per lane.
 constexpr int G57 = 57;
-__global__ void __launch_bounds__(kRowThreads, 3) sweep57_kernel(const int64_t* __restrict__ row_ptr,
+
+// Warp reduce-scatter of 64 per-lane partial sums (slots >= 57 are zero): five halving
+// steps, each lane trading half its slots with the partner lane o apart and keeping the half
+// that its bit o selects, leave lane l with the warp's totals of slots 2l and 2l + 1 (the kept
+// halves' offsets add up to 2l).  62 shuffles instead of 57 full butterflies, and the FP64
+// accumulation that follows is two full-warp additions per flush instead of 57 one-lane ones
+// (the FP64 pipe is narrow on this part).
+__device__ __forceinline__ void warp_reduce_scatter64(const float (&a)[G57], float& s0, float& s1)
+{
+    const int lane = threadIdx.x & 31;
+    float b[32], c[16], d[8], e[4], f[2];
+    {
+        const bool up = lane & 16;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const float lo = a[i], hi = i + 32 < G57 ? a[i + 32] : 0.f;
+            b[i] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, 16);
+        }
+    }
+    {
+        const bool up = lane & 8;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) c[i] = (up ? b[i + 16] : b[i]) + __shfl_xor_sync(0xffffffffu, up ? b[i] : b[i + 16], 8);
+    }
+    {
+        const bool up = lane & 4;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) d[i] = (up ? c[i + 8] : c[i]) + __shfl_xor_sync(0xffffffffu, up ? c[i] : c[i + 8], 4);
+    }
+    {
+        const bool up = lane & 2;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) e[i] = (up ? d[i + 4] : d[i]) + __shfl_xor_sync(0xffffffffu, up ? d[i] : d[i + 4], 2);
+    }
+    {
+        const bool up = lane & 1;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) f[i] = (up ? e[i + 2] : e[i]) + __shfl_xor_sync(0xffffffffu, up ? e[i] : e[i + 2], 1);
+    }
+    s0 = f[0];
+    s1 = f[1];
+}
+
+__global__ void __launch_bounds__(kRowThreads, 2) sweep57_kernel(const int64_t* __restrict__ row_ptr,
                                                             const int32_t* __restrict__ col,
                                                             const float* __restrict__ ed2, int64_t n,
                                                             const float* __restrict__ irho,
@@ -241,35 +284,52 @@ __global__ void __launch_bounds__(kRowThreads, 3) sweep57_kernel(const int64_t* 
         const int64_t e0 = row_ptr[a0], e1 = row_ptr[a1];
 #pragma unroll
         for (int g = 0; g < G57; ++g) acc[g] = 0.f;
+        double dacc0 = 0.0, dacc1 = 0.0;   // this lane's share of the warp's totals: slots 2 lane, 2 lane + 1
+        auto flush = [&]() {
+            float s0, s1;
+            warp_reduce_scatter64(acc, s0, s1);
+            dacc0 += (double)s0;
+            dacc1 += (double)s1;
+#pragma unroll
+            for (int g = 0; g < G57; ++g) acc[g] = 0.f;
+        };
         int64_t i = a0;
         int64_t inext = row_ptr[min(a0 + 1, n)];
         float ri = a0 < n ? irho[a0] : 0.f;
+        int64_t inext2 = row_ptr[min(a0 + 2, n)];   // the next row's end and bandwidth, loaded a row ahead
+        float ri_next = irho[min(a0 + 1, n - 1)];
         int since = 0;
-        // two-deep software pipeline: the column and squared distance of the entry two chunks
-        // ahead and the bandwidth gather of the next chunk's entry are in flight while this
-        // chunk's 57 kernel values are formed (column -1: past the warp's range)
-        int32_t j0 = -1, j1 = -1;
-        float x0 = 0.f, x1 = 0.f;
+        // software pipeline: the column and squared distance of the entry three chunks ahead and
+        // the bandwidth gather of the entry two chunks ahead are in flight while this chunk's 57
+        // kernel values are formed (column -1: past the warp's range); the row cursor keeps the
+        // next row's end and bandwidth loaded a row ahead
+        int32_t j0 = -1, j1 = -1, j2 = -1;
+        float x0 = 0.f, x1 = 0.f, x2 = 0.f;
         if (e0 + lane < e1) { j0 = col[e0 + lane]; x0 = ed2[e0 + lane]; }
         if (e0 + 32 + lane < e1) { j1 = col[e0 + 32 + lane]; x1 = ed2[e0 + 32 + lane]; }
+        if (e0 + 64 + lane < e1) { j2 = col[e0 + 64 + lane]; x2 = ed2[e0 + 64 + lane]; }
         float rj0 = j0 >= 0 ? irho[j0] : 0.f;
+        float rj1 = j1 >= 0 ? irho[j1] : 0.f;
         for (int64_t eb = e0; eb < e1; eb += 32) {
             const int64_t e = eb + lane;
-            int32_t j2 = -1;
-            float x2 = 0.f;
-            if (e + 64 < e1) { j2 = col[e + 64]; x2 = ed2[e + 64]; }
-            const float rj1 = j1 >= 0 ? irho[j1] : 0.f;
+            int32_t j3 = -1;
+            float x3 = 0.f;
+            if (e + 96 < e1) { j3 = col[e + 96]; x3 = ed2[e + 96]; }
+            const float rj2 = j2 >= 0 ? irho[j2] : 0.f;
             float u = INFINITY;
             if (e < e1) {
                 while (inext <= e) {
                     ++i;
-                    inext = row_ptr[i + 1];
-                    ri = irho[i];
+                    inext = inext2;
+                    ri = ri_next;
+                    inext2 = row_ptr[min(i + 2, n)];
+                    ri_next = irho[min(i + 1, n - 1)];
                 }
                 if (j0 != i) u = x0 * (ri * rj0) * c0;
             }
             j0 = j1; x0 = x1; rj0 = rj1;
-            j1 = j2; x1 = x2;
+            j1 = j2; x1 = x2; rj1 = rj2;
+            j2 = j3; x2 = x3;
             float prev[4];
 #pragma unroll
             for (int g = G57 - 1; g >= 0; --g) {
@@ -280,19 +340,12 @@ __global__ void __launch_bounds__(kRowThreads, 3) sweep57_kernel(const int64_t* 
             }
             if (++since == 32) {
                 since = 0;
-#pragma unroll
-                for (int g = 0; g < G57; ++g) {
-                    float v = warp_sum_f32(acc[g]);
-                    if (lane == 0) wacc[w][g] += (double)v;
-                    acc[g] = 0.f;
-                }
+                flush();
             }
         }
-#pragma unroll
-        for (int g = 0; g < G57; ++g) {
-            float v = warp_sum_f32(acc[g]);
-            if (lane == 0) wacc[w][g] += (double)v;
-        }
+        flush();
+        if (2 * lane < G57) wacc[w][2 * lane] = dacc0;
+        if (2 * lane + 1 < G57) wacc[w][2 * lane + 1] = dacc1;
         __syncthreads();
         for (int g = threadIdx.x; g < G57; g += blockDim.x) {
             double sum = 0.0;
