@@ -563,6 +563,7 @@ def main():
                           "points_per_s": job_throughput(spec.n, a.steps, ws, res[f]["total_s"]),
                           "knn_ms": round(sum(res[f]["stage_ms"].get(k, 0.0) for k in KNN_SEARCH_STAGES), 4),
                           "knn_candidate_pairs": res[f]["rep"]["knn_candidates"] // steps_prof,
+                          "knn_redo_tiles": res[f]["rep"]["knn_redo_tiles"] // steps_prof,
                           "knn_retry_tiles": res[f]["rep"]["knn_retry_tiles"] // steps_prof,
                           "knn_fallback_rows": res[f]["rep"]["knn_fallback_rows"] // steps_prof,
                           "autotuned": {kk: v for kk, v in shapes[f].items() if kk != "knn_ms"}} for f in forms},

@@ -82,6 +82,7 @@ typedef struct {
     int64_t knn_rows_long_run;  /* rows whose FP32/16-bit ties or error band exceeded the exact-order buffer */
     int64_t knn_rows_uncertified; /* rows whose k-th FP64 distance did not clear the certificate bound */
     int64_t knn_retry_candidates; /* the part of knn_candidates evaluated by the exact FP32 pass over handed-back tiles */
+    int64_t knn_redo_tiles;     /* query tiles the 16-bit radius-first search searched again at twice the radius */
 } vb_report;
 
 /* Waits for the context's stream and copies the device report to *out. */
@@ -146,6 +147,8 @@ vb_status vb_profile_read(vb_ctx* ctx, float* ms, int64_t* launches);
  * accumulator buffers, and four warps select, all overlapped. */
 #define VB_KEYS_COMPACT 0
 #define VB_KEYS_FULL    1
+#define VB_CURVE_AUTO    0
+#define VB_CURVE_MORTON  1
 #define VB_TC_AUTO      0
 #define VB_TC_STAGED    1
 #define VB_TC_PIPELINED 2
@@ -184,6 +187,9 @@ typedef struct {
                                 the lower edge of the key's bucket, 2^-10 relative below the distance) */
     int32_t* dbg_idx;        /* with dbg_d2: n x (k + margin) device int32, the original index of each of those
                                 candidates (-1 for an unused slot) */
+    int32_t curve;           /* spatial order of the search's tiles at 2 <= m <= 4: VB_CURVE_AUTO (default, the
+                                Hilbert curve) or VB_CURVE_MORTON; m = 1 and m > 4 (principal-axis keys) always
+                                take the Morton interleave.  The lists are exact either way */
 } vb_knn_params;
 
 /* Launch-shape autotuner (a16).  Times vb_knn on the caller's input for every

@@ -47,7 +47,8 @@ c_i32, c_i64, c_f32, c_f64, c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_floa
 class KnnParams(ctypes.Structure):
     _fields_ = [("k", c_i32), ("margin", c_i32), ("precision", c_i32), ("prune", c_i32), ("radius", c_p),
                 ("mlp", c_p), ("radius_inflate", c_f32), ("radius_log_shift", c_f32), ("cloud_log_shift", c_p),
-                ("seed_tiles", c_i32), ("tc_variant", c_i32), ("heap_keys", c_i32), ("dbg_d2", c_p), ("dbg_idx", c_p)]
+                ("seed_tiles", c_i32), ("tc_variant", c_i32), ("heap_keys", c_i32), ("dbg_d2", c_p), ("dbg_idx", c_p),
+                ("curve", c_i32)]
 
 
 class GraphC(ctypes.Structure):
@@ -88,7 +89,8 @@ class Report(ctypes.Structure):
     _fields_ = [("error", c_i32), ("warnings", c_i32), ("knn_fallback_rows", c_i64), ("knn_candidates", c_i64),
                 ("union_big_rows", c_i64), ("knn_heap_levels", c_i64), ("knn_tiles_staged", c_i64),
                 ("knn_insert_rounds", c_i64), ("knn_retry_tiles", c_i64), ("knn_rows_short", c_i64),
-                ("knn_rows_long_run", c_i64), ("knn_rows_uncertified", c_i64), ("knn_retry_candidates", c_i64)]
+                ("knn_rows_long_run", c_i64), ("knn_rows_uncertified", c_i64), ("knn_retry_candidates", c_i64),
+                ("knn_redo_tiles", c_i64)]
 
 
 _SIGS = {
@@ -266,12 +268,14 @@ class Graph:
 # ----------------------------------------------------------------------------- the calls
 def knn(x: torch.Tensor, k: int, margin: int = 16, prune: bool = True, radius: torch.Tensor | None = None,
         inflate: float = 0.0, mlp=None, log_shift: float = 0.0, tensor_cores: str | None = None,
-        tc_variant: str = "auto", seed_tiles: int = 0, heap_keys: str = "compact", debug: bool = False):
+        tc_variant: str = "auto", seed_tiles: int = 0, heap_keys: str = "compact", debug: bool = False,
+        curve: str = "auto"):
     """Exact kNN (vb_knn): returns (nbr int32 [n, k], nbr_d2 fp64 [n, k]).  With `radius` (per-point
     guess of the k-th neighbour distance) or a learned `mlp`, the radius-first search runs;
     tensor_cores = "fp16" or "bf16" computes its distance tiles on the tensor cores, with the
     kernel tc_variant = "auto", "staged" or "pipelined" (VB_TC_*); seed_tiles and heap_keys
-    ("compact" or "full") as in vb_knn_params.  debug=True (16-bit tiles) also returns the
+    ("compact" or "full") and curve ("auto": Hilbert order at 2 <= m <= 4, or "morton") as in
+    vb_knn_params.  debug=True (16-bit tiles) also returns the
     candidates each row kept and their 16-bit tile distances before rescoring:
     (nbr, nbr_d2, dbg_idx int32 [n, k + margin], dbg_d2 fp32 [n, k + margin])."""
     n, m = x.shape
@@ -283,6 +287,7 @@ def knn(x: torch.Tensor, k: int, margin: int = 16, prune: bool = True, radius: t
     p.tc_variant = {"auto": VB_TC_AUTO, "staged": VB_TC_STAGED, "pipelined": VB_TC_PIPELINED}[tc_variant]
     p.seed_tiles = seed_tiles
     p.heap_keys = {"compact": VB_KEYS_COMPACT, "full": VB_KEYS_FULL}[heap_keys]
+    p.curve = {"auto": 0, "morton": 1}[curve]
     nbr = torch.empty((n, k), dtype=torch.int32, device=dev)
     d2 = torch.empty((n, k), dtype=torch.float64, device=dev)
     if debug:

@@ -191,8 +191,40 @@ __global__ void bbox_kernel(const float* __restrict__ x, int64_t n, int m, int m
     }
 }
 
+// Hilbert curve index of md coordinates of `bits` bits each, by Skilling's transpose method
+// (J. Skilling, "Programming the Hilbert curve", AIP Conf. Proc. 707, 2004): undo the excess
+// work of the coordinates from the top bit down (invert the low bits of the first coordinate,
+// or exchange them with those of coordinate i), Gray-encode across the coordinates, then
+// interleave the bits as a Morton key would.  Consecutive indices are unit steps in space, so
+// the 64-point tiles of the order never straddle a jump of the curve, as Morton tiles can.
+__device__ __forceinline__ uint32_t hilbert_key(uint32_t (&X)[8], int md, int bits)
+{
+    const uint32_t M = 1u << (bits - 1);
+    for (uint32_t Q = M; Q > 1; Q >>= 1) {
+        const uint32_t P = Q - 1;
+        for (int i = 0; i < md; ++i) {
+            if (X[i] & Q) {
+                X[0] ^= P;
+            } else {
+                const uint32_t t = (X[0] ^ X[i]) & P;
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    for (int i = 1; i < md; ++i) X[i] ^= X[i - 1];
+    uint32_t t = 0;
+    for (uint32_t Q = M; Q > 1; Q >>= 1)
+        if (X[md - 1] & Q) t ^= Q - 1;
+    for (int i = 0; i < md; ++i) X[i] ^= t;
+    uint32_t k = 0;
+    for (int b = bits - 1; b >= 0; --b)
+        for (int r = 0; r < md; ++r) k = (k << 1) | ((X[r] >> b) & 1u);
+    return k;
+}
+
 __global__ void morton_kernel(const float* __restrict__ x, int64_t n, int m, int md, int bits,
-                              const int* __restrict__ bbox, uint32_t* key, uint32_t* val)
+                              const int* __restrict__ bbox, uint32_t* key, uint32_t* val, int hilbert)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -206,8 +238,12 @@ __global__ void morton_kernel(const float* __restrict__ x, int64_t n, int m, int
         q[r] = min((uint32_t)v, (1u << bits) - 1u);
     }
     uint32_t k = 0;
-    for (int b = bits - 1; b >= 0; --b)
-        for (int r = 0; r < md; ++r) k = (k << 1) | ((q[r] >> b) & 1u);
+    if (hilbert) {
+        k = hilbert_key(q, md, bits);
+    } else {
+        for (int b = bits - 1; b >= 0; --b)
+            for (int r = 0; r < md; ++r) k = (k << 1) | ((q[r] >> b) & 1u);
+    }
     key[i] = k;
     val[i] = (uint32_t)i;
 }
@@ -799,7 +835,7 @@ __device__ __forceinline__ float point_box_lb(const float* q, const float* lo, c
 // a distance bucket [lo, hi] instead of a value: runs and the certificate use its edges.
 template <int MP, int COLS = TILE, class K = uint64_t>
 __device__ bool finalize_row(const TileArgs& a, K* arr, int t, int size, bool is_heap, int64_t pq,
-                             int64_t ncl, unsigned& levels, const int* vtab = nullptr)
+                             int64_t ncl, unsigned& levels, const int* vtab = nullptr, int* short_flag = nullptr)
 {
     constexpr bool K32 = sizeof(K) == 4;
     constexpr K EMPTY = (K)~(K)0;
@@ -900,7 +936,11 @@ __device__ bool finalize_row(const TileArgs& a, K* arr, int t, int size, bool is
     }
     if (ok && out < a.k) emit();
     if (!ok) { atomicAdd(&a.rep->knn_rows_long_run, 1ull); return false; }
-    if (out < a.k) { atomicAdd(&a.rep->knn_rows_short, 1ull); return false; }
+    if (out < a.k) {
+        atomicAdd(&a.rep->knn_rows_short, 1ull);
+        if (short_flag) *short_flag = 1;
+        return false;
+    }
     // every candidate was kept (a small cloud without a radius, or an unfilled heap); a radius
     // excludes the candidates beyond it even in a small cloud, so the certificate decides there
     if ((ncl - 1 <= (int64_t)size && !a.r2) || Hkey == EMPTY) return true;
@@ -991,7 +1031,8 @@ template <> struct BandKey<uint32_t> {
 
 template <int MP, int COLS, class K = uint64_t, int D = 2>
 __device__ bool finalize_row_band(const TileArgs& a, K* arr, int t, int size, int64_t pq, int64_t ncl,
-                                  unsigned& levels, const Band& bd, float qn, const int* vtab = nullptr)
+                                  unsigned& levels, const Band& bd, float qn, const int* vtab = nullptr,
+                                  int* short_flag = nullptr)
 {
     using BK = BandKey<K>;
     for (int e = size - 1; e > 0; --e) {   // heap sort (arr is a D-ary max-heap)
@@ -1105,7 +1146,11 @@ __device__ bool finalize_row_band(const TileArgs& a, K* arr, int t, int size, in
             }
         }
     }
-    if (out < k) { atomicAdd(&a.rep->knn_rows_short, 1ull); return false; }
+    if (out < k) {
+        atomicAdd(&a.rep->knn_rows_short, 1ull);
+        if (short_flag) *short_flag = 1;
+        return false;
+    }
     // every candidate was kept (a small cloud without a radius, or an unfilled heap); with a
     // radius the candidates beyond it were never kept, so the certificate decides
     if ((ncl - 1 <= (int64_t)size && !a.r2) || Hkey == BK::EMPTY) return true;
@@ -1168,7 +1213,7 @@ __global__ void __launch_bounds__(TILE, MP <= 8 ? 10 : 8) knn_tile_kernel(TileAr
     int* vtab = (int*)(qs + (MP > 16 ? TILE * MP : 0));
     __shared__ float sqlo[MP], sqhi[MP];
     __shared__ uint32_t sred[2];
-    __shared__ int s_tile, s_nvis;
+    __shared__ int s_tile, s_nvis, s_short;
     __shared__ int s_wc[2][TILE / 32];   // block_append scratch
     int apar = 0;
     __shared__ int64_t s_ct[2];
@@ -1179,10 +1224,16 @@ __global__ void __launch_bounds__(TILE, MP <= 8 ? 10 : 8) knn_tile_kernel(TileAr
     unsigned long long evaluated = 0;
     unsigned levels = 0, staged = 0, rounds = 0;
 
+    // radius-first: a tile with a row short of k points inside its radius is searched once more at
+    // twice the radius before it goes to the exact search (its rows are rewritten)
+    bool redo = false;
     for (;;) {
         if (t == 0) {
-            const int idx = atomicAdd(a.work, 1);
-            s_tile = a.tile_list ? (idx < *a.tile_count ? a.tile_list[idx] : 0x7fffffff) : idx;
+            if (!redo) {
+                const int idx = atomicAdd(a.work, 1);
+                s_tile = a.tile_list ? (idx < *a.tile_count ? a.tile_list[idx] : 0x7fffffff) : idx;
+            }
+            s_short = 0;
         }
         __syncthreads();
         const int64_t qt = s_tile;
@@ -1228,7 +1279,7 @@ __global__ void __launch_bounds__(TILE, MP <= 8 ? 10 : 8) knn_tile_kernel(TileAr
             // candidates inside the radius ever enter and tiles are pruned from the start (appending
             // the first L keys and ordering them once instead was slower: the one-time heapify of a
             // lane holds up its warp)
-            const float R2 = valid ? __fmul_ru(a.r2[p], a.r2_scale) : 0.f;
+            const float R2 = valid ? __fmul_ru(a.r2[p], redo ? 4.f * a.r2_scale : a.r2_scale) : 0.f;
             if constexpr (K32) sentinel = ((__float_as_uint(R2) >> 13) << 14) | 0x3fffu;   // slot 0x3fff: no candidate
             else sentinel = ((uint64_t)__float_as_uint(R2) << 32) | 0xffffffffu;
             for (int sl = 0; sl < L; ++sl) heap[sl * TILE + t] = sentinel;
@@ -1490,11 +1541,16 @@ __global__ void __launch_bounds__(TILE, MP <= 8 ? 10 : 8) knn_tile_kernel(TileAr
         // ---------------- a5: order the kept candidates, rescore in FP64, certify
         bool row_ok = true;
         if (valid && !(K32 && overflow))
-            row_ok = finalize_row<MP, TILE, KT>(a, heap, t, L, fill == L, p, qhi - qlo, levels, vtab);
+            row_ok = finalize_row<MP, TILE, KT>(a, heap, t, L, fill == L, p, qhi - qlo, levels, vtab, &s_short);
         if (K32 && overflow) row_ok = false;
+        bool again = false;
         if (rmode || K32) {
-            // a row with fewer than k points inside its radius, or uncertified: redo the tile exactly
-            if (__syncthreads_or(!row_ok) && t == 0 && atomicExch(&a.fail_flag[qt], 1) == 0) {
+            // a row with fewer than k points inside its radius, or uncertified: once more at twice the
+            // radius when a row came up short, else redo the tile exactly
+            const bool fail = __syncthreads_or(!row_ok);
+            again = rmode && !redo && fail && s_short;
+            if (again && t == 0) atomicAdd(&a.rep->knn_redo_tiles, 1ull);
+            if (fail && !again && t == 0 && atomicExch(&a.fail_flag[qt], 1) == 0) {
                 a.fail_list[atomicAdd(a.fail_count, 1)] = (int)qt;
                 atomicAdd(&a.rep->knn_retry_tiles, 1ull);
             }
@@ -1503,7 +1559,8 @@ __global__ void __launch_bounds__(TILE, MP <= 8 ? 10 : 8) knn_tile_kernel(TileAr
             a.fb_list[slot] = (int)a.perm[p];
             atomicAdd(&a.rep->knn_fallback_rows, 1ull);
         }
-        __syncthreads();
+        __syncthreads();   // every thread has read s_short before thread 0 resets it
+        redo = again;
     }
     unsigned long long ev = evaluated;
 #pragma unroll
@@ -1588,7 +1645,7 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
     KT* buf = (KT*)(slist + SCAP_TC);                          // [C][T2] max-heaps
     __shared__ float sqlo[MP], sqhi[MP], scen[MP];
     __shared__ uint32_t sred[4];
-    __shared__ int s_tile, s_fail, s_abort;
+    __shared__ int s_tile, s_fail, s_abort, s_short;
     __shared__ int s_wc[2][T2 / 32];   // block_append scratch
     int apar = 0;
     __shared__ int s_need[2][T2 / 32];   // per warp: bit h set if a query needs the visit's tile h
@@ -1621,10 +1678,14 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
     constexpr uint32_t idesc = tc::idesc_f16(T2, TILE, F16);        // one candidate tile per visit
     constexpr uint32_t idesc2 = tc::idesc_f16(T2, 2 * TILE, F16);   // two
 
+    // radius-first: a query tile with a row short of k points inside its radius is searched once
+    // more at twice the radius before it goes to the FP32 search (its rows are rewritten)
+    bool redo = false;
     for (;;) {
         if (t == 0) {
-            s_tile = atomicAdd(a.work, 1);
+            if (!redo) s_tile = atomicAdd(a.work, 1);
             s_fail = 0;
+            s_short = 0;
             s_nvis = 0;
         }
         __syncthreads();
@@ -1699,7 +1760,7 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
             }
         }
         const float qn = sqrtf(sqa);
-        const float R2 = rmode && valid ? __fmul_ru(a.r2[p], a.r2_scale) : INFINITY;
+        const float R2 = rmode && valid ? __fmul_ru(a.r2[p], redo ? 4.f * a.r2_scale : a.r2_scale) : INFINITY;
         const KT sentinel = rmode ? BK::sentinel(__float_as_uint(R2)) : BK::EMPTY;
         for (int sl = 0; sl < C; ++sl) buf[sl * T2 + t] = sentinel;
         KT heapmax = sentinel;
@@ -2006,10 +2067,12 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
         if (s_abort) break;
 
         bool ok = !far && !s_fail;   // s_fail here: the visit table overflowed (compact keys)
-        if (valid && ok) ok = finalize_row_band<MP, T2, KT, TC_ARITY>(a, buf, t, C, p, qhi - qlo, levels, bd, qn, vtab);
+        if (valid && ok)
+            ok = finalize_row_band<MP, T2, KT, TC_ARITY>(a, buf, t, C, p, qhi - qlo, levels, bd, qn, vtab, &s_short);
         if (valid && !ok) s_fail = 1;
         __syncthreads();
-        if (t == 0 && s_fail) {
+        const bool again = rmode && !redo && s_fail && s_short;
+        if (!again && t == 0 && s_fail) {
             for (int h = 0; h < 2; ++h) {
                 const int64_t qt = 2 * qs + h;
                 if (qt < nt && atomicExch(&a.fail_flag[qt], 1) == 0) {
@@ -2018,7 +2081,9 @@ __global__ void __launch_bounds__(T2) knn_tc_kernel(TileArgs a)
                 }
             }
         }
-        __syncthreads();
+        if (again && t == 0) atomicAdd(&a.rep->knn_redo_tiles, 1ull);
+        __syncthreads();   // every thread has read the flags before thread 0 resets them
+        redo = again;
     }
     unsigned long long ev = evaluated, lv = levels, st = staged;
 #pragma unroll
@@ -2834,7 +2899,7 @@ static vb_status launch_tile(const TileArgs& a, cudaStream_t s)
 // coordinates in FP32 and FP64, and the boxes of 64-point tiles and 64-tile super-tiles.
 // perm (sorted position -> original index) is w.val[*cur] afterwards.
 static vb_status order_points(Ctx* ctx, const float* x, int64_t n, int32_t m, const KnnWs& w, Clouds cl,
-                              const uint32_t** perm_out)
+                              const uint32_t** perm_out, int curve = VB_CURVE_AUTO)
 {
     cudaStream_t s = ctx->stream;
     const int mp = pad_dim(m), md = morton_dims(m), bits = morton_bits(md);
@@ -2844,7 +2909,10 @@ static vb_status order_points(Ctx* ctx, const float* x, int64_t n, int32_t m, co
     const unsigned bbox_grid = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 4);
     if (m <= 4) {
         bbox_kernel<<<bbox_grid, 256, 0, s>>>(x, n, m, md, w.bbox, ctx->rep);
-        morton_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n, m, md, bits, w.bbox, w.key[0], w.val[0]);
+        // the Hilbert curve at 2 <= m <= 4 unless the caller asks for the Morton curve
+        const int hilbert = curve == VB_CURVE_AUTO && md >= 2 ? 1 : 0;
+        morton_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n, m, md, bits, w.bbox, w.key[0], w.val[0],
+                                                                  hilbert);
     } else {
         // finite check of the input, then the key on the leading principal axes
         bbox_kernel<<<bbox_grid, 256, 0, s>>>(x, n, m, 0, w.bbox, ctx->rep);
@@ -2856,7 +2924,7 @@ static vb_status order_points(Ctx* ctx, const float* x, int64_t n, int32_t m, co
         pca_project_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n, m, w.pcs + mlen, w.proj);
         bbox_kernel<<<bbox_grid, 256, 0, s>>>(w.proj, n, PCA_D, PCA_D, w.bbox, ctx->rep);
         morton_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.proj, n, PCA_D, PCA_D, bits, w.bbox, w.key[0],
-                                                                  w.val[0]);
+                                                                  w.val[0], 0);
         ctx->launches += 5;   // moments zeroed, moments, axes, projection, box of the projections
     }
     int cur = 0;
@@ -2941,7 +3009,7 @@ vb_status knn_run(Ctx* ctx, const float* x, int64_t n, int32_t m, const vb_knn_p
 
     mark(ctx, VB_STAGE_KNN_ORDER, 0);
     const uint32_t* perm = nullptr;
-    vb_status st = order_points(ctx, x, n, m, w, cl, &perm);
+    vb_status st = order_points(ctx, x, n, m, w, cl, &perm, p->curve);
     if (st != VB_OK) return st;
     mark(ctx, VB_STAGE_KNN_ORDER, 1);
 

@@ -23,6 +23,7 @@ struct DevReport {
     unsigned long long knn_rows_long_run;
     unsigned long long knn_rows_uncertified;
     unsigned long long knn_retry_candidates;
+    unsigned long long knn_redo_tiles;
 };
 static_assert(sizeof(DevReport) == sizeof(vb_report), "report layout");
 

@@ -105,9 +105,13 @@ def test_radius_search_exact_for_any_radius(vb, mode):
     assert np.array_equal(d2.cpu().numpy(), ref_d2)
     ntiles = (x.shape[0] + 63) // 64
     if mode == "small":
-        assert rep["knn_retry_tiles"] == ntiles   # nobody finds k points inside: all redone exactly
+        # nobody finds k points inside: every tile is searched again at twice the radius, and the
+        # tiles still short after that are redone exactly
+        assert rep["knn_redo_tiles"] == ntiles
+        assert rep["knn_retry_tiles"] <= ntiles
     else:
         assert rep["knn_retry_tiles"] == 0        # a loose radius only loosens the initial pruning
+        assert rep["knn_redo_tiles"] == 0
 
 
 @pytest.mark.parametrize("scale", [0.5, 1.0, 1.5])
