@@ -4,10 +4,11 @@
 // nearest other samples of every point, ordered by the canonical FP64 squared
 // distance and then by index.  The search itself runs in FP32 and is made
 // exact by an FP64 certificate:
-//   a1  Morton order: bounding box, 32-bit Morton keys of the m coordinates when
-//       m <= 4, else of the projections on the cloud's 5 leading principal axes
-//       (sampled covariance, subspace iteration), stable LSD radix sort, gather of the
-//       coordinates into 64-point tiles (zero-padded to MP = 4, 8, ..., 128).
+//   a1  spatial order: bounding box, 32-bit Hilbert keys of the m coordinates when
+//       2 <= m <= 4 (Morton keys on request, and at m = 1), else Morton keys of the
+//       projections on the cloud's 5 leading principal axes (sampled covariance,
+//       subspace iteration), stable LSD radix sort, gather of the coordinates into
+//       64-point tiles (zero-padded to MP = 4, 8, ..., 128).
 //   a2  pruning: every tile carries its bounding box; a candidate tile is
 //       skipped when the box-to-box (and, per query, point-to-box) distance,
 //       rounded down by a proven FP32 error factor, exceeds the running

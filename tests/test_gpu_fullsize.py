@@ -156,7 +156,7 @@ def test_ellipsoids_256_per_cloud(vb):
     refs = {b: M.build(bt.x[ptr[b]:ptr[b + 1]], k, d=d, c=c, beta=beta, nbr=ref_lists[b][0],
                        nbr_d2=ref_lists[b][1]) for b in sorted(sub)}
     xt = _t(bt.x)
-    for tc in (None, "fp16"):
+    for tc in (None, "fp16", "bf16"):
         builder = vb.Builder(n, 3, k, d, c, beta, cloud_ptr=ptr, tensor_cores=tc)
         builder.autotune(xt)
         vb.report_reset()

@@ -87,6 +87,25 @@ def test_knn_two_level_scan_70k(vb, prune):
     _knn_case(vb, x, 24, prune)
 
 
+@pytest.mark.parametrize("m", [2, 3, 4])
+def test_knn_hilbert_and_morton_orders(vb, m):
+    # the tile order (Hilbert curve by default at 2 <= m <= 4, or Morton) changes which tiles are
+    # visited, never the lists; the Hilbert tiles visit fewer candidate pairs on a uniform cloud
+    x = np.random.default_rng(40 + m).uniform(-1.0, 1.0, (30000, m)).astype(np.float32)
+    ref_nbr, ref_d2 = OK.knn(x, 24)
+    pairs = {}
+    for curve in ("auto", "morton"):
+        for tc in (None, "bf16"):
+            vb.report_reset()
+            nbr, d2 = vb.knn(_t(x), 24, margin=8, curve=curve, tensor_cores=tc)
+            torch.cuda.synchronize()
+            rep = vb.raise_on_device_error()
+            assert np.array_equal(nbr.cpu().numpy(), ref_nbr), (curve, tc)
+            assert np.array_equal(d2.cpu().numpy(), ref_d2), (curve, tc)
+            pairs[curve, tc] = rep["knn_candidates"]
+    assert pairs["auto", None] < pairs["morton", None], pairs
+
+
 def test_knn_torus_1m_sampled_rows(vb):
     x = W.TORUS_1M.sample()
     nbr, d2 = vb.knn(_t(x), 64)
