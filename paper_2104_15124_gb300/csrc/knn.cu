@@ -2876,7 +2876,11 @@ static vb_status launch_tile_m(const TileArgs& a, cudaStream_t s)
             return VB_ERR_CUDA;
         attr_set[dev & 15] = true;
     }
-    knn_tile_kernel<MP, MR, K32><<<(unsigned)a.ntiles, TILE, sm, s>>>(a);
+    // one CTA per tile for a full pass; a pass over a list of handed-back tiles (usually few or
+    // none) takes them from the same counter with one resident wave of CTAs, so that an empty
+    // list costs one short launch rather than a CTA per tile of the cloud
+    const int64_t grid = a.tile_list ? std::min<int64_t>(a.ntiles, 152 * 10) : a.ntiles;
+    knn_tile_kernel<MP, MR, K32><<<(unsigned)grid, TILE, sm, s>>>(a);
     return last_launch();
 }
 
