@@ -357,6 +357,67 @@ __device__ void merge_row(int64_t j, int k, int r, uint64_t* rb, const int64_t* 
     }
 }
 
+// The same for a row with at most 32 reverse entries (nearly every row), one per lane, without
+// sorting them: every reverse column is broadcast to the warp once, and each lane counts the
+// reverse columns below its own reverse entry (its rank among them; the columns of R(j) are
+// distinct) and below each of its own-list entries; a reverse entry's place among the own
+// entries is a binary search of the sorted own columns in shared memory.
+template <int OWN_PER_LANE>   // own-list entries per lane: k <= 32 OWN_PER_LANE
+__device__ void merge_row_small(int64_t j, int k, int r, const int64_t* __restrict__ row_ptr,
+                                const int32_t* __restrict__ own_col, const float* __restrict__ own_d2,
+                                const int32_t* __restrict__ rev_col, const float* __restrict__ rev_d2, int32_t* col,
+                                float* ed2, int lane, int32_t* oc_s)
+{
+    const int64_t roff = row_ptr[j] - j * (1 + k);
+    int32_t rc = INT32_MAX;
+    float rd = 0.f;
+    if (lane < r) {
+        rc = rev_col[roff + lane];
+        rd = rev_d2[roff + lane];
+    }
+    const int32_t* oc = own_col + j * k;
+    int32_t c[OWN_PER_LANE];
+    int below[OWN_PER_LANE];
+#pragma unroll
+    for (int s = 0; s < OWN_PER_LANE; ++s) {
+        const int a = lane + 32 * s;
+        c[s] = a < k ? oc[a] : INT32_MAX;
+        below[s] = 0;
+        if (a < k) oc_s[a] = c[s];
+    }
+    int rrank = 0;
+    for (int b = 0; b < r; ++b) {
+        const int32_t cb = __shfl_sync(0xffffffffu, rc, b);
+        rrank += cb < rc ? 1 : 0;
+#pragma unroll
+        for (int s = 0; s < OWN_PER_LANE; ++s) below[s] += cb < c[s] ? 1 : 0;
+    }
+    const int rev_below_j = __popc(__ballot_sync(0xffffffffu, lane < r && rc < (int32_t)j));
+    __syncwarp();   // the own columns in shared memory, for the searches below
+    const int64_t ob = row_ptr[j];
+    const float* od = own_d2 + j * k;
+#pragma unroll
+    for (int s = 0; s < OWN_PER_LANE; ++s) {
+        const int a = lane + 32 * s;
+        if (a < k) {
+            const int rank = a + below[s] + ((int32_t)j < c[s] ? 1 : 0);
+            col[ob + rank] = c[s];
+            ed2[ob + rank] = fabsf(od[a]);   // without the non-mutual mark
+        }
+    }
+    if (lane < r) {
+        const int rank = rrank + lower_bound_i32(oc_s, k, rc) + ((int32_t)j < rc ? 1 : 0);
+        col[ob + rank] = rc;
+        ed2[ob + rank] = rd;
+    }
+    if (lane == 0) {
+        const int rank = lower_bound_i32(oc_s, k, (int32_t)j) + rev_below_j;
+        col[ob + rank] = (int32_t)j;
+        ed2[ob + rank] = 0.f;
+    }
+}
+
+template <int KL>   // own-list entries per lane, k <= 32 KL
 __global__ void __launch_bounds__(SORT_WARPS * 32) merge_kernel(const int64_t* __restrict__ row_ptr, int64_t n, int k,
                                                                  const int32_t* __restrict__ own_col,
                                                                  const float* __restrict__ own_d2,
@@ -382,7 +443,10 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) merge_kernel(const int64_t* _
             }
             continue;
         }
-        merge_row(j, k, r, buf[w], row_ptr, own_col, own_d2, rev_col, rev_d2, col, ed2, lane, 32, true, ocs[w]);
+        if (r <= 32)
+            merge_row_small<KL>(j, k, r, row_ptr, own_col, own_d2, rev_col, rev_d2, col, ed2, lane, ocs[w]);
+        else
+            merge_row(j, k, r, buf[w], row_ptr, own_col, own_d2, rev_col, rev_d2, col, ed2, lane, 32, true, ocs[w]);
         __syncwarp();
     }
 }
@@ -444,7 +508,17 @@ vb_status graph_run(Ctx* ctx, int64_t n, int32_t k, const int32_t* nbr, const do
     vb_status st = scan_counts(s, w.cnt, n, row_ptr, w.scan);
     if (st != VB_OK) return st;
     reverse_kernel<<<ge, 256, 0, s>>>(w.own_col, w.own_d2, n, k, row_ptr, w.fill, w.rev_col, w.rev_d2);
-    merge_kernel<<<152 * 16, SORT_WARPS * 32, 0, s>>>(row_ptr, n, k, w.own_col, w.own_d2, w.rev_col, w.rev_d2, col, ed2,
+    if (k <= 32)
+        merge_kernel<1><<<152 * 16, SORT_WARPS * 32, 0, s>>>(row_ptr, n, k, w.own_col, w.own_d2, w.rev_col, w.rev_d2, col, ed2,
+                                                      cap, w.big, w.nbig, nnz_dev, ctx->rep);
+    else if (k <= 64)
+        merge_kernel<2><<<152 * 16, SORT_WARPS * 32, 0, s>>>(row_ptr, n, k, w.own_col, w.own_d2, w.rev_col, w.rev_d2, col, ed2,
+                                                      cap, w.big, w.nbig, nnz_dev, ctx->rep);
+    else if (k <= 128)
+        merge_kernel<4><<<152 * 16, SORT_WARPS * 32, 0, s>>>(row_ptr, n, k, w.own_col, w.own_d2, w.rev_col, w.rev_d2, col, ed2,
+                                                      cap, w.big, w.nbig, nnz_dev, ctx->rep);
+    else
+        merge_kernel<OWN_CAP / 32><<<152 * 16, SORT_WARPS * 32, 0, s>>>(row_ptr, n, k, w.own_col, w.own_d2, w.rev_col, w.rev_d2, col, ed2,
                                                       cap, w.big, w.nbig, nnz_dev, ctx->rep);
     static bool big_attr[16] = {};
     int dev = ctx->device & 15;
