@@ -165,14 +165,14 @@ vb_status sweep_run(Ctx* ctx, const vb_graph* g, const double* rho, double scale
                     void* ws, size_t ws_bytes, Clouds cl = Clouds());
 size_t density_ws_bytes(int64_t n, int B = 1);
 vb_status density_run(Ctx* ctx, const vb_graph* g, const double* b, const double* eps2_dev, double d, double beta,
-                      double* psi, double* P, void* ws, size_t ws_bytes, Clouds cl = Clouds(), int lpr = 16);
+                      double* psi, double* P, void* ws, size_t ws_bytes, Clouds cl = Clouds(), int lpr = 8);
 size_t centre_ws_bytes(int64_t n, int B = 1);
 vb_status centre_run(Ctx* ctx, const vb_graph* g, const double* b, const double* P, double* xi_c_dev, void* ws,
                      size_t ws_bytes, Clouds cl = Clouds());
 size_t kernel_csr_ws_bytes(int64_t n, int B = 1);
 vb_status kernel_csr_run(Ctx* ctx, const vb_graph* g, const double* psi, const double* P, const vb_op_params* op,
                          const double* eps2_op_dev, float* val, double* q, double* D, double* S, void* ws,
-                         size_t ws_bytes, Clouds cl = Clouds(), int lpr = 16);
+                         size_t ws_bytes, Clouds cl = Clouds(), int lpr = 8);
 size_t spmv_ws_bytes(int64_t n);
 vb_status spmv_lap_launch(cudaStream_t s, const vb_graph* g, const float* val, const double* S, float alpha,
                           const float* x, float beta, float* y, double* z, float* sf);
