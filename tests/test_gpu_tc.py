@@ -114,3 +114,32 @@ def test_split_operand_tile_distances(name, m, prec, u, dabs):
     E = 1.01 * (2.0 * np.sqrt(d) * delta + delta ** 2 + 2 * (16 + 4) * 2.0 ** -24 * Z ** 2)
     assert np.all(np.abs(dt - d) <= E)
     assert np.max(np.abs(dt - d) / D) < 1e-3
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_short_radius_tiles_are_searched_again_in_the_launch(prec):
+    """Radius-first 16-bit search with a radius far below the k-th neighbour distance: every
+    128-point query tile has a row short of k points, is searched again at twice the radius by
+    the same CTA, and whatever is still short goes to the FP32 search; the lists stay exact."""
+    import paper_2104_15124_gb300 as vb
+    from paper_2104_15124_gb300 import workloads as W
+    n, k = 12000, 32
+    x = W.torus4(n, 0.01, 41)
+    ref_nbr, ref_d2 = _knn_ref(x, k)
+    rk = np.sqrt(ref_d2[:, k - 1]).astype(np.float32)
+    xt = torch.from_numpy(x).cuda()
+    qtiles, tiles = (n + 127) // 128, (n + 63) // 64
+    # inside 0.85 r_k no row holds k points, so every query tile is searched again: at 1.7 r_k
+    # every row is settled; at 0.6 r_k none is, and every tile goes on to the FP32 search
+    for scale, retried in ((0.85, 0), (0.3, tiles)):
+        vb.report_reset()
+        nbr, d2 = vb.knn(xt, k, margin=8, radius=torch.from_numpy(scale * rk).cuda(), inflate=1.0,
+                         tensor_cores=prec, tc_variant="staged")
+        torch.cuda.synchronize()
+        rep = vb.raise_on_device_error()
+        assert np.array_equal(nbr.cpu().numpy(), ref_nbr), scale
+        assert np.array_equal(d2.cpu().numpy(), ref_d2), scale
+        assert rep["knn_redo_tiles"] == qtiles, (scale, rep["knn_redo_tiles"])
+        # (the FP32 pass over handed-back tiles counts the few it hands on in turn)
+        assert rep["knn_retry_tiles"] >= retried and (retried or rep["knn_retry_tiles"] == 0), \
+            (scale, rep["knn_retry_tiles"])
