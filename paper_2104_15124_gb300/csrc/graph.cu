@@ -247,6 +247,34 @@ __global__ void kth_kernel(const int32_t* __restrict__ nbr, const double* __rest
 // (the reverse entries of row j): (i -> j) is mutual exactly when (d2(i, j), i) does not exceed
 // the k-th pair of j's own list (kth[j]).  A non-mutual entry carries the sign bit in own_d2
 // (distances are >= 0), so the scatter pass reads the sorted lists alone.
+// For k <= 64 and n <= 2^26 the list is instead sorted as 32-bit keys column << 6 | position
+// (columns distinct, so the order is the columns' order) by a bitonic network across the warp,
+// two keys per lane: 21 compare-exchange steps of one shuffle each instead of k broadcasts with
+// k compares, and each sorted key names the entry it came from.
+template <int KL>
+__device__ __forceinline__ void warp_bitonic(uint32_t (&key)[KL], int lane)
+{
+    constexpr int N = 32 * KL;
+#pragma unroll
+    for (int size = 2; size <= N; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride == 32) {   // N = 64: the partner is this lane's other key
+                const uint32_t a = key[0], b = key[KL - 1];
+                key[0] = min(a, b);
+                key[KL - 1] = max(a, b);
+            } else {
+#pragma unroll
+                for (int s = 0; s < KL; ++s) {
+                    const uint32_t o = __shfl_xor_sync(0xffffffffu, key[s], stride);
+                    const bool lower = (lane & stride) == 0, up = ((lane + 32 * s) & size) == 0;
+                    key[s] = lower == up ? min(key[s], o) : max(key[s], o);
+                }
+            }
+        }
+    }
+}
+
 template <int KL>
 __global__ void __launch_bounds__(SORT_WARPS * 32) own_sort_kernel(const int32_t* __restrict__ nbr,
                                                                     const double* __restrict__ nbr_d2, int64_t n,
@@ -254,6 +282,35 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) own_sort_kernel(const int32_t
                                                                     const Kth* __restrict__ kth, int32_t* rcnt)
 {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if constexpr (KL <= 2) {
+        if (n <= ((int64_t)1 << 26)) {
+            for (int64_t i = (int64_t)blockIdx.x * SORT_WARPS + w; i < n; i += (int64_t)gridDim.x * SORT_WARPS) {
+                const int32_t* row = nbr + i * k;
+                uint32_t key[KL];
+#pragma unroll
+                for (int s = 0; s < KL; ++s) {
+                    const int e = lane + 32 * s;
+                    key[s] = e < k ? ((uint32_t)row[e] << 6) | (uint32_t)e : 0xffffffffu;
+                }
+                warp_bitonic<KL>(key, lane);
+#pragma unroll
+                for (int s = 0; s < KL; ++s) {
+                    const int pos = lane + 32 * s;   // the key's place in the sorted list
+                    if (pos < k) {
+                        const int32_t j = (int32_t)(key[s] >> 6);
+                        const int e = (int)(key[s] & 63u);
+                        const double d = nbr_d2[i * k + e];
+                        const Kth q = kth[j];
+                        const bool rev = !(d < q.d2 || (d == q.d2 && (int32_t)i <= q.idx));
+                        own_col[i * k + pos] = j;
+                        own_d2[i * k + pos] = rev ? -(float)d : (float)d;
+                        if (rev) atomicAdd(&rcnt[j], 1);
+                    }
+                }
+            }
+            return;
+        }
+    }
     for (int64_t i = (int64_t)blockIdx.x * SORT_WARPS + w; i < n; i += (int64_t)gridDim.x * SORT_WARPS) {
         const int32_t* row = nbr + i * k;
         int32_t c[KL];
