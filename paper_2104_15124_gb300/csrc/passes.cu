@@ -81,6 +81,36 @@ __device__ __forceinline__ void load_entries(const int32_t* __restrict__ col, co
     }
 }
 
+// The lane's quad of consecutive entries b0 .. b0 + 3 (b0 a multiple of 4) of the row [rb, re):
+// one 16-byte load of the columns and one of the squared distances when the quad lies inside
+// the row and the arrays are 16-byte aligned, else four masked loads (column -1 outside the
+// row).  A group of LPR lanes covers 4 LPR consecutive entries per step, so each load
+// instruction of the group reads whole 16-byte pieces.
+static_assert(UNR == 4, "a quad of entries per lane");
+__device__ __forceinline__ void load_quad(const int32_t* __restrict__ col, const float* __restrict__ ed2, bool vec,
+                                          int64_t b0, int64_t rb, int64_t re, int32_t* jj, float* xx)
+{
+    if (vec && b0 >= rb && b0 + 3 < re) {
+        const int4 c4 = *(const int4*)(col + b0);
+        const float4 x4 = *(const float4*)(ed2 + b0);
+        jj[0] = c4.x; jj[1] = c4.y; jj[2] = c4.z; jj[3] = c4.w;
+        xx[0] = x4.x; xx[1] = x4.y; xx[2] = x4.z; xx[3] = x4.w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t e = b0 + u;
+            const bool in = e >= rb && e < re;
+            jj[u] = in ? col[e] : -1;
+            xx[u] = in ? ed2[e] : 0.f;
+        }
+    }
+}
+__device__ __forceinline__ bool aligned16(const void* a, const void* b)
+{
+    return (((uintptr_t)a | (uintptr_t)b) & 15u) == 0;
+}
+__device__ __forceinline__ int64_t quad_start(int64_t rb, int sub) { return (rb & ~(int64_t)3) + 4 * (int64_t)sub; }
+
 __global__ void recip_f32_kernel(const double* __restrict__ v, int64_t n, float scale, float* out)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -455,6 +485,7 @@ __global__ void __launch_bounds__(kRowThreads) density_kernel(const int64_t* __r
                                                             const float* __restrict__ cden, Clouds cl, double* psi)
 {
     RowGroup<LPR> it;
+    const bool vec = aligned16(col, ed2);
     for (int64_t b0 = it.base; b0 < n; b0 += it.step) {
         const int64_t i = b0 + it.grp;
         const bool ok = i < n;
@@ -462,10 +493,10 @@ __global__ void __launch_bounds__(kRowThreads) density_kernel(const int64_t* __r
         const int64_t rb = ok ? row_ptr[i] : 0, re = ok ? row_ptr[i + 1] : 0;
         const float bi = ok ? ib[i] : 0.f;
         float s = 0.f;
-        for (int64_t e0 = rb + it.sub; e0 < re; e0 += UNR * LPR) {
+        for (int64_t e0 = quad_start(rb, it.sub); e0 < re; e0 += 4 * LPR) {
             int32_t jj[UNR];
             float xx[UNR];
-            load_entries<LPR>(col, ed2, e0, re, jj, xx);
+            load_quad(col, ed2, vec, e0, rb, re, jj, xx);
 #pragma unroll
             for (int u = 0; u < UNR; ++u)
                 if (jj[u] >= 0) s += ex2_approx(-(xx[u] * (bi * ib[jj[u]])) * c);
@@ -680,12 +711,11 @@ __global__ void op_const_kernel(const double* __restrict__ eps2, int B, C1* out)
 }
 
 // A lane's next UNR entries with their column records gathered, all loads in flight together.
-template <int LPR>
 __device__ __forceinline__ void load_op_entries(const int32_t* __restrict__ col, const float* __restrict__ ed2,
-                                                const PointOp* __restrict__ pv, int64_t e0, int64_t re, int32_t* jj,
-                                                float* xx, PointOp* pj)
+                                                const PointOp* __restrict__ pv, bool vec, int64_t e0, int64_t rb,
+                                                int64_t re, int32_t* jj, float* xx, PointOp* pj)
 {
-    load_entries<LPR>(col, ed2, e0, re, jj, xx);
+    load_quad(col, ed2, vec, e0, rb, re, jj, xx);
 #pragma unroll
     for (int u = 0; u < UNR; ++u)
         if (jj[u] >= 0) pj[u] = pv[jj[u]];
@@ -704,6 +734,7 @@ __global__ void __launch_bounds__(kRowThreads) q_kernel(const int64_t* __restric
 {
     const float mbd = (float)(-beta * d), malpha = (float)(-alpha);
     RowGroup<LPR> it;
+    const bool vec = aligned16(col, ed2);
     for (int64_t b0 = it.base; b0 < n; b0 += it.step) {
         const int64_t i = b0 + it.grp;
         const bool ok = i < n;
@@ -711,11 +742,11 @@ __global__ void __launch_bounds__(kRowThreads) q_kernel(const int64_t* __restric
         const int64_t rb = ok ? row_ptr[i] : 0, re = ok ? row_ptr[i + 1] : 0;
         const float ph = ok ? pv[i].iPh : 0.f, pl = ok ? pv[i].iPl : 0.f;
         float s = 0.f;
-        for (int64_t e0 = rb + it.sub; e0 < re; e0 += UNR * LPR) {
+        for (int64_t e0 = quad_start(rb, it.sub); e0 < re; e0 += 4 * LPR) {
             int32_t jj[UNR];
             float xx[UNR];
             PointOp pj[UNR];
-            load_op_entries<LPR>(col, ed2, pv, e0, re, jj, xx, pj);
+            load_op_entries(col, ed2, pv, vec, e0, rb, re, jj, xx, pj);
 #pragma unroll
             for (int u = 0; u < UNR; ++u)
                 if (jj[u] >= 0) s += k_op(xx[u], ph, pl, pj[u].iPh, pj[u].iPl, c1.h, c1.l);
@@ -743,6 +774,7 @@ __global__ void __launch_bounds__(kRowThreads) d_kernel(const int64_t* __restric
                                                       const C1* __restrict__ cop, Clouds cl, double* D, double* S)
 {
     RowGroup<LPR> it;
+    const bool vec = aligned16(col, ed2);
     for (int64_t b0 = it.base; b0 < n; b0 += it.step) {
         const int64_t i = b0 + it.grp;
         const bool ok = i < n;
@@ -750,11 +782,11 @@ __global__ void __launch_bounds__(kRowThreads) d_kernel(const int64_t* __restric
         const int64_t rb = ok ? row_ptr[i] : 0, re = ok ? row_ptr[i + 1] : 0;
         const PointOp pi = ok ? pv[i] : PointOp{0.f, 0.f, 0.f, 0.f};
         float s = 0.f;
-        for (int64_t e0 = rb + it.sub; e0 < re; e0 += UNR * LPR) {
+        for (int64_t e0 = quad_start(rb, it.sub); e0 < re; e0 += 4 * LPR) {
             int32_t jj[UNR];
             float xx[UNR];
             PointOp pj[UNR];
-            load_op_entries<LPR>(col, ed2, pv, e0, re, jj, xx, pj);
+            load_op_entries(col, ed2, pv, vec, e0, rb, re, jj, xx, pj);
 #pragma unroll
             for (int u = 0; u < UNR; ++u) {
                 if (jj[u] < 0) continue;
@@ -772,7 +804,7 @@ __global__ void __launch_bounds__(kRowThreads) d_kernel(const int64_t* __restric
 }
 
 template <int LPR>
-__global__ void __launch_bounds__(kRowThreads) lhat_kernel(const int64_t* __restrict__ row_ptr,
+__global__ void __launch_bounds__(kRowThreads, 4) lhat_kernel(const int64_t* __restrict__ row_ptr,
                                                          const int32_t* __restrict__ col,
                                                          const float* __restrict__ ed2, int64_t n,
                                                          const PointOp* __restrict__ pv, const double* __restrict__ S,
@@ -780,6 +812,7 @@ __global__ void __launch_bounds__(kRowThreads) lhat_kernel(const int64_t* __rest
                                                          const double* __restrict__ eps2_dev, Clouds cl, float* val)
 {
     RowGroup<LPR> it;
+    const bool vec = aligned16(col, ed2) && aligned16(val, val);
     for (int64_t b0 = it.base; b0 < n; b0 += it.step) {
         const int64_t i = b0 + it.grp;
         const bool ok = i < n;
@@ -790,20 +823,28 @@ __global__ void __launch_bounds__(kRowThreads) lhat_kernel(const int64_t* __rest
         const PointOp pi = ok ? pv[i] : PointOp{0.f, 0.f, 0.f, 0.f};
         float off = 0.f;
         int64_t diag = -1;
-        for (int64_t e0 = rb + it.sub; e0 < re; e0 += UNR * LPR) {
+        for (int64_t e0 = quad_start(rb, it.sub); e0 < re; e0 += 4 * LPR) {
             int32_t jj[UNR];
             float xx[UNR];
             PointOp pj[UNR];
-            load_op_entries<LPR>(col, ed2, pv, e0, re, jj, xx, pj);
+            load_op_entries(col, ed2, pv, vec, e0, rb, re, jj, xx, pj);
+            float vq[UNR];
 #pragma unroll
             for (int u = 0; u < UNR; ++u) {
-                const int64_t e = e0 + u * LPR;
+                vq[u] = 0.f;
                 const int32_t j = jj[u];
                 if (j < 0) continue;
-                if (j == i) { diag = e; continue; }
+                if (j == i) { diag = e0 + u; continue; }
                 const float kt = k_op(xx[u], pi.iPh, pi.iPl, pj[u].iPh, pj[u].iPl, c1.h, c1.l) * (pi.qa * pj[u].qa);
                 off += kt;
-                val[e] = kt * (pi.iS * pj[u].iS) * ie;
+                vq[u] = kt * (pi.iS * pj[u].iS) * ie;
+            }
+            if (vec && e0 >= rb && e0 + 3 < re) {   // one 16-byte store (a diagonal slot is rewritten below)
+                *(float4*)(val + e0) = make_float4(vq[0], vq[1], vq[2], vq[3]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < UNR; ++u)
+                    if (jj[u] >= 0 && jj[u] != i) val[e0 + u] = vq[u];
             }
         }
         const double tot = (double)RowGroup<LPR>::sum(off);
