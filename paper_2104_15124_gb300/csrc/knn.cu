@@ -1586,18 +1586,20 @@ __global__ void __launch_bounds__(TILE, MP <= 8 ? 10 : 8) knn_tile_kernel(TileAr
 
 // ------------------------------------------------------------------ 16-bit distance tiles on the tensor cores (a15)
 // Query tiles of 128 points (two 64-point tiles, one TMEM lane and one thread per
-// query) against 64-point candidate tiles: per candidate tile one chain of
-// tcgen05.mma (kind::f16, M = 128, N = 64, K = m padded to 16; BF16 or FP16 operands,
-// FP32 accumulation in tensor memory) gives the 128 x 64 dot products, read back
+// query) against candidate tiles, two 64-point tiles per visit: one chain of
+// tcgen05.mma (kind::f16, M = 128, N = 128, K = m padded to 16; BF16 or FP16 operands,
+// FP32 accumulation in tensor memory) gives the 128 x 128 dot products, read back
 // with tcgen05.ld; distances are |q~|^2 + |x~|^2 - 2 q~.x~ with both operands
-// recentred on the query tile's box centre before rounding.  As in the FP32 search,
-// candidate tiles are sorted by box distance, visited nearest first, and skipped
-// once their box distance passes the largest heap bound of the query tile, which
-// tightens after every visit; each query keeps a 4-ary max-heap of its k + margin
+// recentred on the query tile's box centre before rounding, and at m <= 4 each
+// coordinate carried as a hi + lo pair (see SPLIT below).  As in the FP32 search,
+// candidate tiles are sorted by box distance (super-tiles first), visited nearest first,
+// and skipped once their box distance passes the largest heap bound of the query tile,
+// which tightens after every visit; each query keeps a 4-ary max-heap of its k + margin
 // smallest keys, started full of sentinels at its radius bound when a radius is
 // given (learned pruning) and at +inf otherwise.  Rows are finished by
-// finalize_row_band; a query tile with a row that is not certified goes to the
-// exact FP32 search.
+// finalize_row_band.  With a radius, a query tile with a row short of k points is
+// searched again at twice the radius by the same CTA; a tile still failing (short,
+// uncertified, or past the visit table) goes to the exact FP32 search.
 constexpr int T2 = 128;
 constexpr int TC_ARITY = 4;   // the per-query heaps are 4-ary
 constexpr int SCAP_TC = 512;  // sorted candidate-tile list: tiles in the first half, super-tiles in the second
